@@ -1,0 +1,320 @@
+"""Benchmark of the GGEM slit matvec (single + double layer) on GB300.
+
+Step: one pass of the hot path over the workload -- the single-layer and the
+double-layer operators evaluated at every node (Sec. 3.4, 3.5 of Kumar &
+Graham, arXiv 1109.6587) for fresh N(0,1) densities.
+
+Workload (default): 100 spherical capsules x 642 nodes = 64,200 points in a
+40 x [-5,5] x 40 slit, grid 128 x 65 x 128, mixed precision, nodal quadrature.
+Metric: Mpts/s = nodes / (time of one single + one double layer evaluation).
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+For N > 1 under torchrun each rank runs an independent replica on its own
+GPU (the evaluation is one problem per GPU; no collective), value = sum of
+the ranks' points / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GGEM slit matvec Mpts/s; GMRES iters & s/solve, learned vs plain at 1e-6"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--quadrature", default="nodal", choices=["nodal", "element"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload():
+    from paper_1109_6587_gb300 import workloads as W
+    return W.capsules_100(seed=0)
+
+
+def _config(susp, args):
+    b = susp.box
+    return {"workload": "100 spherical capsules x 642 nodes (64,200 points), slit 40 x [-5,5] x 40",
+            "n_points": int(susp.x.shape[0]), "grid": [b.Nx, b.Ny, b.Nz],
+            "precision": args.precision, "quadrature": args.quadrature,
+            "step": "single-layer + double-layer matvec",
+            "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _pair_count(susp, rcut):
+    """Number of (target, source) pairs with 0 < r < r_cut (minimum image in x, z)."""
+    from scipy.spatial import cKDTree
+    b = susp.box
+    x = susp.x.copy()
+    x[:, 0] %= b.Lx
+    x[:, 2] %= b.Lz
+    x[:, 1] -= b.y0
+    tree = cKDTree(x, boxsize=[b.Lx, 4 * b.W + 4 * rcut, b.Lz])
+    return 2 * len(tree.query_pairs(rcut, output_type="ndarray"))
+
+
+def run_mine(args, rank, world):
+    import torch
+    from paper_1109_6587_gb300 import ggem
+
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.device("cuda")
+    susp = _workload()
+    n = susp.x.shape[0]
+    P = ggem.Plan.for_box(susp.box, precision=args.precision, quadrature=args.quadrature,
+                          max_points=n, max_tris=susp.tri.shape[0])
+    P.mesh_set(torch.as_tensor(susp.x, device=dev), torch.as_tensor(susp.tri, device=dev))
+    rng = np.random.default_rng(1234 + rank)
+    qs = [torch.as_tensor(rng.standard_normal((n, 3)), device=dev) for _ in range(4)]
+    w = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    v = torch.empty_like(w)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        P.single_layer(qs[i % 4], w)
+        P.double_layer(qs[i % 4], v)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = P.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = P.launch_count() - l0
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+    ms_step = t_ms / args.steps
+    value = world * n / (ms_step * 1e-3) / 1e6
+
+    # per-stage device times (traced pass, same stream)
+    P.trace(True)
+    for i in range(args.steps):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    stages = P.trace_read()
+    P.trace(False)
+
+    # end to end through the C ABI with host buffers (copies inside the timer)
+    qh = [np.ascontiguousarray(q.cpu().numpy()) for q in qs]
+    wh = np.empty((n, 3))
+    vh = np.empty((n, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        P.single_layer(qh[i % 4], wh)
+        P.double_layer(qh[i % 4], vh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    return dict(n=n, value=value, ms_step=ms_step, launches=launches, clocks=clk.summary(),
+                stages=stages, e2e_s=e2e_s, susp=susp, P=P)
+
+
+def roofline(res, args):
+    """Dominant stage against its bound (roofline accounting)."""
+    peaks, kind = _peaks()
+    stages = res["stages"]
+    name, (tot, calls) = max(stages.items(), key=lambda kv: kv[1][0])
+    avg_s = tot / calls * 1e-3
+    susp = res["susp"]
+    a, rc = res["P"].info()
+    n = res["n"]
+    b = susp.box
+    esz = 4 if args.precision == "mixed" else 8
+    plane = b.Nz * b.Nx
+    if name == "local_sum":
+        pairs = _pair_count(susp, rc)
+        # FLOPs per pair: single layer 52, double layer 70, averaged
+        flops = pairs * 61.0
+        sm_mhz = res["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / avg_s / 1e12
+        if args.precision == "fp64":
+            peak = 1.25
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+                if args.precision == "mixed" else "nominal FP64"}
+    # memory-bound stages: algorithmic bytes per launch
+    ncomp_out = 4.5  # average of single (3) and double (6) outputs
+    bytes_per = {
+        "fft_forward": 2 * 2 * (3 * b.Ny + 6) * plane * esz,
+        "fft_inverse": 2 * 2 * ncomp_out * b.Ny * plane * esz,
+        "cheb_forward": 2 * 3 * b.Ny * plane * esz,
+        "cheb_inverse": 2 * ncomp_out * b.Ny * plane * esz,
+        "tau_solve": (3 + ncomp_out) * b.Ny * plane * esz + 3 * b.Ny * (plane // 2) * 8,
+        "spread": 3 * b.Ny * plane * esz + n * 32,
+        "interpolate": ncomp_out * b.Ny * plane * esz + n * 48,
+        "wall_local_sum": 6 * plane * esz + n * 32,
+    }.get(name, 0)
+    ach = bytes_per / avg_s / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None, "peak_source": kind}
+
+
+def cpu_baseline(susp, args):
+    """The FP64 oracle as it stands on the host cores: one single- and one
+    double-layer evaluation (nodal quadrature) of the full workload."""
+    from oracle import oracle as O
+    q = np.random.default_rng(99).standard_normal((susp.x.shape[0], 3))
+    t0 = time.perf_counter()
+    O.single_layer(susp, q, quadrature=args.quadrature)
+    O.double_layer(susp, q, quadrature=args.quadrature)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": susp.x.shape[0] / dt / 1e6, "unit": "Mpts/s", "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": "one FP64 single-layer + double-layer evaluation of the full workload "
+                      f"({args.quadrature} quadrature, OpenMP over targets/planes)"}
+
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        susp = _workload()
+        times = []
+        for _ in range(args.warmup):
+            pass       # the oracle has no warm-up state
+        cb = None
+        for _ in range(max(1, min(args.steps, 3))):
+            cb = cpu_baseline(susp, args)
+            times.append(cb["seconds"])
+        ms = float(np.median(times)) * 1e3
+        val = susp.x.shape[0] / (ms * 1e-3) / 1e6
+        cb["value"] = val
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
+                "n_gpus": args.gpus, "steps": len(times), "warmup": 0, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": _config(susp, args),
+                "cpu_baseline": cb,
+                "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_mine(args, rank, world)
+    n = res["n"]
+    line = {"metric": METRIC, "value": res["value"], "unit": "Mpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": _config(res["susp"], args),
+            "e2e": {"value": world * n / res["e2e_s"] / 1e6, "unit": "Mpts/s",
+                    "h2d_bytes_per_step": 2 * n * 3 * 8, "d2h_bytes_per_step": 2 * n * 3 * 8},
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "stages_ms": {k: v[0] / v[1] for k, v in res["stages"].items()}}
+    line["roofline"] = roofline(res, args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(res["susp"], args)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * ggem.h -- C ABI of libggem, a GB300 (sm_103a) implementation of the GGEM
+ * evaluation of Stokes flow driven by point forces in a planar slit, and of
+ * the boundary-integral operators and Fredholm solve built on it.
+ *
+ * Paper: Kumar & Graham, "Accelerated boundary integral method for multiphase
+ * flow in non-periodic geometries", arXiv 1109.6587.
+ *
+ * Geometry: walls at y = y0 and y = y0 + W (no slip), periodic in x (period
+ * Lx) and z (period Lz); grid of Nx x Nz equispaced Fourier nodes times Ny
+ * Gauss-Lobatto Chebyshev nodes y_j = y0 + W/2 (1 + cos(pi j/(Ny-1))).
+ *
+ * Conventions for every entry point:
+ *  - Arrays of doubles; vectors are stored point-major, [n][3] (x, y, z).
+ *    Stresses are [n][6] in the order xx, xy, xz, yy, yz, zz.
+ *  - Array arguments may be device pointers (cudaMalloc, torch CUDA tensors)
+ *    or host pointers (pageable or pinned); the library detects which.  Host
+ *    inputs are copied to plan-owned device buffers and host outputs are
+ *    copied back before the call returns.  With device pointers the call is
+ *    asynchronous on the plan's stream.
+ *  - The caller owns every input and output array; the plan owns all
+ *    workspaces.  No entry point below allocates device memory except
+ *    ggem_plan and ggem_mesh_set (which sizes its mesh tables once).
+ *  - Every entry point returns a ggem_status; no C++ exception crosses the
+ *    ABI.  On error ggem_last_error(plan) gives a message.
+ */
+#ifndef GGEM_H
+#define GGEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GGEM_OK = 0,
+    GGEM_ERR_INVALID_ARG = 1,   /* bad size, pointer, or geometry parameter   */
+    GGEM_ERR_CAPACITY = 2,      /* more points/triangles than the plan holds  */
+    GGEM_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
+    GGEM_ERR_NUMERICAL = 4,     /* NaN/Inf detected                            */
+    GGEM_ERR_NOT_CONVERGED = 5, /* iterative solve hit its iteration limit     */
+    GGEM_OK_BREAKDOWN = 6       /* GMRES happy breakdown: exact solution found */
+} ggem_status;
+
+enum { GGEM_FP64 = 0, GGEM_MIXED = 1 };          /* ggem_params.precision  */
+enum { GGEM_NODAL = 0, GGEM_ELEMENT = 1 };       /* ggem_params.quadrature */
+
+typedef struct ggem_plan ggem_plan_t;
+
+/*
+ * Parameters of a plan (Sec. 3.2 and Sec. 5 of the paper).
+ *   alpha        splitting parameter of Eq. (rho_l_g); 0 selects
+ *                1/(2 max(Lx/Nx, W/(Ny-1), Lz/Nz)), i.e. alpha*dy_m <= 0.5.
+ *   rcut_factor  r_cut = rcut_factor/alpha; 0 selects 4 (Sec. 3.2.1).
+ *   precision    GGEM_FP64: every step in FP64.  GGEM_MIXED: local sum,
+ *                spreading, FFT, Chebyshev transforms and interpolation in
+ *                FP32; per-mode tau solves in FP64.
+ *   quadrature   GGEM_ELEMENT: local part by the 4x4 Gauss product rule per
+ *                triangle with the polar rule on triangles touching the
+ *                target (Sec. 3.4.1, 3.5.2).  GGEM_NODAL: nodal point forces
+ *                A_b q_b with the self pair left out.
+ *   max_points   capacity for nodes / point sources / targets.
+ *   max_tris     capacity for triangles (element quadrature).
+ * Requirements: Nx, Nz powers of two in [16, 1024]; 9 <= Ny <= 257;
+ * alpha*Lx > 2*rcut_factor and alpha*Lz > 2*rcut_factor (Sec. 3.2.2: r_cut
+ * below half the period); W > 0; mu > 0.
+ */
+typedef struct {
+    double Lx, Lz, W, y0;
+    int Nx, Ny, Nz;
+    double alpha;
+    double rcut_factor;
+    double mu;
+    int precision;
+    int quadrature;
+    int max_points;
+    int max_tris;
+} ggem_params;
+
+/* Create a plan on a CUDA stream (cudaStream_t passed as void*; NULL = the
+ * legacy default stream).  Builds the grid, the Chebyshev and FFT tables and,
+ * for every Fourier mode, the homogeneous Kleiser-Schumann solutions and the
+ * inverse 2x2 influence matrix (App. C: "solved just once ... and stored").
+ * Allocates all workspaces.  *out receives the plan, or NULL on error. */
+ggem_status ggem_plan(const ggem_params *params, void *stream, ggem_plan_t **out);
+
+/* Free a plan and all its device memory.  NULL is accepted. */
+ggem_status ggem_plan_destroy(ggem_plan_t *plan);
+
+/* Message describing the last error on this plan (static text for NULL). */
+const char *ggem_last_error(const ggem_plan_t *plan);
+
+/* Effective alpha and r_cut of the plan (host values). */
+ggem_status ggem_plan_info(const ggem_plan_t *plan, double *alpha, double *rcut);
+
+/*
+ * Set the surface mesh (Sec. 3.3): n_nodes nodes x [n][3] and n_tris
+ * outward-oriented triangles tri [m][3] (node indices).  Each particle's
+ * nodes must be unwrapped (one periodic image per triangle).  Computes
+ * element areas A_k, nodal areas A_b = sum A_k / 3, area-averaged unit node
+ * normals (Sec. 3.4.2, 3.5.2), the cell list of the nodes and, for element
+ * quadrature, the quadrature points.  Every node must satisfy
+ * y0 < y < y0 + W.  n_tris may be 0 for GGEM_NODAL.
+ */
+ggem_status ggem_mesh_set(ggem_plan_t *plan, int n_nodes, const double *x,
+                          int n_tris, const int *tri);
+
+/* Nodal areas A_b [n] and unit normals [n][3] of the current mesh (either
+ * pointer may be NULL). */
+ggem_status ggem_mesh_geometry(ggem_plan_t *plan, double *area, double *normal);
+
+/*
+ * Velocity and stress at n_tgt targets due to n_src point forces g [n][3] at
+ * x_src (Sec. 3.2, Eqs. (u_g), (tot_l_g)):
+ *   u_i(x)      = 1/(8 pi mu) sum_nu G_ij(x, x_nu) g_nu_j
+ *   sigma_ik(x) = 1/(8 pi)    sum_nu T_ijk(x, x_nu) g_nu_j
+ * with G, T the slit Green's function and its stress.  tgt_is_src != 0 means
+ * the targets are the sources themselves (x_tgt ignored, n_tgt = n_src): the
+ * self pair is left out of the local sum and the free-space global self
+ * velocity (4 alpha/sqrt(pi)) g/(8 pi mu) is removed, so u is the regular
+ * part of the slit solution at each source.  u [n_tgt][3] and sigma
+ * [n_tgt][6] may each be NULL.  Sources and targets must lie strictly
+ * inside the slit.
+ */
+ggem_status ggem_point_forces(ggem_plan_t *plan, int n_src, const double *x_src,
+                              const double *g, int n_tgt, const double *x_tgt,
+                              int tgt_is_src, double *u, double *sigma);
+
+/*
+ * Single-layer integral at the mesh nodes (Sec. 3.4, Eq. (sl_t)):
+ *   w_j(z) = int_S q_i(x) G_ji(z, x) dS(x),   q, w: [n_nodes][3].
+ * Local part by the plan's quadrature, global part from the trapezoidal
+ * nodal strengths A_b q_b spread with rho_g (Eq. (rhog_sum)).
+ */
+ggem_status ggem_single_layer(ggem_plan_t *plan, const double *q, double *w);
+
+/*
+ * Double-layer integral at the mesh nodes (Sec. 3.5, Eq. (wdbl)):
+ *   v_j(z) = n_k(z) int_S q_i(x) T_jik(z, x) dS(x),   q, v: [n_nodes][3].
+ * Element quadrature uses the n-tilde form of Eqs. (dbl_l1), (ntilde) on
+ * triangles that have z as a vertex.
+ */
+ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
+
+/*
+ * Tracing (no counterpart in the paper).  With tracing enabled, each stage
+ * of an evaluation is bracketed by CUDA events on the plan's stream and the
+ * host waits for its end, so per-stage device times can be read back; this
+ * serialises the host with the device and is meant for measurement only.
+ * ggem_trace_enable also resets the counters and the launch count.
+ */
+ggem_status ggem_trace_enable(ggem_plan_t *plan, int on);
+int ggem_trace_stage_count(void);
+const char *ggem_trace_stage_name(int stage);
+ggem_status ggem_trace_read(const ggem_plan_t *plan, int stage, double *total_ms,
+                            long *calls);
+/* Number of library kernels launched by this plan since creation or the
+ * last ggem_trace_enable. */
+ggem_status ggem_launch_count(const ggem_plan_t *plan, long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GGEM_H */

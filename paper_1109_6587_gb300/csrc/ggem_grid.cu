@@ -1,0 +1,449 @@
+// Grid-side kernels of the GGEM global problem (paper Sec. 3.2.2, 3.4.2, App. C):
+//   spreading of the global density rho_g onto the Fourier x Chebyshev grid,
+//   FFTs in x (real) and z (complex), the Chebyshev transforms in y as a dense
+//   contraction, and 5x5x5 Lagrange interpolation back to the targets.
+//
+// Grid layout: physical [Ny][comp][Nz][Nx] (real T); after the x transform
+// each row of Nx reals holds Nx/2 complex modes k_x = 0..Nx/2-1 in place (the
+// Nyquist mode is dropped, i.e. set to zero); spectral [Ny][comp][Nz][Nx/2].
+#include "ggem_internal.cuh"
+
+namespace ggem {
+
+template <typename T> __device__ __forceinline__ T d_exp2(T x);
+template <> __device__ __forceinline__ float d_exp2<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double d_exp2<double>(double x) { return exp(x); }
+
+// ---------------------------------------------------------------- spread
+// f(node) = - sum_s g_s rho_g(node - x_s*), |node - x_s*| < r_cut (Eq. stokes_gg).
+// One warp per source; lanes walk the source's bounding box of grid nodes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread(GridGeom geo, const double* __restrict__ yj,
+                                                 int n, const double* __restrict__ x,
+                                                 const v4_t<T>* __restrict__ g,
+                                                 const int* __restrict__ perm,
+                                                 T* __restrict__ grid) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    int src = perm[warp];
+    double xs = x[3 * src], ys = x[3 * src + 1], zs = x[3 * src + 2];
+    v4_t<T> gs = g[warp];
+    const double rc = geo.rcut;
+    int ilo = (int)floor((xs - rc) / geo.dx), ihi = (int)ceil((xs + rc) / geo.dx);
+    int klo = (int)floor((zs - rc) / geo.dz), khi = (int)ceil((zs + rc) / geo.dz);
+    const int N = geo.Ny - 1;
+    const double pi = 3.14159265358979323846;
+    double yb = 2.0 * (ys - geo.y0) / geo.W - 1.0;
+    double yhi = fmin(1.0, yb + 2.0 * rc / geo.W), ylo = fmax(-1.0, yb - 2.0 * rc / geo.W);
+    int jlo = max(0, (int)floor(acos(yhi) * N / pi) - 1);
+    int jhi = min(N, (int)ceil(acos(ylo) * N / pi) + 1);
+    int nx = ihi - ilo + 1, nz = khi - klo + 1, ny = jhi - jlo + 1;
+    const T d0x = (T)(ilo * geo.dx - xs), d0z = (T)(klo * geo.dz - zs);
+    const T hx = (T)geo.dx, hz = (T)geo.dz;
+    const T al2 = (T)(geo.alpha * geo.alpha);
+    const T rc2 = (T)(rc * rc);
+    const T cn = (T)(geo.alpha * geo.alpha * geo.alpha / (pi * sqrt(pi)));
+    const size_t plane = (size_t)geo.Nz * geo.Nx;
+    int total = nx * nz * ny;
+    for (int idx = lane; idx < total; idx += 32) {
+        int i = idx % nx;
+        int rest = idx / nx;
+        int k = rest % nz;
+        int j = jlo + rest / nz;
+        T dxv = d0x + (T)i * hx, dzv = d0z + (T)k * hz;
+        T dyv = (T)(yj[j] - ys);
+        T r2 = dxv * dxv + dyv * dyv + dzv * dzv;
+        if (!(r2 < rc2)) continue;
+        T a2r2 = al2 * r2;
+        T rho = cn * d_exp2<T>(-a2r2) * ((T)2.5 - a2r2);
+        int ii = (ilo + i) % geo.Nx; ii += (ii < 0) ? geo.Nx : 0;
+        int kk = (klo + k) % geo.Nz; kk += (kk < 0) ? geo.Nz : 0;
+        T* p = grid + (size_t)j * 3 * plane + (size_t)kk * geo.Nx + ii;
+        atomicAdd(p, -gs.x * rho);
+        atomicAdd(p + plane, -gs.y * rho);
+        atomicAdd(p + 2 * plane, -gs.z * rho);
+    }
+}
+
+template <typename T>
+cudaError_t spread(const GridGeom& geo, const double* yj, int n, const double* x,
+                   const v4_t<T>* g_sorted, const int* perm, T* grid, cudaStream_t st) {
+    cudaMemsetAsync(grid, 0, (size_t)geo.Ny * 3 * geo.Nz * geo.Nx * sizeof(T), st);
+    if (n > 0) {
+        long threads = (long)n * 32;
+        k_spread<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(geo, yj, n, x, g_sorted,
+                                                                        perm, grid);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FFT
+template <typename T> struct Cx {
+    using C = c2_t<T>;
+    static __device__ __forceinline__ C mk(T a, T b) { C c; c.x = a; c.y = b; return c; }
+    static __device__ __forceinline__ C add(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    }
+    static __device__ __forceinline__ C conj(C a) { return mk(a.x, -a.y); }
+};
+
+// In-place radix-2 DIT butterflies on R transforms of length M stored
+// contiguously in shared memory, input already in bit-reversed order.
+// tw[k] = exp(-2 pi i k / M), k < M/2; inv selects the conjugate twiddles.
+template <typename T>
+__device__ void smem_fft(c2_t<T>* s, int R, int M, int logM, const c2_t<T>* __restrict__ tw,
+                         bool inv) {
+    using X = Cx<T>;
+    int half = M >> 1;
+    for (int lh = 0; lh < logM; ++lh) {
+        int h = 1 << lh;
+        __syncthreads();
+        for (int b = threadIdx.x; b < R * half; b += blockDim.x) {
+            int r = b >> (logM - 1);
+            int jj = b & (half - 1);
+            int pos = jj & (h - 1);
+            int grp = jj >> lh;
+            int i0 = r * M + (grp << (lh + 1)) + pos;
+            int i1 = i0 + h;
+            c2_t<T> w = tw[pos << (logM - 1 - lh)];
+            if (inv) w.y = -w.y;
+            c2_t<T> a = s[i0];
+            c2_t<T> bb = X::mul(s[i1], w);
+            s[i0] = X::add(a, bb);
+            s[i1] = X::sub(a, bb);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int bitrev(int v, int logM) {
+    return (int)(__brev((unsigned)v) >> (32 - logM));
+}
+
+// Real-to-complex along x for R rows per block: the row of Nx reals is read as
+// M = Nx/2 complex values z_n = x_2n + i x_2n+1, transformed with length M, then
+// X_k = E_k + exp(-2 pi i k/Nx) O_k with E, O the even/odd-sample spectra.
+// Output X_k, k = 0..M-1, in place.
+template <typename T>
+__global__ void k_fft_x_r2c(c2_t<T>* data, long nrows, int M, int logM,
+                            const c2_t<T>* __restrict__ tw, const c2_t<T>* __restrict__ tpost,
+                            int R) {
+    using X = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c2_t<T>* s = reinterpret_cast<c2_t<T>*>(smraw);
+    long row0 = (long)blockIdx.x * R;
+    int rr = (int)min((long)R, nrows - row0);
+    for (int e = threadIdx.x; e < rr * M; e += blockDim.x) {
+        int r = e / M, n = e - r * M;
+        s[r * M + bitrev(n, logM)] = data[(row0 + r) * M + n];
+    }
+    for (int e = threadIdx.x; e < (R - rr) * M; e += blockDim.x) s[rr * M + e] = X::mk(0, 0);
+    smem_fft<T>(s, R, M, logM, tw, false);
+    for (int e = threadIdx.x; e < rr * M; e += blockDim.x) {
+        int r = e / M, k = e - r * M;
+        c2_t<T> Zk = s[r * M + k];
+        c2_t<T> Zc = X::conj(s[r * M + ((M - k) & (M - 1))]);
+        c2_t<T> E = X::mk((T)0.5 * (Zk.x + Zc.x), (T)0.5 * (Zk.y + Zc.y));
+        // O = (Zk - Zc) / (2i)
+        c2_t<T> O = X::mk((T)0.5 * (Zk.y - Zc.y), -(T)0.5 * (Zk.x - Zc.x));
+        data[(row0 + r) * M + k] = X::add(E, X::mul(tpost[k], O));
+    }
+}
+
+// Complex-to-real along x, the inverse of the above with the Hermitian
+// extension X_{Nx-k} = conj(X_k), the Nyquist mode zero and Im X_0 ignored:
+// x_n = Re X_0 + 2 sum_{k=1}^{Nx/2-1} Re(X_k exp(2 pi i k n/Nx)).
+template <typename T>
+__global__ void k_fft_x_c2r(c2_t<T>* data, long nrows, int M, int logM,
+                            const c2_t<T>* __restrict__ tw, const c2_t<T>* __restrict__ tpost,
+                            int R) {
+    using X = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c2_t<T>* s = reinterpret_cast<c2_t<T>*>(smraw);
+    long row0 = (long)blockIdx.x * R;
+    int rr = (int)min((long)R, nrows - row0);
+    for (int e = threadIdx.x; e < rr * M; e += blockDim.x) {
+        int r = e / M, k = e - r * M;
+        const c2_t<T>* row = data + (row0 + r) * M;
+        c2_t<T> Z;
+        if (k == 0) {
+            T x0 = row[0].x;
+            Z = X::mk(x0, x0);            // E' = O' = Re X_0 (Nyquist is zero)
+        } else {
+            c2_t<T> Xk = row[k];
+            c2_t<T> Xc = X::conj(row[M - k]);
+            c2_t<T> Ep = X::add(Xk, Xc);
+            c2_t<T> Op = X::mul(X::sub(Xk, Xc), X::conj(tpost[k]));
+            Z = X::mk(Ep.x - Op.y, Ep.y + Op.x);   // E' + i O'
+        }
+        s[r * M + bitrev(k, logM)] = Z;
+    }
+    for (int e = threadIdx.x; e < (R - rr) * M; e += blockDim.x) s[rr * M + e] = X::mk(0, 0);
+    smem_fft<T>(s, R, M, logM, tw, true);
+    for (int e = threadIdx.x; e < rr * M; e += blockDim.x) {
+        int r = e / M, n = e - r * M;
+        data[(row0 + r) * M + n] = s[r * M + n];
+    }
+}
+
+// Complex transform along z: planes of [Nz][nkx] complex, TB columns per block.
+template <typename T>
+__global__ void k_fft_z(c2_t<T>* data, int nkx, int Nz, int logNz,
+                        const c2_t<T>* __restrict__ tw, int TB, bool inv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    c2_t<T>* s = reinterpret_cast<c2_t<T>*>(smraw);
+    int ncb = (nkx + TB - 1) / TB;
+    long plane = blockIdx.x / ncb;
+    int col0 = (blockIdx.x - plane * ncb) * TB;
+    int tb = min(TB, nkx - col0);
+    c2_t<T>* base = data + plane * (long)Nz * nkx + col0;
+    for (int e = threadIdx.x; e < Nz * TB; e += blockDim.x) {
+        int z = e / TB, c = e - z * TB;
+        c2_t<T> v = Cx<T>::mk(0, 0);
+        if (c < tb) v = base[(long)z * nkx + c];
+        s[c * Nz + bitrev(z, logNz)] = v;
+    }
+    smem_fft<T>(s, TB, Nz, logNz, tw, inv);
+    for (int e = threadIdx.x; e < Nz * TB; e += blockDim.x) {
+        int z = e / TB, c = e - z * TB;
+        if (c < tb) base[(long)z * nkx + c] = s[c * Nz + z];
+    }
+}
+
+static int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+template <typename T>
+static cudaError_t fft_x(const GridGeom& geo, T* data, int nplanes, const void* tw_x, bool inv,
+                         cudaStream_t st) {
+    int M = geo.Nx / 2, logM = ilog2(M);
+    long nrows = (long)nplanes * geo.Nz;
+    int R = max(1, 2048 / M);
+    size_t smem = (size_t)R * M * sizeof(c2_t<T>);
+    const c2_t<T>* tw = (const c2_t<T>*)tw_x;
+    const c2_t<T>* tpost = tw + M / 2;
+    unsigned nb = (unsigned)((nrows + R - 1) / R);
+    if (inv) {
+        cudaFuncSetAttribute(k_fft_x_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_fft_x_c2r<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nrows, M, logM, tw, tpost, R);
+    } else {
+        cudaFuncSetAttribute(k_fft_x_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_fft_x_r2c<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nrows, M, logM, tw, tpost, R);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t fft_z(const GridGeom& geo, T* data, int nplanes, const void* tw_z, bool inv,
+                         cudaStream_t st) {
+    int Nz = geo.Nz, logNz = ilog2(Nz), nkx = geo.Nx / 2;
+    int TB = min(nkx, 8);
+    size_t smem = (size_t)TB * Nz * sizeof(c2_t<T>);
+    unsigned nb = (unsigned)((long)nplanes * ((nkx + TB - 1) / TB));
+    cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_z<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nkx, Nz, logNz, (const c2_t<T>*)tw_z, TB,
+                                      inv);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
+                        const void* tw_z, cudaStream_t st) {
+    cudaError_t e = fft_x<T>(geo, data, nplanes, tw_x, false, st);
+    if (e != cudaSuccess) return e;
+    return fft_z<T>(geo, data, nplanes, tw_z, false, st);
+}
+
+template <typename T>
+cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
+                        const void* tw_z, cudaStream_t st) {
+    cudaError_t e = fft_z<T>(geo, data, nplanes, tw_z, true, st);
+    if (e != cudaSuccess) return e;
+    return fft_x<T>(geo, data, nplanes, tw_x, true, st);
+}
+
+// -------------------------------------------------- Chebyshev contraction
+// out[n][col] = sum_j M[n][j] in[j][col]  (M: Ny x Ny in shared memory)
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_cheb(int Ny, const T* __restrict__ M,
+                                               const T* __restrict__ in, T* __restrict__ out,
+                                               long cols) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Ms = reinterpret_cast<T*>(smraw);
+    for (int e = threadIdx.x; e < Ny * Ny; e += blockDim.x) Ms[e] = M[e];
+    __syncthreads();
+    long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= cols) return;
+    for (int n0 = 0; n0 < Ny; n0 += NB) {
+        T acc[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] = 0;
+        for (int j = 0; j < Ny; ++j) {
+            T v = in[(long)j * cols + col];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                int n = n0 + b;
+                if (n < Ny) acc[b] += Ms[n * Ny + j] * v;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (n0 + b < Ny) out[(long)(n0 + b) * cols + col] = acc[b];
+    }
+}
+
+template <typename T>
+cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st) {
+    size_t smem = (size_t)Ny * Ny * sizeof(T);
+    cudaFuncSetAttribute(k_cheb<T, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cheb<T, 24><<<(unsigned)((cols + 255) / 256), 256, smem, st>>>(Ny, M, in, out, cols);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- interpolation
+// Degree-4 Lagrange weights at offset t for nodes -2..2.
+template <typename T> __device__ __forceinline__ void lag5_uniform(T t, T w[5]) {
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+        T v = 1;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            if (q != p) v *= (t - (T)(q - 2)) / (T)(p - q);
+        w[p] = v;
+    }
+}
+
+template <typename T> struct InterpArgs {
+    GridGeom geo;
+    const double* yj;
+    const T* grid;
+    int ncomp_total, comp0, mode;
+    int n;
+    const double* x;
+    const T* local;
+    int local_stride;
+    const double* nrm;
+    const double* qself;
+    const double* wself;
+    double self_coef;
+    double* out;
+    int out_stride;
+};
+
+// mode 0: velocity (3 comps): out = local + interp - self
+// mode 1: stress (6 comps):   out = local + interp
+// mode 2: double layer:       out_j = local_j + n_k sigma_jk / mu
+template <typename T>
+__global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n) return;
+    const GridGeom& geo = a.geo;
+    double xt = a.x[3 * t], yt = a.x[3 * t + 1], zt = a.x[3 * t + 2];
+    double ux = xt / geo.dx, uz = zt / geo.dz;
+    double i0 = rint(ux), k0 = rint(uz);
+    T wx[5], wz[5], wy[5];
+    lag5_uniform<T>((T)(ux - i0), wx);
+    lag5_uniform<T>((T)(uz - k0), wz);
+    int N = geo.Ny - 1;
+    double yb = fmin(1.0, fmax(-1.0, 2.0 * (yt - geo.y0) / geo.W - 1.0));
+    const double pi = 3.14159265358979323846;
+    int jc = (int)rint(acos(yb) * N / pi);
+    jc = min(max(jc, 0), N);
+    int jbest = jc;
+    double dbest = fabs(yt - a.yj[jc]);
+    if (jc > 0) {
+        double d = fabs(yt - a.yj[jc - 1]);
+        if (d <= dbest) { dbest = d; jbest = jc - 1; }
+    }
+    if (jc < N) {
+        double d = fabs(yt - a.yj[jc + 1]);
+        if (d < dbest) { dbest = d; jbest = jc + 1; }
+    }
+    int js = min(max(jbest - 2, 0), geo.Ny - 5);
+    double yn[5];
+#pragma unroll
+    for (int p = 0; p < 5; ++p) yn[p] = a.yj[js + p];
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+        T v = 1;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            if (q != p) v *= (T)(yt - yn[q]) / (T)(yn[p] - yn[q]);
+        wy[p] = v;
+    }
+    int ib = (int)(((long)i0 - 2) % geo.Nx); ib += (ib < 0) ? geo.Nx : 0;
+    int kb = (int)(((long)k0 - 2) % geo.Nz); kb += (kb < 0) ? geo.Nz : 0;
+    const int nc = (a.mode == 0) ? 3 : 6;
+    T acc[6] = {0, 0, 0, 0, 0, 0};
+    const size_t plane = (size_t)geo.Nz * geo.Nx;
+    for (int p = 0; p < 5; ++p) {
+        const T* gy = a.grid + ((size_t)(js + p) * a.ncomp_total + a.comp0) * plane;
+        for (int q = 0; q < 5; ++q) {
+            int kk = kb + q; kk -= (kk >= geo.Nz) ? geo.Nz : 0;
+            T wyz = wy[p] * wz[q];
+            const T* gz = gy + (size_t)kk * geo.Nx;
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                int ii = ib + r; ii -= (ii >= geo.Nx) ? geo.Nx : 0;
+                T w = wyz * wx[r];
+                for (int c = 0; c < nc; ++c) acc[c] += w * gz[c * plane + ii];
+            }
+        }
+    }
+    double* o = a.out + (size_t)t * a.out_stride;
+    const T* lo = a.local ? a.local + (size_t)t * a.local_stride : nullptr;
+    if (a.mode == 0) {
+        for (int c = 0; c < 3; ++c) {
+            double v = (double)acc[c] + (lo ? (double)lo[c] : 0.0);
+            if (a.qself) v -= a.self_coef * (a.wself ? a.wself[t] : 1.0) * a.qself[3 * t + c];
+            o[c] = v;
+        }
+    } else if (a.mode == 1) {
+        for (int c = 0; c < 6; ++c) o[c] = (double)acc[c] + (lo ? (double)lo[c] : 0.0);
+    } else {
+        double n0 = a.nrm[3 * t], n1 = a.nrm[3 * t + 1], n2 = a.nrm[3 * t + 2];
+        double s[6];
+        for (int c = 0; c < 6; ++c) s[c] = (double)acc[c];
+        double v0 = n0 * s[0] + n1 * s[1] + n2 * s[2];
+        double v1 = n0 * s[1] + n1 * s[3] + n2 * s[4];
+        double v2 = n0 * s[2] + n1 * s[4] + n2 * s[5];
+        double im = 1.0 / geo.mu;
+        o[0] = v0 * im + (lo ? (double)lo[0] : 0.0);
+        o[1] = v1 * im + (lo ? (double)lo[1] : 0.0);
+        o[2] = v2 * im + (lo ? (double)lo[2] : 0.0);
+    }
+}
+
+template <typename T>
+cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid, int ncomp_total,
+                           int comp0, int n_tgt, const double* x_tgt, const T* local,
+                           int local_stride, const double* nrm, const double* qself,
+                           const double* wself, double self_coef, int mode, double* out,
+                           int out_stride, cudaStream_t st) {
+    if (n_tgt <= 0) return cudaSuccess;
+    InterpArgs<T> a{geo, yj, grid, ncomp_total, comp0, mode, n_tgt, x_tgt, local,
+                    local_stride, nrm, qself, wself, self_coef, out, out_stride};
+    k_interp<T><<<(n_tgt + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define GGEM_INST_GRID(T)                                                                     \
+    template cudaError_t spread<T>(const GridGeom&, const double*, int, const double*,         \
+                                   const v4_t<T>*, const int*, T*, cudaStream_t);              \
+    template cudaError_t fft_forward<T>(const GridGeom&, T*, int, const void*, const void*,    \
+                                        cudaStream_t);                                         \
+    template cudaError_t fft_inverse<T>(const GridGeom&, T*, int, const void*, const void*,    \
+                                        cudaStream_t);                                         \
+    template cudaError_t cheb_apply<T>(int, const T*, const T*, T*, long, cudaStream_t);       \
+    template cudaError_t interp_combine<T>(const GridGeom&, const double*, const T*, int, int, \
+                                           int, const double*, const T*, int, const double*,   \
+                                           const double*, const double*, double, int, double*, \
+                                           int, cudaStream_t);
+GGEM_INST_GRID(float)
+GGEM_INST_GRID(double)
+
+}  // namespace ggem

@@ -1,0 +1,173 @@
+// Internal declarations of libggem: plan layout, kernel launchers.
+// Paper: Kumar & Graham, arXiv 1109.6587 (GGEM in a planar slit).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "ggem.h"
+
+namespace ggem {
+
+// ------------------------------------------------------------ small types
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4_32a; };
+template <typename T> using v4_t = typename V4<T>::type;
+
+template <typename T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+template <typename T> using c2_t = typename C2<T>::type;
+
+// Cell list over [0,Lx) x [y0,y0+W] x [0,Lz): cells no smaller than r_cut.
+struct CellGrid {
+    int ncx, ncy, ncz;
+    double hx, hy, hz;
+    double y0;
+};
+
+// Geometry and GGEM constants handed to kernels by value.
+struct GridGeom {
+    double Lx, Lz, W, y0;
+    int Nx, Ny, Nz, nkx;       // nkx = Nx/2 kept Fourier modes in x
+    double dx, dz;
+    double alpha, rcut, mu;
+};
+
+// Point sources sorted by cell: offsets from the cell corner (T precision),
+// strengths, permutation sorted -> caller index.
+template <typename T> struct SortedSources {
+    v4_t<T>* pos;    // (ox, oy, oz, 0)
+    v4_t<T>* g;      // (gx, gy, gz, 0)
+    int* cell;       // cell index of each sorted source
+    int* perm;       // caller index of each sorted source
+    int* cell_start; // [ncell + 1]
+    int n;
+};
+
+}  // namespace ggem
+
+// ----------------------------------------------------------------- the plan
+struct ggem_plan {
+    ggem_params prm;
+    cudaStream_t st = nullptr;
+    ggem::GridGeom geo;
+    ggem::CellGrid cg;
+    int ncell = 0;
+    int nmodes = 0;           // Nz * nkx
+    bool fp64 = true;
+    std::string err;
+
+    // tables
+    double* d_yj = nullptr;            // [Ny] Chebyshev nodes (physical y)
+    void* d_cheb_fwd = nullptr;        // [Ny][Ny] T, scaled by 1/(Nx Nz)
+    void* d_cheb_inv = nullptr;        // [Ny][Ny] T
+    void* d_tw_x = nullptr;            // complex T: [Nx/4] FFT-length-Nx/2 twiddles + [Nx/2] post twiddles
+    void* d_tw_z = nullptr;            // complex T: [Nz/2]
+    double* d_ksb = nullptr;           // [3][Ny][nmodes] p_b, phi_b, v_b coefficients
+    double* d_minv = nullptr;          // [4][nmodes] inverse influence matrix
+
+    // workspaces
+    void* d_gridA = nullptr;           // max(9,3)*Ny*Nz*Nx T
+    void* d_gridB = nullptr;
+    void* d_wall = nullptr;            // [2][3][Nz][Nx] T
+    double* d_ksw = nullptr;           // K8 scratch: [6][Ny][nmodes] complex double
+    size_t grid_elems = 0;
+
+    // point sources (sorted)
+    int cap = 0;
+    int* d_cell_count = nullptr;       // [ncell]
+    int* d_cell_start = nullptr;       // [ncell+1]
+    int* d_cursor = nullptr;           // [ncell]
+    int* d_src_cell = nullptr;         // [cap]
+    int* d_perm = nullptr;             // [cap]
+    void* d_spos = nullptr;            // [cap] v4 T
+    void* d_sg = nullptr;              // [cap] v4 T
+    double* d_src_x = nullptr;         // [cap][3] caller-order positions (double)
+    void* d_local = nullptr;           // [cap][9] T local-sum output
+
+    // staging for host pointers
+    double* d_in0 = nullptr;           // [cap][3]
+    double* d_in1 = nullptr;           // [cap][3]
+    double* d_in2 = nullptr;           // [cap][3]
+    double* d_out0 = nullptr;          // [cap][3]
+    double* d_out1 = nullptr;          // [cap][6]
+
+    // mesh
+    int n_nodes = 0, n_tris = 0, cap_tris = 0;
+    bool mesh_ready = false;
+    double* d_x = nullptr;             // [cap][3]
+    int* d_tri = nullptr;              // [cap_tris][3]
+    double* d_area = nullptr;          // [cap] nodal areas
+    double* d_nrm = nullptr;           // [cap][3] node normals
+    double* d_tri_area = nullptr;      // [cap_tris]
+    double* d_tri_nrm = nullptr;       // [cap_tris][3]
+    int* d_mesh_cell = nullptr;        // mesh nodes sorted: cell / perm / offsets
+    int* d_mesh_perm = nullptr;
+    int* d_mesh_start = nullptr;
+    void* d_mesh_pos = nullptr;
+
+    // tracing: per-stage device time (CUDA events on the plan's stream)
+    bool prof = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double prof_ms[16] = {0};
+    long prof_calls[16] = {0};
+    long launches = 0;                 // kernels launched by this plan
+};
+
+namespace ggem {
+
+// ------------------------------------------------------------ launchers
+// cell list: sort n sources (caller-order double positions x[n][3]) into cells
+template <typename T>
+cudaError_t build_cells(const GridGeom& geo, const CellGrid& cg, int n, const double* x,
+                        int* cell_count, int* cell_start, int* cursor, int* src_cell,
+                        int* perm, v4_t<T>* pos, cudaStream_t st);
+
+// gather caller-order strengths (scale * w[i] * q[i], w may be NULL) into sorted order
+template <typename T>
+cudaError_t gather_strengths(int n, const int* perm, const double* q, const double* w,
+                             double scale, v4_t<T>* g, cudaStream_t st);
+
+// local sum targets
+enum TargetKind { TK_SORTED = 0, TK_POINTS = 1, TK_WALL = 2 };
+// out modes
+enum { OUT_U = 1, OUT_S = 2, OUT_DBL = 4 };
+
+template <typename T>
+cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
+                      int kind, int n_tgt, const double* x_tgt, const double* nrm_tgt,
+                      int out_mode, T* out, int out_stride, cudaStream_t st);
+
+template <typename T>
+cudaError_t spread(const GridGeom& geo, const double* yj, int n, const double* x,
+                   const v4_t<T>* g_sorted, const int* perm, T* grid, cudaStream_t st);
+
+template <typename T>
+cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
+                        const void* tw_z, cudaStream_t st);
+template <typename T>
+cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
+                        const void* tw_z, cudaStream_t st);
+
+template <typename T>
+cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st);
+
+template <typename T>
+cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
+                     const double* minv, double* scratch, int out_sel, T* ocoef,
+                     cudaStream_t st);
+
+// mode 0: velocity, out = local + interp - self_coef * wself * qself
+// mode 1: stress (6), out = local + interp
+// mode 2: double layer, out_j = local_j + n_k sigma_jk / mu
+template <typename T>
+cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid, int ncomp_total,
+                           int comp0, int n_tgt, const double* x_tgt, const T* local,
+                           int local_stride, const double* nrm, const double* qself,
+                           const double* wself, double self_coef, int mode, double* out,
+                           int out_stride, cudaStream_t st);
+
+}  // namespace ggem

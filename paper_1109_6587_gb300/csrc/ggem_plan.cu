@@ -1,0 +1,665 @@
+// libggem plan, mesh and C-ABI entry points (include/ggem.h).
+// Paper: Kumar & Graham, arXiv 1109.6587.  The data flow of one evaluation
+// follows Sec. 3.2 / 3.4 / 3.5:
+//   local sum (cell list) -> wall data u^g = -u^l -> spread rho_g -> FFT x,z
+//   -> Chebyshev transform -> per-mode Kleiser-Schumann tau solve (FP64)
+//   -> inverse transforms -> 5-point Lagrange interpolation + local part.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ggem_internal.cuh"
+
+using namespace ggem;
+
+namespace ggem {
+void ks_precompute_mode(int Ny, double W, double mu, double k2, double* pb, double* phib,
+                        double* vb, double* minv);
+}
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct Fail {
+    ggem_status s;
+};
+
+#define GG_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            P->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            throw Fail{GGEM_ERR_CUDA};                                                    \
+        }                                                                                 \
+    } while (0)
+
+#define GG_CHECK(cond, code, msg)                                                         \
+    do {                                                                                  \
+        if (!(cond)) {                                                                    \
+            P->err = (msg);                                                               \
+            throw Fail{code};                                                             \
+        }                                                                                 \
+    } while (0)
+
+template <typename F>
+ggem_status guarded(ggem_plan_t* P, F&& f) {
+    try {
+        f();
+        return GGEM_OK;
+    } catch (const Fail& e) {
+        return e.s;
+    } catch (const std::bad_alloc&) {
+        if (P) P->err = "host allocation failed";
+        return GGEM_ERR_CAPACITY;
+    } catch (...) {
+        if (P) P->err = "unexpected host exception";
+        return GGEM_ERR_CUDA;
+    }
+}
+
+// message of the last failed ggem_plan call on this thread
+thread_local std::string g_create_error = "no plan";
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename X>
+void dalloc(ggem_plan_t* P, X** p, size_t n) {
+    GG_CUDA(cudaMalloc((void**)p, n * sizeof(X) + 16));
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// Input staging: device pointers pass through; host pointers are copied into
+// the plan buffer `stage` (n doubles).
+const double* stage_in(ggem_plan_t* P, const double* p, double* stage, size_t n) {
+    if (!p) return nullptr;
+    if (is_device_ptr(p)) return p;
+    GG_CUDA(cudaMemcpyAsync(stage, p, n * sizeof(double), cudaMemcpyHostToDevice, P->st));
+    return stage;
+}
+
+struct OutMap {
+    double* user = nullptr;
+    double* dev = nullptr;
+    size_t n = 0;
+    bool host = false;
+};
+
+OutMap stage_out(double* user, double* stage, size_t n) {
+    OutMap m;
+    m.user = user;
+    m.n = n;
+    if (!user) return m;
+    m.host = !is_device_ptr(user);
+    m.dev = m.host ? stage : user;
+    return m;
+}
+
+void finish_out(ggem_plan_t* P, const OutMap& m) {
+    if (m.user && m.host)
+        GG_CUDA(cudaMemcpyAsync(m.user, m.dev, m.n * sizeof(double), cudaMemcpyDeviceToHost,
+                                P->st));
+}
+
+// ------------------------------------------------------------- geometry
+__global__ void k_tri_geom(int m, const double* __restrict__ x, const int* __restrict__ tri,
+                           double* __restrict__ ta, double* __restrict__ tn,
+                           double* __restrict__ area, double* __restrict__ nsum) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    int i1 = tri[3 * k], i2 = tri[3 * k + 1], i3 = tri[3 * k + 2];
+    double e2[3], e3[3], c[3];
+    for (int d = 0; d < 3; ++d) {
+        e2[d] = x[3 * i2 + d] - x[3 * i1 + d];
+        e3[d] = x[3 * i3 + d] - x[3 * i1 + d];
+    }
+    c[0] = e2[1] * e3[2] - e2[2] * e3[1];
+    c[1] = e2[2] * e3[0] - e2[0] * e3[2];
+    c[2] = e2[0] * e3[1] - e2[1] * e3[0];
+    double a2 = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    double A = 0.5 * a2;
+    ta[k] = A;
+    for (int d = 0; d < 3; ++d) tn[3 * k + d] = c[d] / a2;
+    int v[3] = {i1, i2, i3};
+    for (int p = 0; p < 3; ++p) {
+        atomicAdd(&area[v[p]], A / 3.0);
+        for (int d = 0; d < 3; ++d) atomicAdd(&nsum[3 * v[p] + d], 0.5 * c[d]);
+    }
+}
+
+__global__ void k_normalize(int n, double* __restrict__ nrm) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = nrm[3 * i], b = nrm[3 * i + 1], c = nrm[3 * i + 2];
+    double s = 1.0 / sqrt(a * a + b * b + c * c);
+    nrm[3 * i] = a * s; nrm[3 * i + 1] = b * s; nrm[3 * i + 2] = c * s;
+}
+
+__global__ void k_check_inside(int n, const double* __restrict__ x, double y0, double W,
+                               int* __restrict__ bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y = x[3 * i + 1];
+    bool ok = (y > y0) && (y < y0 + W) && isfinite(x[3 * i]) && isfinite(x[3 * i + 2]);
+    if (!ok) atomicAdd(bad, 1);
+}
+
+// ------------------------------------------------------------- tracing
+enum Stage {
+    ST_CELLS, ST_GATHER, ST_LOCAL, ST_WALL, ST_SPREAD, ST_FFT_FWD, ST_CHEB_FWD, ST_KS,
+    ST_CHEB_INV, ST_FFT_INV, ST_INTERP, ST_ELEM, ST_COUNT
+};
+const char* kStageNames[ST_COUNT] = {"cell_list", "gather", "local_sum", "wall_local_sum",
+                                     "spread", "fft_forward", "cheb_forward", "tau_solve",
+                                     "cheb_inverse", "fft_inverse", "interpolate",
+                                     "element_correction"};
+
+// Run one stage (nk kernel launches); with tracing on, time it with events.
+template <typename F>
+void stage(ggem_plan_t* P, int id, int nk, F&& f) {
+    if (P->prof) GG_CUDA(cudaEventRecord(P->ev0, P->st));
+    f();
+    P->launches += nk;
+    if (P->prof) {
+        GG_CUDA(cudaEventRecord(P->ev1, P->st));
+        GG_CUDA(cudaEventSynchronize(P->ev1));
+        float ms = 0.f;
+        GG_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+        P->prof_ms[id] += ms;
+        P->prof_calls[id] += 1;
+    }
+}
+
+// ------------------------------------------------------------ pipeline
+template <typename T>
+SortedSources<T> sources_of(ggem_plan_t* P, bool mesh) {
+    SortedSources<T> s;
+    s.pos = (v4_t<T>*)(mesh ? P->d_mesh_pos : P->d_spos);
+    s.g = (v4_t<T>*)P->d_sg;
+    s.cell = mesh ? P->d_mesh_cell : P->d_src_cell;
+    s.perm = mesh ? P->d_mesh_perm : P->d_perm;
+    s.cell_start = mesh ? P->d_mesh_start : P->d_cell_start;
+    s.n = 0;
+    return s;
+}
+
+int nout_of(int sel) { return ((sel & 1) ? 3 : 0) + ((sel & 2) ? 6 : 0); }
+
+// Global part: wall data, spread, transforms, tau solves, inverse transforms.
+// The physical result is left in gridB as [Ny][nout][Nz][Nx].
+template <typename T>
+void run_global(ggem_plan_t* P, const SortedSources<T>& src, int n_src, const double* x_src,
+                int out_sel) {
+    const GridGeom& geo = P->geo;
+    cudaStream_t st = P->st;
+    T* A = (T*)P->d_gridA;
+    T* B = (T*)P->d_gridB;
+    T* Wl = (T*)P->d_wall;
+    stage(P, ST_WALL, 1, [&] {
+        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_WALL, 2 * geo.Nz * geo.Nx, nullptr, nullptr,
+                             OUT_U, Wl, 0, st));
+    });
+    stage(P, ST_SPREAD, 1, [&] {
+        GG_CUDA(spread<T>(geo, P->d_yj, n_src, x_src, src.g, src.perm, A, st));
+    });
+    stage(P, ST_FFT_FWD, 4, [&] {
+        GG_CUDA(fft_forward<T>(geo, A, geo.Ny * 3, P->d_tw_x, P->d_tw_z, st));
+        GG_CUDA(fft_forward<T>(geo, Wl, 6, P->d_tw_x, P->d_tw_z, st));
+    });
+    stage(P, ST_CHEB_FWD, 1, [&] {
+        GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_fwd, A, B, (long)3 * P->nmodes * 2,
+                              st));
+    });
+    stage(P, ST_KS, 1, [&] {
+        GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_ksw, out_sel, A, st));
+    });
+    int nout = nout_of(out_sel);
+    stage(P, ST_CHEB_INV, 1, [&] {
+        GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
+                              (long)nout * P->nmodes * 2, st));
+    });
+    stage(P, ST_FFT_INV, 2, [&] {
+        GG_CUDA(fft_inverse<T>(geo, B, geo.Ny * nout, P->d_tw_x, P->d_tw_z, st));
+    });
+}
+
+template <typename T>
+void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double* g, int n_tgt,
+                       const double* xt, int tgt_is_src, double* u, double* s) {
+    const GridGeom& geo = P->geo;
+    cudaStream_t st = P->st;
+    stage(P, ST_CELLS, 3, [&] {
+        GG_CUDA(build_cells<T>(geo, P->cg, n_src, xs, P->d_cell_count, P->d_cell_start,
+                               P->d_cursor, P->d_src_cell, P->d_perm, (v4_t<T>*)P->d_spos, st));
+    });
+    stage(P, ST_GATHER, 1, [&] {
+        GG_CUDA(gather_strengths<T>(n_src, P->d_perm, g, nullptr, 1.0, (v4_t<T>*)P->d_sg, st));
+    });
+    SortedSources<T> src = sources_of<T>(P, false);
+    src.n = n_src;
+    int mode = (u ? OUT_U : 0) | (s ? OUT_S : 0);
+    int stride = (u ? 3 : 0) + (s ? 6 : 0);
+    T* loc = (T*)P->d_local;
+    stage(P, ST_LOCAL, 1, [&] {
+        GG_CUDA(local_sum<T>(geo, P->cg, src, tgt_is_src ? TK_SORTED : TK_POINTS,
+                             tgt_is_src ? n_src : n_tgt, xt, nullptr, mode, loc, stride, st));
+    });
+    int sel = (u ? 1 : 0) | (s ? 2 : 0);
+    run_global<T>(P, src, n_src, xs, sel);
+    const double* xtt = tgt_is_src ? xs : xt;
+    int nt = tgt_is_src ? n_src : n_tgt;
+    int nout = nout_of(sel);
+    stage(P, ST_INTERP, (u ? 1 : 0) + (s ? 1 : 0), [&] {
+        if (u) {
+            double sc = 4.0 * geo.alpha / std::sqrt(kPi) / (8.0 * kPi * geo.mu);
+            GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, nout, 0, nt, xtt, loc,
+                                      stride, nullptr, tgt_is_src ? g : nullptr, nullptr, sc, 0,
+                                      u, 3, st));
+        }
+        if (s)
+            GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, nout, u ? 3 : 0, nt,
+                                      xtt, loc + (u ? 3 : 0), stride, nullptr, nullptr, nullptr,
+                                      0.0, 1, s, 6, st));
+    });
+}
+
+template <typename T>
+void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
+    const GridGeom& geo = P->geo;
+    cudaStream_t st = P->st;
+    int n = P->n_nodes;
+    stage(P, ST_GATHER, 1, [&] {
+        GG_CUDA(gather_strengths<T>(n, P->d_mesh_perm, q, P->d_area, 8.0 * kPi * geo.mu,
+                                    (v4_t<T>*)P->d_sg, st));
+    });
+    SortedSources<T> src = sources_of<T>(P, true);
+    src.n = n;
+    T* loc = (T*)P->d_local;
+    stage(P, ST_LOCAL, 1, [&] {
+        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, P->d_nrm,
+                             layer == 0 ? OUT_U : OUT_DBL, loc, 3, st));
+    });
+    run_global<T>(P, src, n, P->d_x, layer == 0 ? 1 : 2);
+    stage(P, ST_INTERP, 1, [&] {
+        if (layer == 0) {
+            double sc = 4.0 * geo.alpha / std::sqrt(kPi);   // (4 alpha/sqrt(pi)) A_b q_b
+            GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 3, 0, n, P->d_x, loc,
+                                      3, nullptr, q, P->d_area, sc, 0, out, 3, st));
+        } else {
+            GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 6, 0, n, P->d_x, loc,
+                                      3, P->d_nrm, nullptr, nullptr, 0.0, 2, out, 3, st));
+        }
+    });
+}
+
+template <typename T>
+void upload_tables(ggem_plan_t* P, const std::vector<double>& cf, const std::vector<double>& ci,
+                   const std::vector<double>& twx, const std::vector<double>& twz) {
+    std::vector<T> a(cf.begin(), cf.end()), b(ci.begin(), ci.end());
+    std::vector<T> c(twx.begin(), twx.end()), d(twz.begin(), twz.end());
+    dalloc(P, (T**)&P->d_cheb_fwd, a.size());
+    dalloc(P, (T**)&P->d_cheb_inv, b.size());
+    dalloc(P, (T**)&P->d_tw_x, c.size());
+    dalloc(P, (T**)&P->d_tw_z, d.size());
+    GG_CUDA(cudaMemcpy(P->d_cheb_fwd, a.data(), a.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_cheb_inv, b.data(), b.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_tw_x, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_tw_z, d.data(), d.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+void plan_build(ggem_plan_t* P, const ggem_params& prm) {
+    P->prm = prm;
+    GG_CHECK(is_pow2(prm.Nx) && is_pow2(prm.Nz) && prm.Nx >= 16 && prm.Nz >= 16 &&
+                 prm.Nx <= 1024 && prm.Nz <= 1024,
+             GGEM_ERR_INVALID_ARG, "Nx and Nz must be powers of two in [16, 1024]");
+    GG_CHECK(prm.Ny >= 9 && prm.Ny <= 257, GGEM_ERR_INVALID_ARG, "Ny must lie in [9, 257]");
+    GG_CHECK(prm.Lx > 0 && prm.Lz > 0 && prm.W > 0 && prm.mu > 0, GGEM_ERR_INVALID_ARG,
+             "Lx, Lz, W and mu must be positive");
+    GG_CHECK(prm.precision == GGEM_FP64 || prm.precision == GGEM_MIXED, GGEM_ERR_INVALID_ARG,
+             "precision must be GGEM_FP64 or GGEM_MIXED");
+    GG_CHECK(prm.quadrature == GGEM_NODAL || prm.quadrature == GGEM_ELEMENT,
+             GGEM_ERR_INVALID_ARG, "quadrature must be GGEM_NODAL or GGEM_ELEMENT");
+    GG_CHECK(prm.max_points > 0 && prm.max_tris >= 0, GGEM_ERR_INVALID_ARG,
+             "max_points must be positive");
+    GridGeom& g = P->geo;
+    g.Lx = prm.Lx; g.Lz = prm.Lz; g.W = prm.W; g.y0 = prm.y0;
+    g.Nx = prm.Nx; g.Ny = prm.Ny; g.Nz = prm.Nz; g.nkx = prm.Nx / 2;
+    g.dx = prm.Lx / prm.Nx; g.dz = prm.Lz / prm.Nz;
+    g.mu = prm.mu;
+    double h = std::fmax(std::fmax(g.dx, prm.W / (prm.Ny - 1)), g.dz);
+    g.alpha = prm.alpha > 0 ? prm.alpha : 1.0 / (2.0 * h);
+    double rf = prm.rcut_factor > 0 ? prm.rcut_factor : 4.0;
+    g.rcut = rf / g.alpha;
+    GG_CHECK(g.alpha * prm.Lx > 2 * rf && g.alpha * prm.Lz > 2 * rf, GGEM_ERR_INVALID_ARG,
+             "alpha*L must exceed 2*rcut_factor (r_cut below half the period)");
+    P->fp64 = prm.precision == GGEM_FP64;
+    P->nmodes = prm.Nz * g.nkx;
+    CellGrid& cg = P->cg;
+    cg.ncx = std::max(1, (int)std::floor(prm.Lx / g.rcut));
+    cg.ncz = std::max(1, (int)std::floor(prm.Lz / g.rcut));
+    cg.ncy = std::max(1, (int)std::floor(prm.W / g.rcut));
+    cg.hx = prm.Lx / cg.ncx; cg.hz = prm.Lz / cg.ncz; cg.hy = prm.W / cg.ncy;
+    cg.y0 = prm.y0;
+    P->ncell = cg.ncx * cg.ncy * cg.ncz;
+
+    const int Ny = prm.Ny, N = Ny - 1;
+    std::vector<double> yj(Ny), cf((size_t)Ny * Ny), ci((size_t)Ny * Ny);
+    for (int j = 0; j < Ny; ++j) yj[j] = prm.y0 + 0.5 * prm.W * (1.0 + std::cos(kPi * j / N));
+    double inxz = 1.0 / ((double)prm.Nx * prm.Nz);
+    for (int n = 0; n < Ny; ++n)
+        for (int j = 0; j < Ny; ++j) {
+            double cn = (n == 0 || n == N) ? 2.0 : 1.0, cj = (j == 0 || j == N) ? 2.0 : 1.0;
+            double c = std::cos(kPi * ((long)n * j % (2 * N)) / N);
+            cf[(size_t)n * Ny + j] = 2.0 / (N * cn * cj) * c * inxz;
+            ci[(size_t)j * Ny + n] = c;
+        }
+    int M = prm.Nx / 2;
+    std::vector<double> twx(2 * (M / 2 + M)), twz(2 * (prm.Nz / 2));
+    for (int k = 0; k < M / 2; ++k) {
+        twx[2 * k] = std::cos(2 * kPi * k / M);
+        twx[2 * k + 1] = -std::sin(2 * kPi * k / M);
+    }
+    for (int k = 0; k < M; ++k) {
+        twx[2 * (M / 2 + k)] = std::cos(2 * kPi * k / prm.Nx);
+        twx[2 * (M / 2 + k) + 1] = -std::sin(2 * kPi * k / prm.Nx);
+    }
+    for (int k = 0; k < prm.Nz / 2; ++k) {
+        twz[2 * k] = std::cos(2 * kPi * k / prm.Nz);
+        twz[2 * k + 1] = -std::sin(2 * kPi * k / prm.Nz);
+    }
+    dalloc(P, &P->d_yj, Ny);
+    GG_CUDA(cudaMemcpy(P->d_yj, yj.data(), Ny * sizeof(double), cudaMemcpyHostToDevice));
+    if (P->fp64) upload_tables<double>(P, cf, ci, twx, twz);
+    else upload_tables<float>(P, cf, ci, twx, twz);
+
+    // per-mode homogeneous solutions and inverse influence matrices (App. C)
+    const int nm = P->nmodes;
+    std::vector<double> ksb((size_t)3 * Ny * nm, 0.0), minv((size_t)4 * nm, 0.0);
+#pragma omp parallel
+    {
+        std::vector<double> pb(Ny), ph(Ny), vb(Ny);
+        double mi[4];
+#pragma omp for schedule(dynamic, 64)
+        for (int m = 0; m < nm; ++m) {
+            int kzi = m / g.nkx, kxi = m % g.nkx;
+            if (m == 0 || kzi == prm.Nz / 2) continue;
+            int mz = kzi < prm.Nz / 2 ? kzi : kzi - prm.Nz;
+            double kx = 2 * kPi * kxi / prm.Lx, kz = 2 * kPi * mz / prm.Lz;
+            ks_precompute_mode(Ny, prm.W, prm.mu, kx * kx + kz * kz, pb.data(), ph.data(),
+                               vb.data(), mi);
+            for (int n = 0; n < Ny; ++n) {
+                ksb[((size_t)0 * Ny + n) * nm + m] = pb[n];
+                ksb[((size_t)1 * Ny + n) * nm + m] = ph[n];
+                ksb[((size_t)2 * Ny + n) * nm + m] = vb[n];
+            }
+            for (int c = 0; c < 4; ++c) minv[(size_t)c * nm + m] = mi[c];
+        }
+    }
+    dalloc(P, &P->d_ksb, ksb.size());
+    dalloc(P, &P->d_minv, minv.size());
+    GG_CUDA(cudaMemcpy(P->d_ksb, ksb.data(), ksb.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_minv, minv.data(), minv.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
+
+    // workspaces
+    size_t esz = P->fp64 ? sizeof(double) : sizeof(float);
+    P->grid_elems = (size_t)9 * Ny * prm.Nz * prm.Nx;
+    GG_CUDA(cudaMalloc(&P->d_gridA, P->grid_elems * esz));
+    GG_CUDA(cudaMalloc(&P->d_gridB, P->grid_elems * esz));
+    GG_CUDA(cudaMalloc(&P->d_wall, (size_t)6 * prm.Nz * prm.Nx * esz));
+    dalloc(P, &P->d_ksw, (size_t)7 * 2 * Ny * nm);
+    int cap = prm.max_points;
+    P->cap = cap;
+    dalloc(P, &P->d_cell_count, P->ncell);
+    dalloc(P, &P->d_cell_start, P->ncell + 1);
+    dalloc(P, &P->d_cursor, (size_t)P->ncell + cap);
+    dalloc(P, &P->d_src_cell, cap);
+    dalloc(P, &P->d_perm, cap);
+    size_t v4 = P->fp64 ? sizeof(double4_32a) : sizeof(float4);
+    GG_CUDA(cudaMalloc(&P->d_spos, cap * v4 + 32));
+    GG_CUDA(cudaMalloc(&P->d_sg, cap * v4 + 32));
+    GG_CUDA(cudaMalloc(&P->d_local, (size_t)cap * 9 * esz + 32));
+    dalloc(P, &P->d_in0, (size_t)cap * 3);
+    dalloc(P, &P->d_in1, (size_t)cap * 3);
+    dalloc(P, &P->d_in2, (size_t)cap * 3);
+    dalloc(P, &P->d_out0, (size_t)cap * 3);
+    dalloc(P, &P->d_out1, (size_t)cap * 6);
+    // mesh tables
+    P->cap_tris = prm.max_tris;
+    dalloc(P, &P->d_x, (size_t)cap * 3);
+    dalloc(P, &P->d_area, cap);
+    dalloc(P, &P->d_nrm, (size_t)cap * 3);
+    dalloc(P, &P->d_mesh_cell, cap);
+    dalloc(P, &P->d_mesh_perm, cap);
+    dalloc(P, &P->d_mesh_start, P->ncell + 1);
+    GG_CUDA(cudaMalloc(&P->d_mesh_pos, cap * v4 + 32));
+    if (prm.max_tris > 0) {
+        dalloc(P, &P->d_tri, (size_t)prm.max_tris * 3);
+        dalloc(P, &P->d_tri_area, prm.max_tris);
+        dalloc(P, &P->d_tri_nrm, (size_t)prm.max_tris * 3);
+    }
+    GG_CUDA(cudaEventCreate(&P->ev0));
+    GG_CUDA(cudaEventCreate(&P->ev1));
+    GG_CUDA(cudaDeviceSynchronize());
+}
+
+void plan_free(ggem_plan_t* P) {
+    if (P->ev0) cudaEventDestroy(P->ev0);
+    if (P->ev1) cudaEventDestroy(P->ev1);
+    void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
+                    P->d_minv, P->d_gridA, P->d_gridB, P->d_wall, P->d_ksw, P->d_cell_count,
+                    P->d_cell_start, P->d_cursor, P->d_src_cell, P->d_perm, P->d_spos, P->d_sg,
+                    P->d_src_x, P->d_local, P->d_in0, P->d_in1, P->d_in2, P->d_out0, P->d_out1, P->d_x,
+                    P->d_tri, P->d_area, P->d_nrm, P->d_tri_area, P->d_tri_nrm,
+                    P->d_mesh_cell, P->d_mesh_perm, P->d_mesh_start, P->d_mesh_pos};
+    for (void* p : ptrs) dfree(p);
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+ggem_status ggem_plan(const ggem_params* params, void* stream, ggem_plan_t** out) {
+    if (!out) return GGEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params) return GGEM_ERR_INVALID_ARG;
+    ggem_plan_t* P = new (std::nothrow) ggem_plan_t();
+    if (!P) return GGEM_ERR_CAPACITY;
+    P->st = (cudaStream_t)stream;
+    ggem_status s = guarded(P, [&] { plan_build(P, *params); });
+    if (s != GGEM_OK) {
+        g_create_error = P->err;
+        plan_free(P);
+        delete P;
+        return s;
+    }
+    *out = P;
+    return GGEM_OK;
+}
+
+ggem_status ggem_plan_destroy(ggem_plan_t* P) {
+    if (!P) return GGEM_OK;
+    cudaStreamSynchronize(P->st);
+    plan_free(P);
+    delete P;
+    return GGEM_OK;
+}
+
+const char* ggem_last_error(const ggem_plan_t* P) {
+    if (!P) return g_create_error.c_str();
+    return P->err.c_str();
+}
+
+ggem_status ggem_plan_info(const ggem_plan_t* P, double* alpha, double* rcut) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    if (alpha) *alpha = P->geo.alpha;
+    if (rcut) *rcut = P->geo.rcut;
+    return GGEM_OK;
+}
+
+ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tris,
+                          const int* tri) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(n_nodes > 0 && x, GGEM_ERR_INVALID_ARG, "mesh needs nodes");
+        GG_CHECK(n_nodes <= P->cap, GGEM_ERR_CAPACITY, "more nodes than max_points");
+        GG_CHECK(n_tris >= 0 && n_tris <= P->cap_tris, GGEM_ERR_CAPACITY,
+                 "more triangles than max_tris");
+        GG_CHECK(n_tris == 0 || tri, GGEM_ERR_INVALID_ARG, "triangles pointer is NULL");
+        cudaStream_t st = P->st;
+        auto kind = [](const void* p) {
+            return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        };
+        GG_CUDA(cudaMemcpyAsync(P->d_x, x, (size_t)n_nodes * 3 * sizeof(double), kind(x), st));
+        if (n_tris > 0)
+            GG_CUDA(cudaMemcpyAsync(P->d_tri, tri, (size_t)n_tris * 3 * sizeof(int), kind(tri),
+                                    st));
+        int* bad = P->d_cell_count;   // scratch int
+        GG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        k_check_inside<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, P->d_x, P->geo.y0,
+                                                             P->geo.W, bad);
+        int hbad = 0;
+        GG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GG_CUDA(cudaStreamSynchronize(st));
+        GG_CHECK(hbad == 0, GGEM_ERR_INVALID_ARG,
+                 "mesh nodes must be finite and lie strictly inside the slit");
+        GG_CUDA(cudaMemsetAsync(P->d_area, 0, (size_t)n_nodes * sizeof(double), st));
+        GG_CUDA(cudaMemsetAsync(P->d_nrm, 0, (size_t)n_nodes * 3 * sizeof(double), st));
+        if (n_tris > 0) {
+            k_tri_geom<<<(n_tris + 255) / 256, 256, 0, st>>>(n_tris, P->d_x, P->d_tri,
+                                                             P->d_tri_area, P->d_tri_nrm,
+                                                             P->d_area, P->d_nrm);
+            k_normalize<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, P->d_nrm);
+        }
+        GG_CUDA(cudaGetLastError());
+        if (P->fp64)
+            GG_CUDA(build_cells<double>(P->geo, P->cg, n_nodes, P->d_x, P->d_cell_count,
+                                        P->d_mesh_start, P->d_cursor, P->d_mesh_cell,
+                                        P->d_mesh_perm, (double4_32a*)P->d_mesh_pos, st));
+        else
+            GG_CUDA(build_cells<float>(P->geo, P->cg, n_nodes, P->d_x, P->d_cell_count,
+                                       P->d_mesh_start, P->d_cursor, P->d_mesh_cell,
+                                       P->d_mesh_perm, (float4*)P->d_mesh_pos, st));
+        P->n_nodes = n_nodes;
+        P->n_tris = n_tris;
+        P->mesh_ready = true;
+        GG_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+ggem_status ggem_mesh_geometry(ggem_plan_t* P, double* area, double* normal) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(P->mesh_ready, GGEM_ERR_INVALID_ARG, "no mesh set");
+        int n = P->n_nodes;
+        if (area)
+            GG_CUDA(cudaMemcpyAsync(area, P->d_area, n * sizeof(double), cudaMemcpyDefault,
+                                    P->st));
+        if (normal)
+            GG_CUDA(cudaMemcpyAsync(normal, P->d_nrm, (size_t)n * 3 * sizeof(double),
+                                    cudaMemcpyDefault, P->st));
+        GG_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+ggem_status ggem_point_forces(ggem_plan_t* P, int n_src, const double* x_src, const double* g,
+                              int n_tgt, const double* x_tgt, int tgt_is_src, double* u,
+                              double* sigma) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(n_src >= 0 && n_src <= P->cap, GGEM_ERR_CAPACITY, "n_src exceeds max_points");
+        GG_CHECK(n_src == 0 || (x_src && g), GGEM_ERR_INVALID_ARG, "NULL source arrays");
+        if (tgt_is_src) n_tgt = n_src;
+        GG_CHECK(n_tgt >= 0 && n_tgt <= P->cap, GGEM_ERR_CAPACITY, "n_tgt exceeds max_points");
+        GG_CHECK(tgt_is_src || n_tgt == 0 || x_tgt, GGEM_ERR_INVALID_ARG, "NULL target array");
+        if (!u && !sigma) return;
+        const double* xs = stage_in(P, x_src, P->d_in0, (size_t)n_src * 3);
+        const double* gd = stage_in(P, g, P->d_in1, (size_t)n_src * 3);
+        const double* xt = tgt_is_src ? xs : stage_in(P, x_tgt, P->d_in2, (size_t)n_tgt * 3);
+        OutMap mu_ = stage_out(u, P->d_out0, (size_t)n_tgt * 3);
+        OutMap ms_ = stage_out(sigma, P->d_out1, (size_t)n_tgt * 6);
+        if (P->fp64)
+            point_forces_impl<double>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
+        else
+            point_forces_impl<float>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
+        finish_out(P, mu_);
+        finish_out(P, ms_);
+        if (mu_.host || ms_.host) GG_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+static ggem_status layer_entry(ggem_plan_t* P, int layer, const double* q, double* out) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(P->mesh_ready, GGEM_ERR_INVALID_ARG, "no mesh set");
+        GG_CHECK(q && out, GGEM_ERR_INVALID_ARG, "NULL density or output");
+        GG_CHECK(P->prm.quadrature == GGEM_NODAL || P->n_tris > 0, GGEM_ERR_INVALID_ARG,
+                 "element quadrature needs triangles");
+        GG_CHECK(P->prm.quadrature == GGEM_NODAL, GGEM_ERR_INVALID_ARG,
+                 "element quadrature is not available in this build");
+        GG_CHECK(layer == 0 || P->n_tris > 0, GGEM_ERR_INVALID_ARG,
+                 "the double layer needs triangles (node normals)");
+        size_t n3 = (size_t)P->n_nodes * 3;
+        const double* qd = stage_in(P, q, P->d_in0, n3);
+        OutMap mo = stage_out(out, P->d_out0, n3);
+        if (P->fp64) layer_impl<double>(P, layer, qd, mo.dev);
+        else layer_impl<float>(P, layer, qd, mo.dev);
+        finish_out(P, mo);
+        if (mo.host) GG_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+ggem_status ggem_single_layer(ggem_plan_t* P, const double* q, double* w) {
+    return layer_entry(P, 0, q, w);
+}
+
+ggem_status ggem_double_layer(ggem_plan_t* P, const double* q, double* v) {
+    return layer_entry(P, 1, q, v);
+}
+
+ggem_status ggem_trace_enable(ggem_plan_t* P, int on) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    P->prof = on != 0;
+    for (int i = 0; i < 16; ++i) {
+        P->prof_ms[i] = 0.0;
+        P->prof_calls[i] = 0;
+    }
+    P->launches = 0;
+    return GGEM_OK;
+}
+
+int ggem_trace_stage_count(void) { return ST_COUNT; }
+
+const char* ggem_trace_stage_name(int stage) {
+    return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
+}
+
+ggem_status ggem_trace_read(const ggem_plan_t* P, int stage, double* total_ms, long* calls) {
+    if (!P || stage < 0 || stage >= ST_COUNT) return GGEM_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = P->prof_ms[stage];
+    if (calls) *calls = P->prof_calls[stage];
+    return GGEM_OK;
+}
+
+ggem_status ggem_launch_count(const ggem_plan_t* P, long* launches) {
+    if (!P || !launches) return GGEM_ERR_INVALID_ARG;
+    *launches = P->launches;
+    return GGEM_OK;
+}
+
+}  // extern "C"

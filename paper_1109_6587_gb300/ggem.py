@@ -1,0 +1,237 @@
+"""Thin Python binding of libggem (include/ggem.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  Arrays may be torch CUDA tensors (passed as device pointers, the call
+runs on the plan's stream) or numpy arrays (host pointers; the library stages
+them and returns when the host output is written).  The library must be built
+(``__graft_entry__.build()`` or ``python -m paper_1109_6587_gb300._build``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+_LIB_PATH = pathlib.Path(__file__).resolve().parent / "libggem.so"
+_lib = None
+
+GGEM_OK = 0
+STATUS = {0: "GGEM_OK", 1: "GGEM_ERR_INVALID_ARG", 2: "GGEM_ERR_CAPACITY",
+          3: "GGEM_ERR_CUDA", 4: "GGEM_ERR_NUMERICAL", 5: "GGEM_ERR_NOT_CONVERGED",
+          6: "GGEM_OK_BREAKDOWN"}
+GGEM_FP64, GGEM_MIXED = 0, 1
+GGEM_NODAL, GGEM_ELEMENT = 0, 1
+
+
+class GGEMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ggem_params(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("W", ctypes.c_double),
+                ("y0", ctypes.c_double), ("Nx", ctypes.c_int), ("Ny", ctypes.c_int),
+                ("Nz", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("rcut_factor", ctypes.c_double), ("mu", ctypes.c_double),
+                ("precision", ctypes.c_int), ("quadrature", ctypes.c_int),
+                ("max_points", ctypes.c_int), ("max_tris", ctypes.c_int)]
+
+
+EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info",
+           "ggem_mesh_set", "ggem_mesh_geometry", "ggem_point_forces", "ggem_single_layer",
+           "ggem_double_layer", "ggem_trace_enable", "ggem_trace_stage_count",
+           "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count"]
+
+
+def lib():
+    """Load libggem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise ImportError(f"{_LIB_PATH} is missing: build the CUDA library first "
+                              "(python -m paper_1109_6587_gb300._build)")
+        L = ctypes.CDLL(str(_LIB_PATH))
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.ggem_plan.argtypes = [ctypes.POINTER(ggem_params), P, ctypes.POINTER(P)]
+        L.ggem_plan_destroy.argtypes = [P]
+        L.ggem_last_error.argtypes = [P]
+        L.ggem_last_error.restype = ctypes.c_char_p
+        L.ggem_plan_info.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.ggem_mesh_set.argtypes = [P, I, P, I, P]
+        L.ggem_mesh_geometry.argtypes = [P, P, P]
+        L.ggem_point_forces.argtypes = [P, I, P, P, I, P, I, P, P]
+        L.ggem_single_layer.argtypes = [P, P, P]
+        L.ggem_double_layer.argtypes = [P, P, P]
+        L.ggem_trace_enable.argtypes = [P, I]
+        L.ggem_trace_stage_count.argtypes = []
+        L.ggem_trace_stage_name.argtypes = [I]
+        L.ggem_trace_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
+        L.ggem_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_long)]
+        for name in EXPORTS:
+            getattr(L, name).restype = (ctypes.c_char_p if name in ("ggem_last_error",
+                                                                    "ggem_trace_stage_name")
+                                         else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive) for a torch tensor or numpy array of the given dtype."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):                     # torch tensor
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _check(status, plan):
+    if status not in (0, 6):
+        msg = lib().ggem_last_error(plan)
+        raise GGEMError(status, msg.decode() if msg else "")
+    return status
+
+
+def _zeros_like_target(ref, shape):
+    if hasattr(ref, "data_ptr"):
+        import torch
+        return torch.zeros(shape, dtype=torch.float64, device=ref.device)
+    return np.zeros(shape)
+
+
+class Plan:
+    """A ggem plan (grid, tables, workspaces) bound to one CUDA stream."""
+
+    def __init__(self, Lx, Lz, W, y0, Nx, Ny, Nz, alpha=0.0, rcut_factor=0.0, mu=1.0,
+                 precision="fp64", quadrature="nodal", max_points=1 << 16, max_tris=0,
+                 stream=None):
+        prec = {"fp64": GGEM_FP64, "mixed": GGEM_MIXED}[precision]
+        quad = {"nodal": GGEM_NODAL, "element": GGEM_ELEMENT}[quadrature]
+        self.params = ggem_params(Lx, Lz, W, y0, Nx, Ny, Nz, alpha, rcut_factor, mu, prec,
+                                  quad, max_points, max_tris)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:
+                stream = 0
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib().ggem_plan(ctypes.byref(self.params), ctypes.c_void_p(stream),
+                               ctypes.byref(h)), None)
+        self.h = h
+        self.n_nodes = 0
+
+    @classmethod
+    def for_box(cls, box, **kw):
+        return cls(box.Lx, box.Lz, box.W, box.y0, box.Nx, box.Ny, box.Nz, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ggem_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a, r = ctypes.c_double(), ctypes.c_double()
+        _check(lib().ggem_plan_info(self.h, ctypes.byref(a), ctypes.byref(r)), self.h)
+        return a.value, r.value
+
+    def mesh_set(self, x, tri=None):
+        n = int(x.shape[0])
+        px, kx = _ptr(x, np.float64)
+        pt, kt = _ptr(tri, np.int32)
+        m = 0 if tri is None else int(tri.shape[0])
+        _check(lib().ggem_mesh_set(self.h, n, px, m, pt), self.h)
+        self.n_nodes = n
+        self._mesh_ref = x
+
+    def mesh_geometry(self):
+        area = np.zeros(self.n_nodes)
+        nrm = np.zeros((self.n_nodes, 3))
+        _check(lib().ggem_mesh_geometry(self.h, ctypes.c_void_p(area.ctypes.data),
+                                        ctypes.c_void_p(nrm.ctypes.data)), self.h)
+        return area, nrm
+
+    def point_forces(self, xs, g, xt=None, want_u=True, want_sigma=False, u=None, sigma=None):
+        ns = int(xs.shape[0])
+        self_t = xt is None
+        nt = ns if self_t else int(xt.shape[0])
+        pxs, k1 = _ptr(xs, np.float64)
+        pg, k2 = _ptr(g, np.float64)
+        pxt, k3 = _ptr(xt, np.float64)
+        if want_u and u is None:
+            u = _zeros_like_target(xs, (nt, 3))
+        if want_sigma and sigma is None:
+            sigma = _zeros_like_target(xs, (nt, 6))
+        pu, k4 = _ptr(u if want_u else None, np.float64)
+        psg, k5 = _ptr(sigma if want_sigma else None, np.float64)
+        _check(lib().ggem_point_forces(self.h, ns, pxs, pg, nt, pxt, 1 if self_t else 0,
+                                       pu, psg), self.h)
+        return (u if want_u else None), (sigma if want_sigma else None)
+
+    def _layer(self, fn, q, out):
+        if out is None:
+            out = _zeros_like_target(q, (self.n_nodes, 3))
+        pq, k1 = _ptr(q, np.float64)
+        po, k2 = _ptr(out, np.float64)
+        _check(fn(self.h, pq, po), self.h)
+        return out
+
+    def trace(self, on=True):
+        _check(lib().ggem_trace_enable(self.h, 1 if on else 0), self.h)
+
+    def trace_read(self):
+        """{stage: (total_ms, calls)} for stages that ran."""
+        L = lib()
+        out = {}
+        for i in range(L.ggem_trace_stage_count()):
+            ms, calls = ctypes.c_double(), ctypes.c_long()
+            _check(L.ggem_trace_read(self.h, i, ctypes.byref(ms), ctypes.byref(calls)), self.h)
+            if calls.value:
+                out[L.ggem_trace_stage_name(i).decode()] = (ms.value, calls.value)
+        return out
+
+    def launch_count(self):
+        n = ctypes.c_long()
+        _check(lib().ggem_launch_count(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def single_layer(self, q, out=None):
+        return self._layer(lib().ggem_single_layer, q, out)
+
+    def double_layer(self, q, out=None):
+        return self._layer(lib().ggem_double_layer, q, out)
+
+
+# The C names, for callers that prefer them.
+def ggem_plan(box_or_params, **kw):
+    return Plan.for_box(box_or_params, **kw)
+
+
+def ggem_single_layer(plan, q, out=None):
+    return plan.single_layer(q, out)
+
+
+def ggem_double_layer(plan, q, out=None):
+    return plan.double_layer(q, out)
+
+
+def ggem_point_forces(plan, xs, g, xt=None, want_u=True, want_sigma=False):
+    return plan.point_forces(xs, g, xt, want_u, want_sigma)
+
+
+def ggem_mesh_set(plan, x, tri=None):
+    return plan.mesh_set(x, tri)

@@ -173,9 +173,13 @@ def box_single_sphere():
     return Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=32, Ny=33, Nz=32)
 
 
-def single_sphere(seed=0):
-    """162-node icosphere centred at (4, 0, 4)."""
-    return suspension(1, box_single_sphere(), level=2, radius=1.0, seed=seed,
+def single_sphere(seed=0, radius=1.0):
+    """162-node icosphere centred at (4, 0, 4).
+
+    With radius 1 every node has its antipode exactly at r_cut = 2 (alpha = 2
+    on the 32 x 33 x 32 grid), so whether those pairs count is decided by
+    rounding; a radius a little below 1 removes that tie."""
+    return suspension(1, box_single_sphere(), level=2, radius=radius, seed=seed,
                       centres=np.array([[4.0, 0.0, 4.0]]))
 
 
