@@ -128,6 +128,18 @@ ggem_status ggem_point_forces(ggem_plan_t *plan, int n_src, const double *x_src,
                               int tgt_is_src, double *u, double *sigma);
 
 /*
+ * Local part alone, Eq. (u_loc) of Sec. 3.2.1: the free-space response to the
+ * local densities rho_l of the point forces, truncated at r_cut,
+ *   u^l_i(x)      = 1/(8 pi mu) sum_{0 < |x - x_nu*| < r_cut} G^l_ij g_nu_j
+ *   sigma^l_ik(x) = 1/(8 pi)    sum_{0 < |x - x_nu*| < r_cut} T^l_ijk g_nu_j
+ * (x_nu* the minimum image in x and z).  Same arguments and layouts as
+ * ggem_point_forces; no global part and no self term.
+ */
+ggem_status ggem_local_sum(ggem_plan_t *plan, int n_src, const double *x_src,
+                           const double *g, int n_tgt, const double *x_tgt,
+                           int tgt_is_src, double *u, double *sigma);
+
+/*
  * Single-layer integral at the mesh nodes (Sec. 3.4, Eq. (sl_t)):
  *   w_j(z) = int_S q_i(x) G_ji(z, x) dS(x),   q, w: [n_nodes][3].
  * Local part by the plan's quadrature, global part from the trapezoidal

@@ -278,6 +278,48 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
 }
 
 template <typename T>
+__global__ void k_split_local(int n, const T* __restrict__ loc, int stride, double* __restrict__ u,
+                              double* __restrict__ s) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const T* o = loc + (size_t)t * stride;
+    int k = 0;
+    if (u) {
+        for (int c = 0; c < 3; ++c) u[3 * t + c] = (double)o[c];
+        k = 3;
+    }
+    if (s)
+        for (int c = 0; c < 6; ++c) s[6 * t + c] = (double)o[k + c];
+}
+
+// Local part alone (Eq. u_loc): cell list of the sources, then the pair sum.
+template <typename T>
+void local_only_impl(ggem_plan_t* P, int n_src, const double* xs, const double* g, int n_tgt,
+                     const double* xt, int tgt_is_src, double* u, double* s) {
+    const GridGeom& geo = P->geo;
+    cudaStream_t st = P->st;
+    stage(P, ST_CELLS, 3, [&] {
+        GG_CUDA(build_cells<T>(geo, P->cg, n_src, xs, P->d_cell_count, P->d_cell_start,
+                               P->d_cursor, P->d_src_cell, P->d_perm, (v4_t<T>*)P->d_spos, st));
+    });
+    stage(P, ST_GATHER, 1, [&] {
+        GG_CUDA(gather_strengths<T>(n_src, P->d_perm, g, nullptr, 1.0, (v4_t<T>*)P->d_sg, st));
+    });
+    SortedSources<T> src = sources_of<T>(P, false);
+    src.n = n_src;
+    int mode = (u ? OUT_U : 0) | (s ? OUT_S : 0);
+    int stride = (u ? 3 : 0) + (s ? 6 : 0);
+    int nt = tgt_is_src ? n_src : n_tgt;
+    T* loc = (T*)P->d_local;
+    stage(P, ST_LOCAL, 2, [&] {
+        GG_CUDA(local_sum<T>(geo, P->cg, src, tgt_is_src ? TK_SORTED : TK_POINTS, nt, xt,
+                             nullptr, mode, loc, stride, st));
+        if (nt > 0) k_split_local<T><<<(nt + 255) / 256, 256, 0, st>>>(nt, loc, stride, u, s);
+        GG_CUDA(cudaGetLastError());
+    });
+}
+
+template <typename T>
 void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
     const GridGeom& geo = P->geo;
     cudaStream_t st = P->st;
@@ -597,6 +639,32 @@ ggem_status ggem_point_forces(ggem_plan_t* P, int n_src, const double* x_src, co
             point_forces_impl<double>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
         else
             point_forces_impl<float>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
+        finish_out(P, mu_);
+        finish_out(P, ms_);
+        if (mu_.host || ms_.host) GG_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+ggem_status ggem_local_sum(ggem_plan_t* P, int n_src, const double* x_src, const double* g,
+                           int n_tgt, const double* x_tgt, int tgt_is_src, double* u,
+                           double* sigma) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(n_src >= 0 && n_src <= P->cap, GGEM_ERR_CAPACITY, "n_src exceeds max_points");
+        GG_CHECK(n_src == 0 || (x_src && g), GGEM_ERR_INVALID_ARG, "NULL source arrays");
+        if (tgt_is_src) n_tgt = n_src;
+        GG_CHECK(n_tgt >= 0 && n_tgt <= P->cap, GGEM_ERR_CAPACITY, "n_tgt exceeds max_points");
+        GG_CHECK(tgt_is_src || n_tgt == 0 || x_tgt, GGEM_ERR_INVALID_ARG, "NULL target array");
+        if (!u && !sigma) return;
+        const double* xs = stage_in(P, x_src, P->d_in0, (size_t)n_src * 3);
+        const double* gd = stage_in(P, g, P->d_in1, (size_t)n_src * 3);
+        const double* xt = tgt_is_src ? xs : stage_in(P, x_tgt, P->d_in2, (size_t)n_tgt * 3);
+        OutMap mu_ = stage_out(u, P->d_out0, (size_t)n_tgt * 3);
+        OutMap ms_ = stage_out(sigma, P->d_out1, (size_t)n_tgt * 6);
+        if (P->fp64)
+            local_only_impl<double>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
+        else
+            local_only_impl<float>(P, n_src, xs, gd, n_tgt, xt, tgt_is_src, mu_.dev, ms_.dev);
         finish_out(P, mu_);
         finish_out(P, ms_);
         if (mu_.host || ms_.host) GG_CUDA(cudaStreamSynchronize(P->st));

@@ -41,7 +41,8 @@ class ggem_params(ctypes.Structure):
 
 
 EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info",
-           "ggem_mesh_set", "ggem_mesh_geometry", "ggem_point_forces", "ggem_single_layer",
+           "ggem_mesh_set", "ggem_mesh_geometry", "ggem_point_forces", "ggem_local_sum",
+           "ggem_single_layer",
            "ggem_double_layer", "ggem_trace_enable", "ggem_trace_stage_count",
            "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count"]
 
@@ -63,6 +64,7 @@ def lib():
         L.ggem_mesh_set.argtypes = [P, I, P, I, P]
         L.ggem_mesh_geometry.argtypes = [P, P, P]
         L.ggem_point_forces.argtypes = [P, I, P, P, I, P, I, P, P]
+        L.ggem_local_sum.argtypes = [P, I, P, P, I, P, I, P, P]
         L.ggem_single_layer.argtypes = [P, P, P]
         L.ggem_double_layer.argtypes = [P, P, P]
         L.ggem_trace_enable.argtypes = [P, I]
@@ -166,6 +168,13 @@ class Plan:
         return area, nrm
 
     def point_forces(self, xs, g, xt=None, want_u=True, want_sigma=False, u=None, sigma=None):
+        return self._pf(lib().ggem_point_forces, xs, g, xt, want_u, want_sigma, u, sigma)
+
+    def local_sum(self, xs, g, xt=None, want_u=True, want_sigma=False, u=None, sigma=None):
+        """Local part u^l, sigma^l alone (Eq. u_loc)."""
+        return self._pf(lib().ggem_local_sum, xs, g, xt, want_u, want_sigma, u, sigma)
+
+    def _pf(self, fn, xs, g, xt, want_u, want_sigma, u, sigma):
         ns = int(xs.shape[0])
         self_t = xt is None
         nt = ns if self_t else int(xt.shape[0])
@@ -178,8 +187,7 @@ class Plan:
             sigma = _zeros_like_target(xs, (nt, 6))
         pu, k4 = _ptr(u if want_u else None, np.float64)
         psg, k5 = _ptr(sigma if want_sigma else None, np.float64)
-        _check(lib().ggem_point_forces(self.h, ns, pxs, pg, nt, pxt, 1 if self_t else 0,
-                                       pu, psg), self.h)
+        _check(fn(self.h, ns, pxs, pg, nt, pxt, 1 if self_t else 0, pu, psg), self.h)
         return (u if want_u else None), (sigma if want_sigma else None)
 
     def _layer(self, fn, q, out):

@@ -174,3 +174,25 @@ def test_100_capsules_sampled(ggem, prec):
     torch.cuda.synchronize()
     assert _rel(w[idx], w_ref) < TOL[prec]
     assert _rel(v[idx], v_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_local_sum_alone(ggem, prec):
+    s = W.capsules_100()
+    g = W.normal_forces(s.x.shape[0], seed=6)
+    box = s.box
+    alpha = O.default_alpha(box)
+    rcut = O.default_rcut(alpha)
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(s.x.shape[0], 300, replace=False))
+    xt = s.x[idx] + rng.normal(scale=0.05, size=(300, 3))
+    u_ref, s_ref = O.local_point(box, alpha, rcut, 1.0, s.x, g, xt, want_sig=True)
+    P = ggem.Plan.for_box(box, precision=prec, max_points=s.x.shape[0])
+    u, sig = P.local_sum(_dev(s.x), _dev(g), _dev(xt), want_sigma=True)
+    torch.cuda.synchronize()
+    assert _rel(u, u_ref) < TOL[prec]
+    assert _rel(sig, _sym6(s_ref)) < TOL[prec]
+    # self targets: the self pair (r = 0) is left out
+    us, _ = P.local_sum(_dev(s.x), _dev(g))
+    us_ref, _ = O.local_point(box, alpha, rcut, 1.0, s.x, g, s.x[idx])
+    assert _rel(us[idx], us_ref) < TOL[prec]
