@@ -156,6 +156,37 @@ ggem_status ggem_single_layer(ggem_plan_t *plan, const double *q, double *w);
 ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
 
 /*
+ * Allocation-free local velocity sum (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc -- code recording a CUDA graph
+ * under stream capture, where allocation calls are not allowed; applications
+ * whose device memory belongs to another allocator or a fixed budget; loops
+ * that must avoid the device-wide synchronisation of cudaFree -- and that
+ * therefore cannot create a plan either.  Computes the same u^l as
+ * ggem_local_sum (velocity only, FP64, Eq. (u_loc)) from the geometry and
+ * alpha / r_cut rules of *params (its precision, quadrature and capacity
+ * fields are ignored), on `stream`.
+ *
+ * It allocates nothing: its cell list lives in one file-scope device array
+ * of the library, sized for at most GGEM_NOALLOC_MAX_POINTS sources and
+ * GGEM_NOALLOC_MAX_CELLS cells (about 5.4 MB, held on every GPU that loads
+ * the library until the process exits).  The first call on each device looks
+ * up that array's device address, so make it before any stream capture.
+ * Every call reuses the same array: calls that overlap on the GPU (different
+ * streams or threads) race and must be serialised by the caller.  The array
+ * keeps the last call's contents; each call clears the counters it needs.
+ *
+ * Arrays must be device pointers.  Returns GGEM_ERR_CAPACITY when n_src or
+ * the cell count exceeds the limits, GGEM_ERR_INVALID_ARG for bad sizes,
+ * geometry or host pointers (no message is recorded: there is no plan).
+ */
+#define GGEM_NOALLOC_MAX_POINTS 65536
+#define GGEM_NOALLOC_MAX_CELLS 32768
+ggem_status ggem_local_velocity_noalloc(const ggem_params *params, void *stream, int n_src,
+                                        const double *x_src, const double *g, int n_tgt,
+                                        const double *x_tgt, int tgt_is_src, double *u);
+
+/*
  * Tracing (no counterpart in the paper).  With tracing enabled, each stage
  * of an evaluation is bracketed by CUDA events on the plan's stream and the
  * host waits for its end, so per-stage device times can be read back; this

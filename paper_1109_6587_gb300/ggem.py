@@ -44,7 +44,8 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_mesh_set", "ggem_mesh_geometry", "ggem_point_forces", "ggem_local_sum",
            "ggem_single_layer",
            "ggem_double_layer", "ggem_trace_enable", "ggem_trace_stage_count",
-           "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count"]
+           "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count",
+           "ggem_local_velocity_noalloc"]
 
 
 def lib():
@@ -72,6 +73,8 @@ def lib():
         L.ggem_trace_stage_name.argtypes = [I]
         L.ggem_trace_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)]
         L.ggem_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_long)]
+        L.ggem_local_velocity_noalloc.argtypes = [ctypes.POINTER(ggem_params), P, I, P, P, I,
+                                                  P, I, P]
         for name in EXPORTS:
             getattr(L, name).restype = (ctypes.c_char_p if name in ("ggem_last_error",
                                                                     "ggem_trace_stage_name")
