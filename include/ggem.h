@@ -169,8 +169,9 @@ ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
  *
  * It allocates nothing: its cell list lives in one file-scope device array
  * of the library, sized for at most GGEM_NOALLOC_MAX_POINTS sources and
- * GGEM_NOALLOC_MAX_CELLS cells (about 5.4 MB, held on every GPU that loads
- * the library until the process exits).  The first call on each device looks
+ * GGEM_NOALLOC_MAX_CELLS cells (about 7.8 MB, held on every GPU that loads
+ * the library until the process exits); targets are taken in chunks of
+ * GGEM_NOALLOC_MAX_POINTS, so their number is not limited.  The first call on each device looks
  * up that array's device address, so make it before any stream capture.
  * Every call reuses the same array: calls that overlap on the GPU (different
  * streams or threads) race and must be serialised by the caller.  The array

@@ -10,74 +10,6 @@
 
 namespace ggem {
 
-template <typename T> __device__ __forceinline__ T d_exp2(T x);
-template <> __device__ __forceinline__ float d_exp2<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double d_exp2<double>(double x) { return exp(x); }
-
-// ---------------------------------------------------------------- spread
-// f(node) = - sum_s g_s rho_g(node - x_s*), |node - x_s*| < r_cut (Eq. stokes_gg).
-// One warp per source; lanes walk the source's bounding box of grid nodes.
-template <typename T>
-__global__ void __launch_bounds__(256) k_spread(GridGeom geo, const double* __restrict__ yj,
-                                                 int n, const double* __restrict__ x,
-                                                 const v4_t<T>* __restrict__ g,
-                                                 const int* __restrict__ perm,
-                                                 T* __restrict__ grid) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    int src = perm[warp];
-    double xs = x[3 * src], ys = x[3 * src + 1], zs = x[3 * src + 2];
-    v4_t<T> gs = g[warp];
-    const double rc = geo.rcut;
-    int ilo = (int)floor((xs - rc) / geo.dx), ihi = (int)ceil((xs + rc) / geo.dx);
-    int klo = (int)floor((zs - rc) / geo.dz), khi = (int)ceil((zs + rc) / geo.dz);
-    const int N = geo.Ny - 1;
-    const double pi = 3.14159265358979323846;
-    double yb = 2.0 * (ys - geo.y0) / geo.W - 1.0;
-    double yhi = fmin(1.0, yb + 2.0 * rc / geo.W), ylo = fmax(-1.0, yb - 2.0 * rc / geo.W);
-    int jlo = max(0, (int)floor(acos(yhi) * N / pi) - 1);
-    int jhi = min(N, (int)ceil(acos(ylo) * N / pi) + 1);
-    int nx = ihi - ilo + 1, nz = khi - klo + 1, ny = jhi - jlo + 1;
-    const T d0x = (T)(ilo * geo.dx - xs), d0z = (T)(klo * geo.dz - zs);
-    const T hx = (T)geo.dx, hz = (T)geo.dz;
-    const T al2 = (T)(geo.alpha * geo.alpha);
-    const T rc2 = (T)(rc * rc);
-    const T cn = (T)(geo.alpha * geo.alpha * geo.alpha / (pi * sqrt(pi)));
-    const size_t plane = (size_t)geo.Nz * geo.Nx;
-    int total = nx * nz * ny;
-    for (int idx = lane; idx < total; idx += 32) {
-        int i = idx % nx;
-        int rest = idx / nx;
-        int k = rest % nz;
-        int j = jlo + rest / nz;
-        T dxv = d0x + (T)i * hx, dzv = d0z + (T)k * hz;
-        T dyv = (T)(yj[j] - ys);
-        T r2 = dxv * dxv + dyv * dyv + dzv * dzv;
-        if (!(r2 < rc2)) continue;
-        T a2r2 = al2 * r2;
-        T rho = cn * d_exp2<T>(-a2r2) * ((T)2.5 - a2r2);
-        int ii = (ilo + i) % geo.Nx; ii += (ii < 0) ? geo.Nx : 0;
-        int kk = (klo + k) % geo.Nz; kk += (kk < 0) ? geo.Nz : 0;
-        T* p = grid + (size_t)j * 3 * plane + (size_t)kk * geo.Nx + ii;
-        atomicAdd(p, -gs.x * rho);
-        atomicAdd(p + plane, -gs.y * rho);
-        atomicAdd(p + 2 * plane, -gs.z * rho);
-    }
-}
-
-template <typename T>
-cudaError_t spread(const GridGeom& geo, const double* yj, int n, const double* x,
-                   const v4_t<T>* g_sorted, const int* perm, T* grid, cudaStream_t st) {
-    cudaMemsetAsync(grid, 0, (size_t)geo.Ny * 3 * geo.Nz * geo.Nx * sizeof(T), st);
-    if (n > 0) {
-        long threads = (long)n * 32;
-        k_spread<T><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(geo, yj, n, x, g_sorted,
-                                                                        perm, grid);
-    }
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ FFT
 template <typename T> struct Cx {
     using C = c2_t<T>;
@@ -432,8 +364,6 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
 }
 
 #define GGEM_INST_GRID(T)                                                                     \
-    template cudaError_t spread<T>(const GridGeom&, const double*, int, const double*,         \
-                                   const v4_t<T>*, const int*, T*, cudaStream_t);              \
     template cudaError_t fft_forward<T>(const GridGeom&, T*, int, const void*, const void*,    \
                                         cudaStream_t);                                         \
     template cudaError_t fft_inverse<T>(const GridGeom&, T*, int, const void*, const void*,    \

@@ -68,12 +68,16 @@ struct ggem_plan {
     void* d_tw_z = nullptr;            // complex T: [Nz/2]
     double* d_ksb = nullptr;           // [3][Ny][nmodes] p_b, phi_b, v_b coefficients
     double* d_minv = nullptr;          // [4][nmodes] inverse influence matrix
+    double* d_kscoef = nullptr;        // [3][Ny] recurrence coefficients
+    void* d_ydiff = nullptr;           // [Ny][Ny] T, y_j - y_k
 
     // workspaces
     void* d_gridA = nullptr;           // max(9,3)*Ny*Nz*Nx T
     void* d_gridB = nullptr;
     void* d_wall = nullptr;            // [2][3][Nz][Nx] T
-    double* d_ksw = nullptr;           // K8 scratch: [6][Ny][nmodes] complex double
+    void* d_ksw = nullptr;             // tau-solve scratch (see ks_modes)
+    double* d_thom = nullptr;          // [4][Ny][nmodes] Thomas factors
+    double* d_isq = nullptr;           // [2][nmodes]
     size_t grid_elems = 0;
 
     // point sources (sorted)
@@ -94,6 +98,10 @@ struct ggem_plan {
     double* d_in2 = nullptr;           // [cap][3]
     double* d_out0 = nullptr;          // [cap][3]
     double* d_out1 = nullptr;          // [cap][6]
+    int* d_tgt_cell = nullptr;         // [cap] located point targets
+    void* d_tgt_pos = nullptr;         // [cap] v4 T
+    int* d_wall_cell = nullptr;        // [2 Nz Nx] located wall nodes (plan lifetime)
+    void* d_wall_pos = nullptr;
 
     // mesh
     int n_nodes = 0, n_tris = 0, cap_tris = 0;
@@ -108,6 +116,10 @@ struct ggem_plan {
     int* d_mesh_perm = nullptr;
     int* d_mesh_start = nullptr;
     void* d_mesh_pos = nullptr;
+    int4* d_mesh_sdi = nullptr;        // spreading descriptors of the mesh nodes
+    void* d_mesh_sdf = nullptr;
+    int4* d_sdi = nullptr;             // spreading descriptors of free sources
+    void* d_sdf = nullptr;
 
     // tracing: per-stage device time (CUDA events on the plan's stream)
     bool prof = false;
@@ -136,14 +148,29 @@ enum TargetKind { TK_SORTED = 0, TK_POINTS = 1, TK_WALL = 2 };
 // out modes
 enum { OUT_U = 1, OUT_S = 2, OUT_DBL = 4 };
 
+// targets: TK_SORTED = the sorted sources themselves (output via perm);
+// TK_POINTS / TK_WALL = targets located by locate_targets (cell, offsets)
 template <typename T>
 cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
-                      int kind, int n_tgt, const double* x_tgt, const double* nrm_tgt,
-                      int out_mode, T* out, int out_stride, cudaStream_t st);
+                      int kind, int n_tgt, const int* tcell, const v4_t<T>* tpos,
+                      const double* nrm_tgt, int out_mode, T* out, int out_stride,
+                      cudaStream_t st);
 
+// locate targets: kind TK_POINTS (x[n][3]) or TK_WALL (the 2 Nz Nx wall nodes)
 template <typename T>
-cudaError_t spread(const GridGeom& geo, const double* yj, int n, const double* x,
-                   const v4_t<T>* g_sorted, const int* perm, T* grid, cudaStream_t st);
+cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int kind,
+                           const double* x, int* cell, v4_t<T>* pos, cudaStream_t st);
+
+// per-source spreading descriptors (once per source set), then
+// f = -sum g rho_g on the grid [Ny][3][Nz][Nx]; ydiff[j][k] = y_j - y_k
+template <typename T>
+cudaError_t spread_prepare(const GridGeom& geo, const double* yj, int n, const int* perm,
+                           const double* x, int4* di, v4_t<T>* df, cudaStream_t st);
+// work: scratch of 4 Ny Nz Nx T (interleaved accumulation buffer)
+template <typename T>
+cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, const T* ydiff,
+                   const SortedSources<T>& src, const int4* di, const v4_t<T>* df, T* grid,
+                   T* work, cudaStream_t st);
 
 template <typename T>
 cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
@@ -155,10 +182,13 @@ cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* t
 template <typename T>
 cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st);
 
+// per-mode tau solves; coef = mode-independent recurrence table [3][Ny];
+// thom = per-mode Thomas factors [4][Ny][nmodes], isq = [2][nmodes];
+// scratch = [5][2][Ny][nmodes] T, then (256-byte aligned) [3][2][Ny][nmodes] double
 template <typename T>
 cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
-                     const double* minv, double* scratch, int out_sel, T* ocoef,
-                     cudaStream_t st);
+                     const double* minv, const double* coef, const double* thom,
+                     const double* isq, void* scratch, int out_sel, T* ocoef, cudaStream_t st);
 
 // mode 0: velocity, out = local + interp - self_coef * wself * qself
 // mode 1: stress (6), out = local + interp

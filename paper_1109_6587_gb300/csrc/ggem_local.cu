@@ -130,146 +130,226 @@ cudaError_t gather_strengths(int n, const int* perm, const double* q, const doub
 }
 
 // ------------------------------------------------------------- local sum
+// Kernel constants in T, computed on the host so that the kernels execute no
+// FP64 instruction (GB300 issues FP64 at a small fraction of the FP32 rate).
+template <typename T> struct LocalConst {
+    T al, al2, rc2, c1, c2, c3, c4, fU, fS, hx, hy, hz;
+};
+
+template <typename T> LocalConst<T> local_const(const GridGeom& geo, const CellGrid& cg) {
+    const double sp = 1.7724538509055160273, pi = 3.14159265358979323846;
+    double a = geo.alpha;
+    LocalConst<T> k;
+    k.al = (T)a; k.al2 = (T)(a * a); k.rc2 = (T)(geo.rcut * geo.rcut);
+    k.c1 = (T)(2.0 * a / sp); k.c2 = (T)(12.0 * a / sp);
+    k.c3 = (T)(8.0 * a * a * a / sp); k.c4 = (T)(4.0 * a * a * a / sp);
+    k.fU = (T)(1.0 / (8.0 * pi * geo.mu)); k.fS = (T)(1.0 / (8.0 * pi));
+    k.hx = (T)cg.hx; k.hy = (T)cg.hy; k.hz = (T)cg.hz;
+    return k;
+}
+
 template <typename T> struct LocalArgs {
     GridGeom geo;
     CellGrid cg;
+    LocalConst<T> k;
     SortedSources<T> src;
     int n_tgt;
-    const double* x_tgt;     // TK_POINTS: [n][3] caller order
+    const int* tcell;        // TK_POINTS / TK_WALL: located targets (cell, offsets)
+    const v4_t<T>* tpos;
     const double* nrm;       // OUT_DBL: [n][3] target normals (caller order)
     T* out;
     int out_stride;
 };
 
-// u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
-// (unscaled here; the caller-facing factors are applied at the end).
-template <typename T, int KIND, int MODE>
-__global__ void __launch_bounds__(128) k_local(LocalArgs<T> a) {
+// Locate targets once (one thread each, FP64): cell index and offsets from
+// the cell corner in T.  kind TK_POINTS reads x[n][3]; TK_WALL generates the
+// wall grid nodes (x_i, y0 or y0+W, z_k), index = (wall * Nz + k) * Nx + i.
+template <typename T>
+__global__ void k_locate(GridGeom geo, CellGrid cg, int n, int kind, const double* __restrict__ x,
+                         int* __restrict__ cell, v4_t<T>* __restrict__ pos) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n_tgt) return;
+    if (t >= n) return;
+    double xx, yy, zz;
+    if (kind == TK_POINTS) {
+        xx = x[3 * t]; yy = x[3 * t + 1]; zz = x[3 * t + 2];
+    } else {
+        int nxz = geo.Nz * geo.Nx;
+        int w = t / nxz, rem = t - w * nxz;
+        int k = rem / geo.Nx, i = rem - k * geo.Nx;
+        xx = i * geo.dx; zz = k * geo.dz; yy = geo.y0 + w * geo.W;
+    }
+    int cx, cy, cz;
+    double ox, oy, oz;
+    locate(geo, cg, xx, yy, zz, cx, cy, cz, ox, oy, oz);
+    cell[t] = (cz * cg.ncy + cy) * cg.ncx + cx;
+    v4_t<T> p;
+    p.x = (T)ox; p.y = (T)oy; p.z = (T)oz; p.w = (T)0;
+    pos[t] = p;
+}
+
+template <typename T>
+cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int kind,
+                           const double* x, int* cell, v4_t<T>* pos, cudaStream_t st) {
+    if (n > 0) k_locate<T><<<(n + 255) / 256, 256, 0, st>>>(geo, cg, n, kind, x, cell, pos);
+    return cudaGetLastError();
+}
+
+// u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
+// (unscaled in the loop; the caller-facing factors are applied at the end).
+//
+// One warp per target.  Lane c < 27 looks up neighbour cell c; a warp scan
+// concatenates the 27 source ranges, and the lanes stride over the
+// concatenated list, so consecutive lanes load consecutive sorted sources
+// (coalesced float4 loads) whatever the cell sizes.  Partial sums are reduced
+// with warp shuffles.
+constexpr int LW = 8;   // warps (targets) per block
+
+template <typename T, int KIND, int MODE>
+__global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
+    __shared__ int s_base[LW][32];
+    __shared__ int s_end[LW][32];
+    __shared__ T s_sh[LW][27][3];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * LW + wid;
+    if (t >= a.n_tgt) return;                     // warp-uniform
     const CellGrid& cg = a.cg;
     int cx, cy, cz, oidx = t;
     T ox, oy, oz;
-    double wx = 0, wz = 0;
-    int wall = 0;
-    if (KIND == TK_SORTED) {
-        v4_t<T> p = a.src.pos[t];
+    {
+        v4_t<T> p;
+        int c;
+        if (KIND == TK_SORTED) {
+            p = a.src.pos[t];
+            c = a.src.cell[t];
+            oidx = a.src.perm[t];
+        } else {
+            p = a.tpos[t];
+            c = a.tcell[t];
+        }
         ox = p.x; oy = p.y; oz = p.z;
-        int c = a.src.cell[t];
         cx = c % cg.ncx;
         cy = (c / cg.ncx) % cg.ncy;
         cz = c / (cg.ncx * cg.ncy);
-        oidx = a.src.perm[t];
-    } else {
-        double xx, yy, zz;
-        if (KIND == TK_POINTS) {
-            xx = a.x_tgt[3 * t]; yy = a.x_tgt[3 * t + 1]; zz = a.x_tgt[3 * t + 2];
-        } else {
-            int nxz = a.geo.Nz * a.geo.Nx;
-            wall = t / nxz;
-            int rem = t - wall * nxz;
-            int k = rem / a.geo.Nx, i = rem - k * a.geo.Nx;
-            xx = i * a.geo.dx; zz = k * a.geo.dz;
-            yy = a.geo.y0 + wall * a.geo.W;
-            wx = i; wz = k;
-        }
-        double dox, doy, doz;
-        locate(a.geo, cg, xx, yy, zz, cx, cy, cz, dox, doy, doz);
-        ox = (T)dox; oy = (T)doy; oz = (T)doz;
     }
+    // neighbour cells: lane c < 27 -> offsets (c % 3 - 1, (c / 3) % 3 - 1, c / 9 - 1)
+    int cnt = 0, st = 0;
+    if (lane < 27) {
+        int dxc = lane % 3 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane / 9 - 1;
+        int cyy = cy + dyc;
+        if (cyy >= 0 && cyy < cg.ncy) {
+            int cxx = cx + dxc, czz = cz + dzc;
+            cxx += (cxx < 0) ? cg.ncx : 0;
+            cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
+            czz += (czz < 0) ? cg.ncz : 0;
+            czz -= (czz >= cg.ncz) ? cg.ncz : 0;
+            int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
+            st = a.src.cell_start[c];
+            cnt = a.src.cell_start[c + 1] - st;
+        }
+        s_sh[wid][lane][0] = -(T)dxc * a.k.hx + ox;
+        s_sh[wid][lane][1] = -(T)dyc * a.k.hy + oy;
+        s_sh[wid][lane][2] = -(T)dzc * a.k.hz + oz;
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    s_base[wid][lane] = st - (inc - cnt);         // source index = base + candidate index
+    s_end[wid][lane] = (lane < 27) ? inc : 0x7fffffff;
+    __syncwarp();
+
     T nx = 0, ny = 0, nz = 0;
     if (MODE & OUT_DBL) {
         nx = (T)a.nrm[3 * oidx]; ny = (T)a.nrm[3 * oidx + 1]; nz = (T)a.nrm[3 * oidx + 2];
     }
-    const T al = (T)a.geo.alpha, al2 = al * al;
-    const T rc2 = (T)(a.geo.rcut * a.geo.rcut);
-    const double sp = 1.7724538509055160273;
-    const T c1 = (T)(2.0 * a.geo.alpha / sp);
-    const T c2 = (T)(12.0 * a.geo.alpha / sp);
-    const T c3 = (T)(8.0 * a.geo.alpha * a.geo.alpha * a.geo.alpha / sp);
-    const T c4 = (T)(4.0 * a.geo.alpha * a.geo.alpha * a.geo.alpha / sp);
+    const T al = a.k.al, al2 = a.k.al2, rc2 = a.k.rc2;
+    const T c1 = a.k.c1, c2 = a.k.c2, c3 = a.k.c3, c4 = a.k.c4;
     T ux = 0, uy = 0, uz = 0;
     T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
-    const T hx = (T)cg.hx, hy = (T)cg.hy, hz = (T)cg.hz;
-    for (int dzc = -1; dzc <= 1; ++dzc) {
-        int czz = cz + dzc;
-        czz += (czz < 0) ? cg.ncz : 0;
-        czz -= (czz >= cg.ncz) ? cg.ncz : 0;
-        const T shz = -(T)dzc * hz + oz;
-        for (int dyc = -1; dyc <= 1; ++dyc) {
-            int cyy = cy + dyc;
-            if (cyy < 0 || cyy >= cg.ncy) continue;
-            const T shy = -(T)dyc * hy + oy;
-            for (int dxc = -1; dxc <= 1; ++dxc) {
-                int cxx = cx + dxc;
-                cxx += (cxx < 0) ? cg.ncx : 0;
-                cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
-                const T shx = -(T)dxc * hx + ox;
-                int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
-                int s0 = a.src.cell_start[c], s1 = a.src.cell_start[c + 1];
-                for (int s = s0; s < s1; ++s) {
-                    v4_t<T> p = a.src.pos[s];
-                    T dx = shx - p.x, dy = shy - p.y, dz = shz - p.z;
-                    T r2 = dx * dx + dy * dy + dz * dz;
-                    if (!(r2 < rc2 && r2 > (T)0)) continue;
-                    v4_t<T> g = a.src.g[s];
-                    T ir = d_rsqrt<T>(r2);
-                    T r = r2 * ir;
-                    T ec = d_erfc<T>(al * r);
-                    T ex = d_exp<T>(-al2 * r2);
-                    T xg = dx * g.x + dy * g.y + dz * g.z;
-                    if (MODE & OUT_U) {
-                        T A = ec * ir - c1 * ex;
-                        T B = (ec * ir * ir * ir + c1 * ex * ir * ir) * xg;
-                        ux += A * g.x + B * dx;
-                        uy += A * g.y + B * dy;
-                        uz += A * g.z + B * dz;
-                    }
-                    if (MODE & (OUT_S | OUT_DBL)) {
-                        T ir2 = ir * ir;
-                        T D = -(T)6 * ec * ir2 * ir2 * ir - c2 * ex * ir2 * ir2 - c3 * ex * ir2;
-                        T E = c4 * ex;
-                        if (MODE & OUT_S) {
-                            T Dx = D * xg;
-                            sxx += Dx * dx * dx + E * ((T)2 * g.x * dx + xg);
-                            syy += Dx * dy * dy + E * ((T)2 * g.y * dy + xg);
-                            szz += Dx * dz * dz + E * ((T)2 * g.z * dz + xg);
-                            sxy += Dx * dx * dy + E * (g.y * dx + g.x * dy);
-                            sxz += Dx * dx * dz + E * (g.z * dx + g.x * dz);
-                            syz += Dx * dy * dz + E * (g.z * dy + g.y * dz);
-                        } else {
-                            T xn = dx * nx + dy * ny + dz * nz;
-                            T gn = g.x * nx + g.y * ny + g.z * nz;
-                            T Dxn = D * xg * xn;
-                            ux += Dxn * dx + E * (dx * gn + g.x * xn + nx * xg);
-                            uy += Dxn * dy + E * (dy * gn + g.y * xn + ny * xg);
-                            uz += Dxn * dz + E * (dz * gn + g.z * xn + nz * xg);
-                        }
-                    }
-                }
+    int cell = 0;
+    for (int idx = lane; idx < total; idx += 32) {
+        while (idx >= s_end[wid][cell]) ++cell;
+        const int s = s_base[wid][cell] + idx;
+        v4_t<T> p = a.src.pos[s];
+        T dx = s_sh[wid][cell][0] - p.x, dy = s_sh[wid][cell][1] - p.y,
+          dz = s_sh[wid][cell][2] - p.z;
+        T r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < rc2 && r2 > (T)0)) continue;
+        v4_t<T> g = a.src.g[s];
+        T ir = d_rsqrt<T>(r2);
+        T r = r2 * ir;
+        T ec = d_erfc<T>(al * r);
+        T ex = d_exp<T>(-al2 * r2);
+        T xg = dx * g.x + dy * g.y + dz * g.z;
+        if (MODE & OUT_U) {
+            T A = ec * ir - c1 * ex;
+            T B = (ec * ir * ir * ir + c1 * ex * ir * ir) * xg;
+            ux += A * g.x + B * dx;
+            uy += A * g.y + B * dy;
+            uz += A * g.z + B * dz;
+        }
+        if (MODE & (OUT_S | OUT_DBL)) {
+            T ir2 = ir * ir;
+            T D = -(T)6 * ec * ir2 * ir2 * ir - c2 * ex * ir2 * ir2 - c3 * ex * ir2;
+            T E = c4 * ex;
+            if (MODE & OUT_S) {
+                T Dx = D * xg;
+                sxx += Dx * dx * dx + E * ((T)2 * g.x * dx + xg);
+                syy += Dx * dy * dy + E * ((T)2 * g.y * dy + xg);
+                szz += Dx * dz * dz + E * ((T)2 * g.z * dz + xg);
+                sxy += Dx * dx * dy + E * (g.y * dx + g.x * dy);
+                sxz += Dx * dx * dz + E * (g.z * dx + g.x * dz);
+                syz += Dx * dy * dz + E * (g.z * dy + g.y * dz);
+            } else {
+                T xn = dx * nx + dy * ny + dz * nz;
+                T gn = g.x * nx + g.y * ny + g.z * nz;
+                T Dxn = D * xg * xn;
+                ux += Dxn * dx + E * (dx * gn + g.x * xn + nx * xg);
+                uy += Dxn * dy + E * (dy * gn + g.y * xn + ny * xg);
+                uz += Dxn * dz + E * (dz * gn + g.z * xn + nz * xg);
             }
         }
     }
-    const double pi = 3.14159265358979323846;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (MODE & (OUT_U | OUT_DBL)) {
+            ux += __shfl_xor_sync(0xffffffffu, ux, o);
+            uy += __shfl_xor_sync(0xffffffffu, uy, o);
+            uz += __shfl_xor_sync(0xffffffffu, uz, o);
+        }
+        if (MODE & OUT_S) {
+            sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
+            sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
+            sxz += __shfl_xor_sync(0xffffffffu, sxz, o);
+            syy += __shfl_xor_sync(0xffffffffu, syy, o);
+            syz += __shfl_xor_sync(0xffffffffu, syz, o);
+            szz += __shfl_xor_sync(0xffffffffu, szz, o);
+        }
+    }
+    if (lane != 0) return;
     if (KIND == TK_WALL) {
         // global wall data u^g = -u^l (Sec. 3.2.2), layout [wall][c][Nz][Nx]
-        T f = (T)(-1.0 / (8.0 * pi * a.geo.mu));
-        size_t plane = (size_t)a.geo.Nz * a.geo.Nx;
-        size_t o = (size_t)(wall * 3) * plane + (size_t)wz * a.geo.Nx + (size_t)wx;
-        a.out[o] = f * ux;
-        a.out[o + plane] = f * uy;
-        a.out[o + 2 * plane] = f * uz;
+        const T f = -a.k.fU;
+        const int nxz = a.geo.Nz * a.geo.Nx;
+        const int wall = t / nxz, rem = t - wall * nxz;
+        T* o = a.out + (size_t)wall * 3 * nxz + rem;
+        o[0] = f * ux;
+        o[nxz] = f * uy;
+        o[2 * nxz] = f * uz;
         return;
     }
     T* o = a.out + (size_t)oidx * a.out_stride;
     int k = 0;
     if (MODE & (OUT_U | OUT_DBL)) {
-        T f = (T)(1.0 / (8.0 * pi * a.geo.mu));
+        const T f = a.k.fU;
         o[0] = f * ux; o[1] = f * uy; o[2] = f * uz;
         k = 3;
     }
     if (MODE & OUT_S) {
-        T f = (T)(1.0 / (8.0 * pi));
+        const T f = a.k.fS;
         o[k] = f * sxx; o[k + 1] = f * sxy; o[k + 2] = f * sxz;
         o[k + 3] = f * syy; o[k + 4] = f * syz; o[k + 5] = f * szz;
     }
@@ -277,7 +357,7 @@ __global__ void __launch_bounds__(128) k_local(LocalArgs<T> a) {
 
 template <typename T, int KIND>
 static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
-    dim3 b(128), g((a.n_tgt + 127) / 128);
+    dim3 b(LW * 32), g((a.n_tgt + LW - 1) / LW);
     switch (mode) {
         case OUT_U: k_local<T, KIND, OUT_U><<<g, b, 0, st>>>(a); break;
         case OUT_S: k_local<T, KIND, OUT_S><<<g, b, 0, st>>>(a); break;
@@ -289,10 +369,12 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
 
 template <typename T>
 cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
-                      int kind, int n_tgt, const double* x_tgt, const double* nrm_tgt,
-                      int out_mode, T* out, int out_stride, cudaStream_t st) {
+                      int kind, int n_tgt, const int* tcell, const v4_t<T>* tpos,
+                      const double* nrm_tgt, int out_mode, T* out, int out_stride,
+                      cudaStream_t st) {
     if (n_tgt <= 0) return cudaSuccess;
-    LocalArgs<T> a{geo, cg, src, n_tgt, x_tgt, nrm_tgt, out, out_stride};
+    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, n_tgt, tcell, tpos, nrm_tgt, out,
+                   out_stride};
     if (kind == TK_SORTED) launch_kind<T, TK_SORTED>(a, out_mode, st);
     else if (kind == TK_POINTS) launch_kind<T, TK_POINTS>(a, out_mode, st);
     else launch_kind<T, TK_WALL>(a, OUT_U, st);
@@ -305,8 +387,11 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
     template cudaError_t gather_strengths<T>(int, const int*, const double*, const double*,   \
                                              double, v4_t<T>*, cudaStream_t);                  \
     template cudaError_t local_sum<T>(const GridGeom&, const CellGrid&,                       \
-                                      const SortedSources<T>&, int, int, const double*,       \
-                                      const double*, int, T*, int, cudaStream_t);
+                                      const SortedSources<T>&, int, int, const int*,          \
+                                      const v4_t<T>*, const double*, int, T*, int,             \
+                                      cudaStream_t);                                           \
+    template cudaError_t locate_targets<T>(const GridGeom&, const CellGrid&, int, int,        \
+                                           const double*, int*, v4_t<T>*, cudaStream_t);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

@@ -33,11 +33,13 @@ constexpr size_t kOffCell = al256(kOffCursor + sizeof(int) * (kMaxCells + kMaxPo
 constexpr size_t kOffPerm = al256(kOffCell + sizeof(int) * kMaxPoints);
 constexpr size_t kOffPos = al256(kOffPerm + sizeof(int) * kMaxPoints);
 constexpr size_t kOffG = al256(kOffPos + sizeof(double4_32a) * kMaxPoints);
-constexpr size_t kBytes = al256(kOffG + sizeof(double4_32a) * kMaxPoints);
+constexpr size_t kOffTCell = al256(kOffG + sizeof(double4_32a) * kMaxPoints);
+constexpr size_t kOffTPos = al256(kOffTCell + sizeof(int) * kMaxPoints);
+constexpr size_t kBytes = al256(kOffTPos + sizeof(double4_32a) * kMaxPoints);
 
 }  // namespace
 
-// The scratch array (about 5.4 MB with the limits in ggem.h).
+// The scratch array (about 7.8 MB with the limits in ggem.h).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kBytes];
 
 namespace {
@@ -121,6 +123,8 @@ extern "C" ggem_status ggem_local_velocity_noalloc(const ggem_params* prm, void*
     int* perm = (int*)(base + kOffPerm);
     double4_32a* pos = (double4_32a*)(base + kOffPos);
     double4_32a* gs = (double4_32a*)(base + kOffG);
+    int* tcell = (int*)(base + kOffTCell);
+    double4_32a* tpos = (double4_32a*)(base + kOffTPos);
 
     // build_cells clears the counters it accumulates into (cell counts and
     // cursors) before use, so stale contents from an earlier call do not leak.
@@ -130,8 +134,21 @@ extern "C" ggem_status ggem_local_velocity_noalloc(const ggem_params* prm, void*
     if (gather_strengths<double>(n_src, perm, g, nullptr, 1.0, gs, st) != cudaSuccess)
         return GGEM_ERR_CUDA;
     SortedSources<double> src{pos, gs, cell, perm, start, n_src};
-    if (local_sum<double>(geo, cg, src, tgt_is_src ? TK_SORTED : TK_POINTS, n_tgt, x_tgt,
-                          nullptr, OUT_U, u, 3, st) != cudaSuccess)
-        return GGEM_ERR_CUDA;
+    if (tgt_is_src) {
+        if (local_sum<double>(geo, cg, src, TK_SORTED, n_tgt, nullptr, nullptr, nullptr, OUT_U,
+                              u, 3, st) != cudaSuccess)
+            return GGEM_ERR_CUDA;
+        return GGEM_OK;
+    }
+    // free targets, located in chunks that fit the scratch array
+    for (int t0 = 0; t0 < n_tgt; t0 += kMaxPoints) {
+        int nt = n_tgt - t0 < kMaxPoints ? n_tgt - t0 : kMaxPoints;
+        if (locate_targets<double>(geo, cg, nt, TK_POINTS, x_tgt + 3 * (size_t)t0, tcell, tpos,
+                                   st) != cudaSuccess)
+            return GGEM_ERR_CUDA;
+        if (local_sum<double>(geo, cg, src, TK_POINTS, nt, tcell, tpos, nullptr, OUT_U,
+                              u + 3 * (size_t)t0, 3, st) != cudaSuccess)
+            return GGEM_ERR_CUDA;
+    }
     return GGEM_OK;
 }

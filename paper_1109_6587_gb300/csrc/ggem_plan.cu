@@ -16,6 +16,8 @@ using namespace ggem;
 namespace ggem {
 void ks_precompute_mode(int Ny, double W, double mu, double k2, double* pb, double* phib,
                         double* vb, double* minv);
+void ks_coef_table(int Ny, double* tab);
+void ks_thomas_mode(int Ny, double lam, double* tab, double* isq);
 }
 
 namespace {
@@ -202,19 +204,20 @@ int nout_of(int sel) { return ((sel & 1) ? 3 : 0) + ((sel & 2) ? 6 : 0); }
 // Global part: wall data, spread, transforms, tau solves, inverse transforms.
 // The physical result is left in gridB as [Ny][nout][Nz][Nx].
 template <typename T>
-void run_global(ggem_plan_t* P, const SortedSources<T>& src, int n_src, const double* x_src,
-                int out_sel) {
+void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_sel) {
     const GridGeom& geo = P->geo;
     cudaStream_t st = P->st;
     T* A = (T*)P->d_gridA;
     T* B = (T*)P->d_gridB;
     T* Wl = (T*)P->d_wall;
     stage(P, ST_WALL, 1, [&] {
-        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_WALL, 2 * geo.Nz * geo.Nx, nullptr, nullptr,
-                             OUT_U, Wl, 0, st));
+        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_WALL, 2 * geo.Nz * geo.Nx, P->d_wall_cell,
+                             (const v4_t<T>*)P->d_wall_pos, nullptr, OUT_U, Wl, 0, st));
     });
-    stage(P, ST_SPREAD, 1, [&] {
-        GG_CUDA(spread<T>(geo, P->d_yj, n_src, x_src, src.g, src.perm, A, st));
+    stage(P, ST_SPREAD, 2, [&] {
+        GG_CUDA(spread<T>(geo, P->cg, P->d_yj, (const T*)P->d_ydiff, src,
+                          mesh ? P->d_mesh_sdi : P->d_sdi,
+                          (const v4_t<T>*)(mesh ? P->d_mesh_sdf : P->d_sdf), A, B, st));
     });
     stage(P, ST_FFT_FWD, 4, [&] {
         GG_CUDA(fft_forward<T>(geo, A, geo.Ny * 3, P->d_tw_x, P->d_tw_z, st));
@@ -225,7 +228,8 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, int n_src, const do
                               st));
     });
     stage(P, ST_KS, 1, [&] {
-        GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_ksw, out_sel, A, st));
+        GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom, P->d_isq,
+                            P->d_ksw, out_sel, A, st));
     });
     int nout = nout_of(out_sel);
     stage(P, ST_CHEB_INV, 1, [&] {
@@ -242,9 +246,11 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
                        const double* xt, int tgt_is_src, double* u, double* s) {
     const GridGeom& geo = P->geo;
     cudaStream_t st = P->st;
-    stage(P, ST_CELLS, 3, [&] {
+    stage(P, ST_CELLS, 4, [&] {
         GG_CUDA(build_cells<T>(geo, P->cg, n_src, xs, P->d_cell_count, P->d_cell_start,
                                P->d_cursor, P->d_src_cell, P->d_perm, (v4_t<T>*)P->d_spos, st));
+        GG_CUDA(spread_prepare<T>(geo, P->d_yj, n_src, P->d_perm, xs, P->d_sdi,
+                                  (v4_t<T>*)P->d_sdf, st));
     });
     stage(P, ST_GATHER, 1, [&] {
         GG_CUDA(gather_strengths<T>(n_src, P->d_perm, g, nullptr, 1.0, (v4_t<T>*)P->d_sg, st));
@@ -254,12 +260,16 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
     int mode = (u ? OUT_U : 0) | (s ? OUT_S : 0);
     int stride = (u ? 3 : 0) + (s ? 6 : 0);
     T* loc = (T*)P->d_local;
-    stage(P, ST_LOCAL, 1, [&] {
+    stage(P, ST_LOCAL, tgt_is_src ? 1 : 2, [&] {
+        if (!tgt_is_src)
+            GG_CUDA(locate_targets<T>(geo, P->cg, n_tgt, TK_POINTS, xt, P->d_tgt_cell,
+                                      (v4_t<T>*)P->d_tgt_pos, st));
         GG_CUDA(local_sum<T>(geo, P->cg, src, tgt_is_src ? TK_SORTED : TK_POINTS,
-                             tgt_is_src ? n_src : n_tgt, xt, nullptr, mode, loc, stride, st));
+                             tgt_is_src ? n_src : n_tgt, P->d_tgt_cell,
+                             (const v4_t<T>*)P->d_tgt_pos, nullptr, mode, loc, stride, st));
     });
     int sel = (u ? 1 : 0) | (s ? 2 : 0);
-    run_global<T>(P, src, n_src, xs, sel);
+    run_global<T>(P, src, false, sel);
     const double* xtt = tgt_is_src ? xs : xt;
     int nt = tgt_is_src ? n_src : n_tgt;
     int nout = nout_of(sel);
@@ -298,9 +308,11 @@ void local_only_impl(ggem_plan_t* P, int n_src, const double* xs, const double* 
                      const double* xt, int tgt_is_src, double* u, double* s) {
     const GridGeom& geo = P->geo;
     cudaStream_t st = P->st;
-    stage(P, ST_CELLS, 3, [&] {
+    stage(P, ST_CELLS, 4, [&] {
         GG_CUDA(build_cells<T>(geo, P->cg, n_src, xs, P->d_cell_count, P->d_cell_start,
                                P->d_cursor, P->d_src_cell, P->d_perm, (v4_t<T>*)P->d_spos, st));
+        GG_CUDA(spread_prepare<T>(geo, P->d_yj, n_src, P->d_perm, xs, P->d_sdi,
+                                  (v4_t<T>*)P->d_sdf, st));
     });
     stage(P, ST_GATHER, 1, [&] {
         GG_CUDA(gather_strengths<T>(n_src, P->d_perm, g, nullptr, 1.0, (v4_t<T>*)P->d_sg, st));
@@ -311,9 +323,13 @@ void local_only_impl(ggem_plan_t* P, int n_src, const double* xs, const double* 
     int stride = (u ? 3 : 0) + (s ? 6 : 0);
     int nt = tgt_is_src ? n_src : n_tgt;
     T* loc = (T*)P->d_local;
-    stage(P, ST_LOCAL, 2, [&] {
-        GG_CUDA(local_sum<T>(geo, P->cg, src, tgt_is_src ? TK_SORTED : TK_POINTS, nt, xt,
-                             nullptr, mode, loc, stride, st));
+    stage(P, ST_LOCAL, tgt_is_src ? 2 : 3, [&] {
+        if (!tgt_is_src)
+            GG_CUDA(locate_targets<T>(geo, P->cg, nt, TK_POINTS, xt, P->d_tgt_cell,
+                                      (v4_t<T>*)P->d_tgt_pos, st));
+        GG_CUDA(local_sum<T>(geo, P->cg, src, tgt_is_src ? TK_SORTED : TK_POINTS, nt,
+                             P->d_tgt_cell, (const v4_t<T>*)P->d_tgt_pos, nullptr, mode, loc,
+                             stride, st));
         if (nt > 0) k_split_local<T><<<(nt + 255) / 256, 256, 0, st>>>(nt, loc, stride, u, s);
         GG_CUDA(cudaGetLastError());
     });
@@ -332,10 +348,10 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
     src.n = n;
     T* loc = (T*)P->d_local;
     stage(P, ST_LOCAL, 1, [&] {
-        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, P->d_nrm,
+        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, nullptr, P->d_nrm,
                              layer == 0 ? OUT_U : OUT_DBL, loc, 3, st));
     });
-    run_global<T>(P, src, n, P->d_x, layer == 0 ? 1 : 2);
+    run_global<T>(P, src, true, layer == 0 ? 1 : 2);
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
             double sc = 4.0 * geo.alpha / std::sqrt(kPi);   // (4 alpha/sqrt(pi)) A_b q_b
@@ -425,24 +441,46 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     }
     dalloc(P, &P->d_yj, Ny);
     GG_CUDA(cudaMemcpy(P->d_yj, yj.data(), Ny * sizeof(double), cudaMemcpyHostToDevice));
+    {
+        std::vector<double> yd((size_t)Ny * Ny);
+        for (int j = 0; j < Ny; ++j)
+            for (int k = 0; k < Ny; ++k) yd[(size_t)j * Ny + k] = yj[j] - yj[k];
+        if (prm.precision == GGEM_FP64) {
+            dalloc(P, (double**)&P->d_ydiff, yd.size());
+            GG_CUDA(cudaMemcpy(P->d_ydiff, yd.data(), yd.size() * sizeof(double),
+                               cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> yf(yd.begin(), yd.end());
+            dalloc(P, (float**)&P->d_ydiff, yf.size());
+            GG_CUDA(cudaMemcpy(P->d_ydiff, yf.data(), yf.size() * sizeof(float),
+                               cudaMemcpyHostToDevice));
+        }
+    }
     if (P->fp64) upload_tables<double>(P, cf, ci, twx, twz);
     else upload_tables<float>(P, cf, ci, twx, twz);
 
     // per-mode homogeneous solutions and inverse influence matrices (App. C)
     const int nm = P->nmodes;
     std::vector<double> ksb((size_t)3 * Ny * nm, 0.0), minv((size_t)4 * nm, 0.0);
+    std::vector<double> thom((size_t)4 * Ny * nm, 0.0), isq((size_t)2 * nm, 0.0);
 #pragma omp parallel
     {
-        std::vector<double> pb(Ny), ph(Ny), vb(Ny);
-        double mi[4];
+        std::vector<double> pb(Ny), ph(Ny), vb(Ny), th(4 * Ny);
+        double mi[4], iq[2];
 #pragma omp for schedule(dynamic, 64)
         for (int m = 0; m < nm; ++m) {
             int kzi = m / g.nkx, kxi = m % g.nkx;
-            if (m == 0 || kzi == prm.Nz / 2) continue;
+            if (kzi == prm.Nz / 2) continue;
             int mz = kzi < prm.Nz / 2 ? kzi : kzi - prm.Nz;
             double kx = 2 * kPi * kxi / prm.Lx, kz = 2 * kPi * mz / prm.Lz;
-            ks_precompute_mode(Ny, prm.W, prm.mu, kx * kx + kz * kz, pb.data(), ph.data(),
-                               vb.data(), mi);
+            double k2 = kx * kx + kz * kz;
+            ks_thomas_mode(Ny, k2 * 0.25 * prm.W * prm.W, th.data(), iq);
+            for (int c = 0; c < 4; ++c)
+                for (int n = 0; n < Ny; ++n) thom[((size_t)c * Ny + n) * nm + m] = th[c * Ny + n];
+            isq[m] = iq[0];
+            isq[nm + m] = iq[1];
+            if (m == 0) continue;
+            ks_precompute_mode(Ny, prm.W, prm.mu, k2, pb.data(), ph.data(), vb.data(), mi);
             for (int n = 0; n < Ny; ++n) {
                 ksb[((size_t)0 * Ny + n) * nm + m] = pb[n];
                 ksb[((size_t)1 * Ny + n) * nm + m] = ph[n];
@@ -451,6 +489,12 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             for (int c = 0; c < 4; ++c) minv[(size_t)c * nm + m] = mi[c];
         }
     }
+    dalloc(P, &P->d_thom, thom.size());
+    dalloc(P, &P->d_isq, isq.size());
+    GG_CUDA(cudaMemcpy(P->d_thom, thom.data(), thom.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_isq, isq.data(), isq.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
     dalloc(P, &P->d_ksb, ksb.size());
     dalloc(P, &P->d_minv, minv.size());
     GG_CUDA(cudaMemcpy(P->d_ksb, ksb.data(), ksb.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -463,7 +507,18 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     GG_CUDA(cudaMalloc(&P->d_gridA, P->grid_elems * esz));
     GG_CUDA(cudaMalloc(&P->d_gridB, P->grid_elems * esz));
     GG_CUDA(cudaMalloc(&P->d_wall, (size_t)6 * prm.Nz * prm.Nx * esz));
-    dalloc(P, &P->d_ksw, (size_t)7 * 2 * Ny * nm);
+    {
+        size_t naux = (size_t)5 * 2 * Ny * nm * esz;
+        size_t nbytes = ((naux + 255) & ~(size_t)255) + (size_t)3 * 2 * Ny * nm * sizeof(double);
+        GG_CUDA(cudaMalloc(&P->d_ksw, nbytes));
+    }
+    {
+        std::vector<double> tab(3 * Ny);
+        ks_coef_table(Ny, tab.data());
+        dalloc(P, &P->d_kscoef, tab.size());
+        GG_CUDA(cudaMemcpy(P->d_kscoef, tab.data(), tab.size() * sizeof(double),
+                           cudaMemcpyHostToDevice));
+    }
     int cap = prm.max_points;
     P->cap = cap;
     dalloc(P, &P->d_cell_count, P->ncell);
@@ -480,6 +535,23 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     dalloc(P, &P->d_in2, (size_t)cap * 3);
     dalloc(P, &P->d_out0, (size_t)cap * 3);
     dalloc(P, &P->d_out1, (size_t)cap * 6);
+    dalloc(P, &P->d_tgt_cell, cap);
+    dalloc(P, &P->d_sdi, cap);
+    dalloc(P, &P->d_mesh_sdi, cap);
+    GG_CUDA(cudaMalloc(&P->d_sdf, cap * v4 + 32));
+    GG_CUDA(cudaMalloc(&P->d_mesh_sdf, cap * v4 + 32));
+    GG_CUDA(cudaMalloc(&P->d_tgt_pos, cap * v4 + 32));
+    {
+        int nw = 2 * prm.Nz * prm.Nx;
+        dalloc(P, &P->d_wall_cell, nw);
+        GG_CUDA(cudaMalloc(&P->d_wall_pos, nw * v4 + 32));
+        if (P->fp64)
+            GG_CUDA(locate_targets<double>(g, cg, nw, TK_WALL, nullptr, P->d_wall_cell,
+                                           (double4_32a*)P->d_wall_pos, nullptr));
+        else
+            GG_CUDA(locate_targets<float>(g, cg, nw, TK_WALL, nullptr, P->d_wall_cell,
+                                          (float4*)P->d_wall_pos, nullptr));
+    }
     // mesh tables
     P->cap_tris = prm.max_tris;
     dalloc(P, &P->d_x, (size_t)cap * 3);
@@ -503,11 +575,13 @@ void plan_free(ggem_plan_t* P) {
     if (P->ev0) cudaEventDestroy(P->ev0);
     if (P->ev1) cudaEventDestroy(P->ev1);
     void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
-                    P->d_minv, P->d_gridA, P->d_gridB, P->d_wall, P->d_ksw, P->d_cell_count,
+                    P->d_minv, P->d_ydiff, P->d_sdi, P->d_sdf, P->d_mesh_sdi, P->d_mesh_sdf,
+                    P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall, P->d_ksw, P->d_cell_count,
                     P->d_cell_start, P->d_cursor, P->d_src_cell, P->d_perm, P->d_spos, P->d_sg,
-                    P->d_src_x, P->d_local, P->d_in0, P->d_in1, P->d_in2, P->d_out0, P->d_out1, P->d_x,
-                    P->d_tri, P->d_area, P->d_nrm, P->d_tri_area, P->d_tri_nrm,
-                    P->d_mesh_cell, P->d_mesh_perm, P->d_mesh_start, P->d_mesh_pos};
+                    P->d_src_x, P->d_local, P->d_in0, P->d_in1, P->d_in2, P->d_out0, P->d_out1,
+                    P->d_tgt_cell, P->d_tgt_pos, P->d_wall_cell, P->d_wall_pos, P->d_x,
+                    P->d_tri, P->d_area, P->d_nrm, P->d_tri_area, P->d_tri_nrm, P->d_mesh_cell,
+                    P->d_mesh_perm, P->d_mesh_start, P->d_mesh_pos};
     for (void* p : ptrs) dfree(p);
 }
 
@@ -589,14 +663,19 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
             k_normalize<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, P->d_nrm);
         }
         GG_CUDA(cudaGetLastError());
-        if (P->fp64)
+        if (P->fp64) {
             GG_CUDA(build_cells<double>(P->geo, P->cg, n_nodes, P->d_x, P->d_cell_count,
                                         P->d_mesh_start, P->d_cursor, P->d_mesh_cell,
                                         P->d_mesh_perm, (double4_32a*)P->d_mesh_pos, st));
-        else
+            GG_CUDA(spread_prepare<double>(P->geo, P->d_yj, n_nodes, P->d_mesh_perm, P->d_x,
+                                           P->d_mesh_sdi, (double4_32a*)P->d_mesh_sdf, st));
+        } else {
             GG_CUDA(build_cells<float>(P->geo, P->cg, n_nodes, P->d_x, P->d_cell_count,
                                        P->d_mesh_start, P->d_cursor, P->d_mesh_cell,
                                        P->d_mesh_perm, (float4*)P->d_mesh_pos, st));
+            GG_CUDA(spread_prepare<float>(P->geo, P->d_yj, n_nodes, P->d_mesh_perm, P->d_x,
+                                          P->d_mesh_sdi, (float4*)P->d_mesh_sdf, st));
+        }
         P->n_nodes = n_nodes;
         P->n_tris = n_tris;
         P->mesh_ready = true;

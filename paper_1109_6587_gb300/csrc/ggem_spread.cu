@@ -1,0 +1,209 @@
+// Spreading of the global density onto the grid (paper Eqs. (stokes_gg),
+// (rho_int), (rhog_sum)):
+//   f(node) = - sum_s g_s rho_g(node - x_s*),   |node - x_s*| < r_cut,
+//   rho_g(r) = alpha^3 pi^{-3/2} exp(-alpha^2 r^2) (5/2 - alpha^2 r^2).
+//
+// Output-stationary: a block owns a tile of TS x TS grid columns (x, z) over a
+// slab of NS y-planes, accumulates in shared memory every source whose r_cut
+// ball reaches those nodes, and writes them once with plain stores (no global
+// atomics, no clearing pass).  One warp per candidate source: lane l tests
+// column i0 + l and row k0 + l once (ballot), then the warp walks only the
+// (column, row) pairs inside the source's disc, for the slab's planes.  The
+// Gaussian factor is separable, exp(-a^2 r^2) = exp(-a^2 dx^2)
+// exp(-a^2 dy^2) exp(-a^2 dz^2), so each source costs one exponential per
+// column, row and plane.  Displacements come from per-source descriptors
+// (integer grid offsets plus small remainders, built once per source set), so
+// the kernel runs in T only: no FP64 instruction, accurate in large boxes.
+#include "ggem_internal.cuh"
+
+namespace ggem {
+
+namespace {
+
+// Per-source descriptor for spreading, computed once per source set (one
+// thread per sorted source, FP64): ixb = floor(x/dx) of the wrapped x,
+// rx = x - ixb dx; the same for z; jn = nearest Chebyshev node, ry = y - y_jn;
+// [jlo, jhi] = a superset of the nodes with |y_j - y| < r_cut.
+template <typename T>
+__global__ void k_src_desc(GridGeom geo, const double* __restrict__ yj, int n,
+                           const int* __restrict__ perm, const double* __restrict__ x,
+                           int4* __restrict__ di, v4_t<T>* __restrict__ df) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int src = perm[s];
+    double xs = x[3 * src], ys = x[3 * src + 1], zs = x[3 * src + 2];
+    xs -= geo.Lx * floor(xs / geo.Lx);
+    zs -= geo.Lz * floor(zs / geo.Lz);
+    int ixb = min((int)floor(xs / geo.dx), geo.Nx - 1);
+    int izb = min((int)floor(zs / geo.dz), geo.Nz - 1);
+    const int N = geo.Ny - 1;
+    const double pi = 3.14159265358979323846, rc = geo.rcut;
+    double yb = fmin(1.0, fmax(-1.0, 2.0 * (ys - geo.y0) / geo.W - 1.0));
+    int jn = min(max((int)rint(acos(yb) * N / pi), 0), N);
+    double yh = fmin(1.0, yb + 2.0 * rc / geo.W), yl = fmax(-1.0, yb - 2.0 * rc / geo.W);
+    int jlo = max(0, (int)floor(acos(yh) * N / pi) - 1);
+    int jhi = min(N, (int)ceil(acos(yl) * N / pi) + 1);
+    di[s] = make_int4(ixb, izb, jn, jlo | (jhi << 16));
+    v4_t<T> f;
+    f.x = (T)(xs - ixb * geo.dx);
+    f.y = (T)(zs - izb * geo.dz);
+    f.z = (T)(ys - yj[jn]);
+    f.w = (T)0;
+    df[s] = f;
+}
+
+template <typename T> __device__ __forceinline__ T sexp(T x);
+template <> __device__ __forceinline__ float sexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double sexp<double>(double x) { return exp(x); }
+
+// per-kernel constants in T (computed on the host)
+template <typename T> struct SpreadConst {
+    T dx, dz, rc2, al2, cn;
+};
+
+constexpr int SW = 8;         // warps (sources) per block
+constexpr int MAXJ = 272;     // max y nodes of one source stencil (checked on the host)
+constexpr int MAXR = 32;      // max columns / rows of one source's stencil
+
+// vector reduction into an interleaved (x, y, z, pad) node
+__device__ __forceinline__ void red4(float* p, float a, float b, float c) {
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, 0.f));
+}
+__device__ __forceinline__ void red4(double* p, double a, double b, double c) {
+    atomicAdd(p, a);
+    atomicAdd(p + 1, b);
+    atomicAdd(p + 2, c);
+}
+
+// One warp per source.  The source's stencil is the set of nodes within r_cut:
+// columns i with dx^2 < rc^2, rows k with dz^2 < rc^2, planes j in its y-range.
+// Lanes build the separable factors e_x, e_z, e_y in shared memory, then walk
+// the (column, row) pairs of the disc; each lane runs the planes of its pair
+// with dy^2 < rc^2 - dx^2 - dz^2 and adds into the interleaved buffer with one
+// vector reduction per node.
+template <typename T>
+__global__ void __launch_bounds__(SW * 32) k_spread_scatter(
+    GridGeom geo, SpreadConst<T> kc, const T* __restrict__ ydiff, int n, int R,
+    const int4* __restrict__ sdi, const v4_t<T>* __restrict__ sdf,
+    const v4_t<T>* __restrict__ gsrc, T* __restrict__ f4) {
+    __shared__ T s_xd2[SW][MAXR], s_xe[SW][MAXR], s_zd2[SW][MAXR], s_ze[SW][MAXR];
+    __shared__ int s_xi[SW][MAXR], s_zi[SW][MAXR];
+    __shared__ T s_yd2[SW][MAXJ], s_ye[SW][MAXJ];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * SW + wid;
+    if (s >= n) return;                            // warp-uniform
+    const T rc2 = kc.rc2, al2 = kc.al2;
+    const int4 di = sdi[s];
+    const v4_t<T> df = sdf[s];
+    const v4_t<T> g = gsrc[s];
+    const int mNx = geo.Nx - 1, mNz = geo.Nz - 1;
+    const int nr = 2 * R + 2;                      // candidate offsets -R .. R+1
+    // columns and rows within r_cut (lane = offset index)
+    T dx2 = (T)1e30, dz2 = (T)1e30;
+    if (lane < nr) {
+        T vx = fma((T)(lane - R), kc.dx, -df.x);
+        T vz = fma((T)(lane - R), kc.dz, -df.y);
+        dx2 = vx * vx;
+        dz2 = vz * vz;
+    }
+    const unsigned mx = __ballot_sync(0xffffffffu, dx2 < rc2);
+    const unsigned mz = __ballot_sync(0xffffffffu, dz2 < rc2);
+    const unsigned lt = (1u << lane) - 1u;
+    if (dx2 < rc2) {
+        int rk = __popc(mx & lt);
+        s_xd2[wid][rk] = dx2;
+        s_xe[wid][rk] = sexp<T>(-al2 * dx2);
+        s_xi[wid][rk] = (di.x + lane - R) & mNx;
+    }
+    if (dz2 < rc2) {
+        int rk = __popc(mz & lt);
+        s_zd2[wid][rk] = dz2;
+        s_ze[wid][rk] = sexp<T>(-al2 * dz2);
+        s_zi[wid][rk] = (di.y + lane - R) & mNz;
+    }
+    // planes of the y-range
+    const int jlo = di.w & 0xffff, jhi = di.w >> 16, ny = jhi - jlo + 1;
+    const T* yrow = ydiff + di.z;
+    for (int q = lane; q < ny; q += 32) {
+        T d = yrow[(size_t)(jlo + q) * geo.Ny] - df.z;
+        T d2 = d * d;
+        s_yd2[wid][q] = d2;
+        s_ye[wid][q] = sexp<T>(-al2 * d2);
+    }
+    __syncwarp();
+    const T gx = -kc.cn * g.x, gy = -kc.cn * g.y, gz = -kc.cn * g.z;
+    const int nxs = __popc(mx), nzs = __popc(mz), npair = nxs * nzs;
+    const float inx = 1.0f / (float)nxs;
+    const size_t rowst = (size_t)geo.Nx * 4, planest = (size_t)geo.Nz * geo.Nx * 4;
+    for (int pi = lane; pi < npair; pi += 32) {
+        int b = (int)(((float)pi + 0.5f) * inx);
+        int a = pi - b * nxs;
+        T dxz = s_xd2[wid][a] + s_zd2[wid][b];
+        if (!(dxz < rc2)) continue;
+        T exz = s_xe[wid][a] * s_ze[wid][b];
+        T* col = f4 + (size_t)s_zi[wid][b] * rowst + (size_t)s_xi[wid][a] * 4;
+        for (int q = 0; q < ny; ++q) {
+            T r2 = dxz + s_yd2[wid][q];
+            if (!(r2 < rc2)) continue;
+            T w = exz * s_ye[wid][q] * ((T)2.5 - al2 * r2);
+            red4(col + (size_t)(jlo + q) * planest, gx * w, gy * w, gz * w);
+        }
+    }
+}
+
+// interleaved [Ny][Nz][Nx][4] -> planar [Ny][3][Nz][Nx]
+template <typename T>
+__global__ void k_deinterleave(int Ny, int Nz, int Nx, const T* __restrict__ f4,
+                               T* __restrict__ grid) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t plane = (size_t)Nz * Nx;
+    if (e >= (size_t)Ny * plane) return;
+    size_t j = e / plane, r = e - j * plane;
+    const T* p = f4 + e * 4;
+    T* o = grid + j * 3 * plane + r;
+    o[0] = p[0];
+    o[plane] = p[1];
+    o[2 * plane] = p[2];
+}
+}  // namespace
+
+template <typename T>
+cudaError_t spread_prepare(const GridGeom& geo, const double* yj, int n, const int* perm,
+                           const double* x, int4* di, v4_t<T>* df, cudaStream_t st) {
+    if (n > 0) k_src_desc<T><<<(n + 255) / 256, 256, 0, st>>>(geo, yj, n, perm, x, di, df);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, const T* ydiff,
+                   const SortedSources<T>& src, const int4* di, const v4_t<T>* df, T* grid,
+                   T* work, cudaStream_t st) {
+    (void)cg; (void)yj;
+    int R = (int)std::ceil(std::max(geo.rcut / geo.dx, geo.rcut / geo.dz)) + 1;
+    if (2 * R + 2 > MAXR || geo.Ny > MAXJ) return cudaErrorInvalidConfiguration;
+    const double pi = 3.14159265358979323846;
+    SpreadConst<T> kc;
+    kc.dx = (T)geo.dx; kc.dz = (T)geo.dz;
+    kc.rc2 = (T)(geo.rcut * geo.rcut);
+    kc.al2 = (T)(geo.alpha * geo.alpha);
+    kc.cn = (T)(geo.alpha * geo.alpha * geo.alpha / (pi * std::sqrt(pi)));
+    size_t nodes = (size_t)geo.Ny * geo.Nz * geo.Nx;
+    cudaMemsetAsync(work, 0, nodes * 4 * sizeof(T), st);
+    if (src.n > 0)
+        k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(geo, kc, ydiff, src.n, R,
+                                                                      di, df, src.g, work);
+    k_deinterleave<T><<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(geo.Ny, geo.Nz, geo.Nx,
+                                                                       work, grid);
+    return cudaGetLastError();
+}
+
+#define GGEM_INST_SPREAD(T)                                                                  \
+    template cudaError_t spread_prepare<T>(const GridGeom&, const double*, int, const int*,    \
+                                           const double*, int4*, v4_t<T>*, cudaStream_t);       \
+    template cudaError_t spread<T>(const GridGeom&, const CellGrid&, const double*, const T*,   \
+                                   const SortedSources<T>&, const int4*, const v4_t<T>*, T*,    \
+                                   T*, cudaStream_t);
+GGEM_INST_SPREAD(float)
+GGEM_INST_SPREAD(double)
+
+}  // namespace ggem
