@@ -47,6 +47,13 @@ template <typename T> struct SortedSources {
     int n;
 };
 
+// 4x4 Gauss-Legendre product rule on [0,1]^2 and the polar-rule angles
+struct QuadRule {
+    double t[4], w[4];                // nodes and weights on [0,1]
+    double th[4], cth[4], sth[4];     // theta_a = (pi/2) t_a, cos, sin
+    double rmax[4], wth[4];           // 1/(cos + sin), (pi/2) w_a
+};
+
 }  // namespace ggem
 
 // ----------------------------------------------------------------- the plan
@@ -121,6 +128,26 @@ struct ggem_plan {
     int4* d_sdi = nullptr;             // spreading descriptors of free sources
     void* d_sdf = nullptr;
 
+    // element quadrature (16 points per triangle)
+    ggem::QuadRule rule;
+    int cap_qp = 0, n_qp = 0;
+    double* d_qx = nullptr;            // [cap_qp][3] point positions
+    int4* d_qv = nullptr;              // [cap_qp] triangle vertices
+    int4* d_qv_sorted = nullptr;       // [cap_qp] the same, in sorted point order
+    double near_edge = 0.0;            // longest triangle edge of the mesh
+    void* d_qw = nullptr;              // [cap_qp] v4 T: phi_v * weight
+    int* d_qp_cell = nullptr;          // sorted points: cell / perm / offsets / start
+    int* d_qp_perm = nullptr;
+    int* d_qp_start = nullptr;
+    void* d_qp_pos = nullptr;
+    void* d_qg = nullptr;              // [cap_qp] v4 T sorted strengths
+    int* d_adj_cnt = nullptr;          // node -> triangle adjacency (CSR)
+    int* d_adj_start = nullptr;
+    int* d_adj_cur = nullptr;
+    int* d_adj = nullptr;
+    int* d_node_cell = nullptr;        // mesh nodes located in caller order
+    void* d_node_pos = nullptr;
+
     // tracing: per-stage device time (CUDA events on the plan's stream)
     bool prof = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -155,6 +182,36 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
                       int kind, int n_tgt, const int* tcell, const v4_t<T>* tpos,
                       const double* nrm_tgt, int out_mode, T* out, int out_stride,
                       cudaStream_t st);
+
+// element rule: local sum over sorted quadrature points at located mesh nodes
+// (caller index), skipping points of triangles that contain the target
+// (only tested when closer than `near`); layer 0 velocity, 1 double layer
+template <typename T>
+cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
+                           const int4* qvs, double near, int n_tgt, const int* tcell,
+                           const v4_t<T>* tpos, const double* nrm_tgt, int layer, T* out,
+                           int out_stride, cudaStream_t st);
+cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st);
+
+// exclusive scan of count[0..n) into start[0..n] (start[n] = total)
+cudaError_t scan_counts(int n, const int* count, int* start, cudaStream_t st);
+
+QuadRule make_quad_rule();
+// quadrature points of m triangles and the node -> triangle adjacency
+template <typename T>
+cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri_area,
+                       const QuadRule& rule, double* xq, int4* qv, v4_t<T>* qw, int nnodes,
+                       int* adj_cnt, int* adj_start, int* adj_cur, int* adj, cudaStream_t st);
+// sorted point strengths g = scale sum_v (phi_v w) q_v
+template <typename T>
+cudaError_t qp_strengths(int nq, const int* perm, const int4* qv, const v4_t<T>* qw,
+                         const double* q, double scale, v4_t<T>* g, cudaStream_t st);
+// polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double)
+template <typename T>
+cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x, const int* tri,
+                         const double* tri_nrm, const double* nrm, const int* adj_start,
+                         const int* adj, const double* q, const QuadRule& rule, T* out,
+                         int out_stride, cudaStream_t st);
 
 // locate targets: kind TK_POINTS (x[n][3]) or TK_WALL (the 2 Nz Nx wall nodes)
 template <typename T>

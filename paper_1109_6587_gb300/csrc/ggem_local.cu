@@ -89,6 +89,22 @@ __global__ void k_cell_scatter(GridGeom geo, CellGrid cg, int n, const double* _
     pos[slot] = p;
 }
 
+__global__ void k_gather_int4(int n, const int* __restrict__ perm, const int4* __restrict__ in,
+                              int4* __restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) out[s] = in[perm[s]];
+}
+
+cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st) {
+    if (n > 0) k_gather_int4<<<(n + 255) / 256, 256, 0, st>>>(n, perm, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_counts(int n, const int* count, int* start, cudaStream_t st) {
+    if (n > 0) k_scan<<<1, 1024, 0, st>>>(n, count, start);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t build_cells(const GridGeom& geo, const CellGrid& cg, int n, const double* x,
                         int* cell_count, int* cell_start, int* cursor, int* src_cell,
@@ -153,6 +169,8 @@ template <typename T> struct LocalArgs {
     CellGrid cg;
     LocalConst<T> k;
     SortedSources<T> src;
+    const int4* qvs;         // element rule: vertices of each sorted point's triangle
+    T near2;                 // element rule: points closer than this may share a triangle
     int n_tgt;
     const int* tcell;        // TK_POINTS / TK_WALL: located targets (cell, offsets)
     const v4_t<T>* tpos;
@@ -204,7 +222,10 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
 // with warp shuffles.
 constexpr int LW = 8;   // warps (targets) per block
 
-template <typename T, int KIND, int MODE>
+// ELEM: sources are element quadrature points and targets are mesh nodes
+// (caller index t); points of triangles having the target as a vertex are
+// skipped (their integral is done by the polar rule, Sec. 3.4.1).
+template <typename T, int KIND, int MODE, bool ELEM = false>
 __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     __shared__ int s_base[LW][32];
     __shared__ int s_end[LW][32];
@@ -278,6 +299,10 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
           dz = s_sh[wid][cell][2] - p.z;
         T r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < rc2 && r2 > (T)0)) continue;
+        if (ELEM && r2 < a.near2) {
+            int4 v = a.qvs[s];
+            if (v.x == oidx || v.y == oidx || v.z == oidx) continue;
+        }
         v4_t<T> g = a.src.g[s];
         T ir = d_rsqrt<T>(r2);
         T r = r2 * ir;
@@ -368,13 +393,27 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
 }
 
 template <typename T>
+cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
+                           const int4* qvs, double near, int n_tgt, const int* tcell,
+                           const v4_t<T>* tpos, const double* nrm_tgt, int layer, T* out,
+                           int out_stride, cudaStream_t st) {
+    if (n_tgt <= 0) return cudaSuccess;
+    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), n_tgt, tcell,
+                   tpos, nrm_tgt, out, out_stride};
+    dim3 b(LW * 32), g((n_tgt + LW - 1) / LW);
+    if (layer == 0) k_local<T, TK_POINTS, OUT_U, true><<<g, b, 0, st>>>(a);
+    else k_local<T, TK_POINTS, OUT_DBL, true><<<g, b, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
                       int kind, int n_tgt, const int* tcell, const v4_t<T>* tpos,
                       const double* nrm_tgt, int out_mode, T* out, int out_stride,
                       cudaStream_t st) {
     if (n_tgt <= 0) return cudaSuccess;
-    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, n_tgt, tcell, tpos, nrm_tgt, out,
-                   out_stride};
+    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, nullptr, (T)0, n_tgt, tcell, tpos,
+                   nrm_tgt, out, out_stride};
     if (kind == TK_SORTED) launch_kind<T, TK_SORTED>(a, out_mode, st);
     else if (kind == TK_POINTS) launch_kind<T, TK_POINTS>(a, out_mode, st);
     else launch_kind<T, TK_WALL>(a, OUT_U, st);
@@ -391,7 +430,11 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
                                       const v4_t<T>*, const double*, int, T*, int,             \
                                       cudaStream_t);                                           \
     template cudaError_t locate_targets<T>(const GridGeom&, const CellGrid&, int, int,        \
-                                           const double*, int*, v4_t<T>*, cudaStream_t);
+                                           const double*, int*, v4_t<T>*, cudaStream_t);       \
+    template cudaError_t local_sum_elem<T>(const GridGeom&, const CellGrid&,                  \
+                                           const SortedSources<T>&, const int4*, double, int,   \
+                                           const int*, const v4_t<T>*, const double*, int, T*,  \
+                                           int, cudaStream_t);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

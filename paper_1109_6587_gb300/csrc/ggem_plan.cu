@@ -151,6 +151,21 @@ __global__ void k_normalize(int n, double* __restrict__ nrm) {
     nrm[3 * i] = a * s; nrm[3 * i + 1] = b * s; nrm[3 * i + 2] = c * s;
 }
 
+// longest triangle edge (non-negative doubles compare as unsigned 64-bit integers)
+__global__ void k_max_edge(int m, const double* __restrict__ x, const int* __restrict__ tri,
+                           double* __restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    double l = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        int a = tri[3 * k + e], b = tri[3 * k + (e + 1) % 3];
+        double d0 = x[3 * a] - x[3 * b], d1 = x[3 * a + 1] - x[3 * b + 1],
+               d2 = x[3 * a + 2] - x[3 * b + 2];
+        l = fmax(l, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+    }
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(l));
+}
+
 __global__ void k_check_inside(int n, const double* __restrict__ x, double y0, double W,
                                int* __restrict__ bad) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -340,23 +355,54 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
     const GridGeom& geo = P->geo;
     cudaStream_t st = P->st;
     int n = P->n_nodes;
-    stage(P, ST_GATHER, 1, [&] {
+    const bool elem = P->prm.quadrature == GGEM_ELEMENT;
+    stage(P, ST_GATHER, elem ? 2 : 1, [&] {
         GG_CUDA(gather_strengths<T>(n, P->d_mesh_perm, q, P->d_area, 8.0 * kPi * geo.mu,
                                     (v4_t<T>*)P->d_sg, st));
+        if (elem)
+            GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qp_perm, P->d_qv, (const v4_t<T>*)P->d_qw, q,
+                                    8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
     T* loc = (T*)P->d_local;
-    stage(P, ST_LOCAL, 1, [&] {
-        GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, nullptr, P->d_nrm,
-                             layer == 0 ? OUT_U : OUT_DBL, loc, 3, st));
-    });
+    if (!elem) {
+        stage(P, ST_LOCAL, 1, [&] {
+            GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, nullptr, P->d_nrm,
+                                 layer == 0 ? OUT_U : OUT_DBL, loc, 3, st));
+        });
+    } else if (P->n_qp == 0) {
+        // no triangles: every element integral is empty
+        GG_CUDA(cudaMemsetAsync(loc, 0, (size_t)n * 3 * sizeof(T), st));
+    } else {
+        // local part by the element rule: all quadrature points, then the polar
+        // rule on the triangles that touch each node (Sec. 3.4.1, 3.5.2)
+        SortedSources<T> qs;
+        qs.pos = (v4_t<T>*)P->d_qp_pos;
+        qs.g = (v4_t<T>*)P->d_qg;
+        qs.cell = P->d_qp_cell;
+        qs.perm = P->d_qp_perm;
+        qs.cell_start = P->d_qp_start;
+        qs.n = P->n_qp;
+        stage(P, ST_LOCAL, 1, [&] {
+            GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, n,
+                                      P->d_node_cell, (const v4_t<T>*)P->d_node_pos, P->d_nrm,
+                                      layer, loc, 3, st));
+        });
+        stage(P, ST_ELEM, 1, [&] {
+            GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
+                                    P->d_adj_start, P->d_adj, q, P->rule, loc, 3, st));
+        });
+    }
     run_global<T>(P, src, true, layer == 0 ? 1 : 2);
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
-            double sc = 4.0 * geo.alpha / std::sqrt(kPi);   // (4 alpha/sqrt(pi)) A_b q_b
+            // nodal form: remove the free-space global self term (4 alpha/sqrt(pi)) A_b q_b;
+            // the element rule integrates the near field itself
+            double sc = elem ? 0.0 : 4.0 * geo.alpha / std::sqrt(kPi);
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 3, 0, n, P->d_x, loc,
-                                      3, nullptr, q, P->d_area, sc, 0, out, 3, st));
+                                      3, nullptr, elem ? nullptr : q, P->d_area, sc, 0, out, 3,
+                                      st));
         } else {
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 6, 0, n, P->d_x, loc,
                                       3, P->d_nrm, nullptr, nullptr, 0.0, 2, out, 3, st));
@@ -523,7 +569,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     P->cap = cap;
     dalloc(P, &P->d_cell_count, P->ncell);
     dalloc(P, &P->d_cell_start, P->ncell + 1);
-    dalloc(P, &P->d_cursor, (size_t)P->ncell + cap);
+    dalloc(P, &P->d_cursor, (size_t)P->ncell + std::max<size_t>(cap, (size_t)16 * prm.max_tris));
     dalloc(P, &P->d_src_cell, cap);
     dalloc(P, &P->d_perm, cap);
     size_t v4 = P->fp64 ? sizeof(double4_32a) : sizeof(float4);
@@ -565,6 +611,27 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
         dalloc(P, &P->d_tri, (size_t)prm.max_tris * 3);
         dalloc(P, &P->d_tri_area, prm.max_tris);
         dalloc(P, &P->d_tri_nrm, (size_t)prm.max_tris * 3);
+        dalloc(P, &P->d_adj_cnt, cap);
+        dalloc(P, &P->d_adj_start, (size_t)cap + 1);
+        dalloc(P, &P->d_adj_cur, cap);
+        dalloc(P, &P->d_adj, (size_t)prm.max_tris * 3);
+    }
+    P->rule = make_quad_rule();
+    dalloc(P, &P->d_node_cell, cap);
+    GG_CUDA(cudaMalloc(&P->d_node_pos, cap * v4 + 32));
+    if (prm.quadrature == GGEM_ELEMENT && prm.max_tris > 0) {
+        size_t cq = (size_t)16 * prm.max_tris;
+        GG_CHECK(cq < (size_t)1 << 31, GGEM_ERR_CAPACITY, "too many quadrature points");
+        P->cap_qp = (int)cq;
+        dalloc(P, &P->d_qx, cq * 3);
+        dalloc(P, &P->d_qv, cq);
+        dalloc(P, &P->d_qv_sorted, cq);
+        GG_CUDA(cudaMalloc(&P->d_qw, cq * v4 + 32));
+        dalloc(P, &P->d_qp_cell, cq);
+        dalloc(P, &P->d_qp_perm, cq);
+        dalloc(P, &P->d_qp_start, (size_t)P->ncell + 1);
+        GG_CUDA(cudaMalloc(&P->d_qp_pos, cq * v4 + 32));
+        GG_CUDA(cudaMalloc(&P->d_qg, cq * v4 + 32));
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
     GG_CUDA(cudaEventCreate(&P->ev1));
@@ -576,12 +643,16 @@ void plan_free(ggem_plan_t* P) {
     if (P->ev1) cudaEventDestroy(P->ev1);
     void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
                     P->d_minv, P->d_ydiff, P->d_sdi, P->d_sdf, P->d_mesh_sdi, P->d_mesh_sdf,
-                    P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall, P->d_ksw, P->d_cell_count,
-                    P->d_cell_start, P->d_cursor, P->d_src_cell, P->d_perm, P->d_spos, P->d_sg,
-                    P->d_src_x, P->d_local, P->d_in0, P->d_in1, P->d_in2, P->d_out0, P->d_out1,
-                    P->d_tgt_cell, P->d_tgt_pos, P->d_wall_cell, P->d_wall_pos, P->d_x,
-                    P->d_tri, P->d_area, P->d_nrm, P->d_tri_area, P->d_tri_nrm, P->d_mesh_cell,
-                    P->d_mesh_perm, P->d_mesh_start, P->d_mesh_pos};
+                    P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall,
+                    P->d_ksw, P->d_cell_count, P->d_cell_start, P->d_cursor, P->d_src_cell,
+                    P->d_perm, P->d_spos, P->d_sg, P->d_src_x, P->d_local, P->d_in0, P->d_in1,
+                    P->d_in2, P->d_out0, P->d_out1, P->d_tgt_cell, P->d_tgt_pos,
+                    P->d_wall_cell, P->d_wall_pos, P->d_x, P->d_tri, P->d_area, P->d_nrm,
+                    P->d_tri_area, P->d_tri_nrm, P->d_mesh_cell, P->d_mesh_perm,
+                    P->d_mesh_start, P->d_mesh_pos, P->d_qx, P->d_qv, P->d_qw, P->d_qp_cell,
+                    P->d_qp_perm, P->d_qp_start, P->d_qp_pos, P->d_qg, P->d_adj_cnt,
+                    P->d_adj_start, P->d_adj_cur, P->d_adj, P->d_node_cell, P->d_node_pos,
+                    P->d_qv_sorted};
     for (void* p : ptrs) dfree(p);
 }
 
@@ -676,6 +747,47 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
             GG_CUDA(spread_prepare<float>(P->geo, P->d_yj, n_nodes, P->d_mesh_perm, P->d_x,
                                           P->d_mesh_sdi, (float4*)P->d_mesh_sdf, st));
         }
+        const bool elem = P->prm.quadrature == GGEM_ELEMENT && n_tris > 0;
+        if (elem) {
+            // the quadrature-point and adjacency buffers exist only in element-rule plans
+            GG_CHECK(P->d_qx && P->d_qv && P->d_qw && P->d_adj, GGEM_ERR_INVALID_ARG,
+                     "element buffers missing");
+            if (P->fp64)
+                GG_CUDA(elem_setup<double>(n_tris, P->d_x, P->d_tri, P->d_tri_area, P->rule,
+                                           P->d_qx, P->d_qv, (double4_32a*)P->d_qw, n_nodes,
+                                           P->d_adj_cnt, P->d_adj_start, P->d_adj_cur, P->d_adj,
+                                           st));
+            else
+                GG_CUDA(elem_setup<float>(n_tris, P->d_x, P->d_tri, P->d_tri_area, P->rule,
+                                          P->d_qx, P->d_qv, (float4*)P->d_qw, n_nodes,
+                                          P->d_adj_cnt, P->d_adj_start, P->d_adj_cur, P->d_adj,
+                                          st));
+        }
+        P->n_qp = 0;
+        if (elem) {
+            double* dmax = P->d_out0;   // scratch
+            GG_CUDA(cudaMemsetAsync(dmax, 0, sizeof(double), st));
+            k_max_edge<<<(n_tris + 255) / 256, 256, 0, st>>>(n_tris, P->d_x, P->d_tri, dmax);
+            GG_CUDA(cudaMemcpyAsync(&P->near_edge, dmax, sizeof(double), cudaMemcpyDeviceToHost,
+                                    st));
+            GG_CUDA(cudaStreamSynchronize(st));
+            int nq = 16 * n_tris;
+            if (P->fp64) {
+                GG_CUDA(build_cells<double>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
+                                            P->d_qp_start, P->d_cursor, P->d_qp_cell,
+                                            P->d_qp_perm, (double4_32a*)P->d_qp_pos, st));
+                GG_CUDA(locate_targets<double>(P->geo, P->cg, n_nodes, TK_POINTS, P->d_x,
+                                               P->d_node_cell, (double4_32a*)P->d_node_pos, st));
+            } else {
+                GG_CUDA(build_cells<float>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
+                                           P->d_qp_start, P->d_cursor, P->d_qp_cell,
+                                           P->d_qp_perm, (float4*)P->d_qp_pos, st));
+                GG_CUDA(locate_targets<float>(P->geo, P->cg, n_nodes, TK_POINTS, P->d_x,
+                                              P->d_node_cell, (float4*)P->d_node_pos, st));
+            }
+            GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
+            P->n_qp = nq;
+        }
         P->n_nodes = n_nodes;
         P->n_tris = n_tris;
         P->mesh_ready = true;
@@ -757,8 +869,7 @@ static ggem_status layer_entry(ggem_plan_t* P, int layer, const double* q, doubl
         GG_CHECK(q && out, GGEM_ERR_INVALID_ARG, "NULL density or output");
         GG_CHECK(P->prm.quadrature == GGEM_NODAL || P->n_tris > 0, GGEM_ERR_INVALID_ARG,
                  "element quadrature needs triangles");
-        GG_CHECK(P->prm.quadrature == GGEM_NODAL, GGEM_ERR_INVALID_ARG,
-                 "element quadrature is not available in this build");
+
         GG_CHECK(layer == 0 || P->n_tris > 0, GGEM_ERR_INVALID_ARG,
                  "the double layer needs triangles (node normals)");
         size_t n3 = (size_t)P->n_nodes * 3;

@@ -200,3 +200,39 @@ def test_local_sum_alone(ggem, prec):
     us, _ = P.local_sum(_dev(s.x), _dev(g))
     us_ref, _ = O.local_point(box, alpha, rcut, 1.0, s.x, g, s.x[idx])
     assert _rel(us[idx], us_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_element_single_and_double_layer(ggem, prec):
+    """4x4 Gauss rule per triangle, polar rule on the target's own triangles,
+    n-tilde in the double layer (Sec. 3.4.1, 3.5.2)."""
+    s = W.single_sphere(radius=R_STRICT)
+    q = W.normal_forces(s.x.shape[0], seed=7)
+    w_ref = O.single_layer(s, q, quadrature="element")
+    v_ref = O.double_layer(s, q, quadrature="element")
+    P = ggem.Plan.for_box(s.box, precision=prec, quadrature="element", max_points=1000,
+                          max_tris=1000)
+    P.mesh_set(_dev(s.x), torch.as_tensor(s.tri, device="cuda"))
+    w = P.single_layer(_dev(q))
+    v = P.double_layer(_dev(q))
+    torch.cuda.synchronize()
+    assert _rel(w, w_ref) < TOL[prec]
+    assert _rel(v, v_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_element_100_capsules_sampled(ggem, prec):
+    s = W.capsules_100()
+    q = W.normal_forces(s.x.shape[0], seed=8)
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(s.x.shape[0], 200, replace=False))
+    w_ref = O.single_layer(s, q, quadrature="element", targets=idx)
+    v_ref = O.double_layer(s, q, quadrature="element", targets=idx)
+    P = ggem.Plan.for_box(s.box, precision=prec, quadrature="element",
+                          max_points=s.x.shape[0], max_tris=s.tri.shape[0])
+    P.mesh_set(_dev(s.x), torch.as_tensor(s.tri, device="cuda"))
+    w = P.single_layer(_dev(q))
+    v = P.double_layer(_dev(q))
+    torch.cuda.synchronize()
+    assert _rel(w[idx], w_ref) < TOL[prec]
+    assert _rel(v[idx], v_ref) < TOL[prec]
