@@ -15,8 +15,8 @@ Paper: Kumar & Graham, arXiv 1109.6587.  Steps, in the paper's order:
   6. stress sigma^g = -p + mu (grad u + grad u^T) ..... Sec. 3.5.1
   7. 4th-order (5-point) Lagrange interpolation ....... Sec. 3.2.2
   8. u = u^l + u^g ..................................... Eq. (tot_l_g)
-Boundary integral operators (Sec. 3.4, 3.5) and the Fredholm solve (Sec. 5)
-are built on top.
+Boundary integral operators (Sec. 3.4, 3.5) and the Fredholm solve (Sec. 5,
+restarted GMRES with modified Gram-Schmidt) are built on top.
 
 Readings (the paper is silent, ambiguous or garbled here):
   * alpha = 1/(2 h), h = max(Lx/Nx, W/(Ny-1), Lz/Nz); r_cut = 4/alpha.
@@ -559,3 +559,84 @@ def double_layer(susp, q, quadrature="element", mu=1.0, alpha=None, rcut=None,
         return vg + np.einsum("nk,njk->nj", nb[tsel], sl) / mu
     vl = local_elem(box, alpha, rcut, 1, susp.x, susp.tri, q, nrm=nb, targets=tsel)
     return vg + vl
+
+
+# ------------------------------------------------------------- Fredholm solve
+
+def bie_operator(susp, kappa, q, quadrature="element", mu=1.0, alpha=None, rcut=None):
+    """(I + kappa/(4 pi) D) q at the nodes (Sec. 5): q [N, 3], kappa [N] (the
+    kappa_m = (lambda_m - 1)/(lambda_m + 1) of each node's particle, Eq. (qa)),
+    D the discretised double layer of Sec. 3.5."""
+    q = _f64(q)
+    v = double_layer(susp, q, quadrature, mu, alpha, rcut)
+    return q + (np.asarray(kappa, dtype=np.float64)[:, None] / (4.0 * math.pi)) * v
+
+
+def gmres(apply, b, x0=None, tol=1e-6, restart=30, maxit=300):
+    """Restarted GMRES(m) (Saad) for A x = b on flat FP64 vectors, with modified
+    Gram-Schmidt Arnoldi, Givens rotations and the least-squares update at the
+    end of each cycle.  Each cycle starts from the true residual b - A x.
+    Stops when ||b - A x|| / ||b|| <= tol (true residual at the end of a cycle,
+    the Arnoldi estimate inside one).  Returns (x, iterations, true relative
+    residual, converged)."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    n = b.size
+    x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).ravel().copy()
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros(n), 0, 0.0, True
+    its = 0
+    while True:
+        r = b - apply(x)
+        beta = np.linalg.norm(r)
+        if beta / nb <= tol:
+            return x, its, beta / nb, True
+        if its >= maxit:
+            return x, its, beta / nb, False
+        m = min(restart, maxit - its)
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            w = apply(V[j])
+            its += 1
+            for i in range(j + 1):              # modified Gram-Schmidt
+                H[i, j] = V[i] @ w
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):                  # earlier rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            d = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / d, H[j + 1, j] / d
+            H[j, j] = d
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            if abs(g[j + 1]) / nb <= tol or H[j, j] == 0.0:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + V[:k].T @ y
+
+
+def bie_solve(susp, kappa, b, q0=None, tol=1e-6, restart=30, maxit=300,
+              quadrature="element", mu=1.0, alpha=None, rcut=None):
+    """q with (I + kappa/(4 pi) D) q = b by GMRES (Sec. 5).  b [N, 3] ->
+    (q [N, 3], iterations, true relative residual, converged)."""
+    n = susp.x.shape[0]
+
+    def apply(v):
+        return bie_operator(susp, kappa, v.reshape(n, 3), quadrature, mu, alpha, rcut).ravel()
+
+    x, its, rr, ok = gmres(apply, np.asarray(b).ravel(), None if q0 is None else np.asarray(q0).ravel(),
+                           tol, restart, maxit)
+    return x.reshape(n, 3), its, rr, ok

@@ -1,0 +1,106 @@
+"""Pins of the oracle's Fredholm solve (Sec. 5), CPU only.
+
+  * GMRES against numpy's dense LU on random well-conditioned systems, with
+    restarts forced (m < n): the solution to 1e-10 and the reported residual
+    equal to the recomputed one;
+  * the iteration limit reports non-convergence with the true residual;
+  * kappa = 0 makes the operator the identity: q = b, one Arnoldi step from
+    a zero guess (happy breakdown) and none from the guess b;
+  * the discretised operator (I + kappa/(4 pi) D) on a small sphere, assembled
+    column by column, solved by LU, against GMRES on the same system;
+  * a sphere carrying q = n: by the double-layer identity D n = lambda n the
+    solution for b = n is n / (1 + kappa lambda/(4 pi)), lambda measured from
+    the operator itself at the same mesh.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1109_6587_gb300 import workloads as W
+
+
+def _system(n, seed):
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / math.sqrt(n)
+    b = rng.standard_normal(n)
+    return A, b
+
+
+@pytest.mark.parametrize("restart", [5, 12, 60])
+def test_gmres_matches_dense_solve(restart):
+    A, b = _system(60, 3)
+    x, its, rr, ok = O.gmres(lambda v: A @ v, b, tol=1e-13, restart=restart, maxit=500)
+    xd = np.linalg.solve(A, b)
+    assert ok
+    assert np.abs(x - xd).max() < 1e-10 * np.abs(xd).max()
+    assert abs(rr - np.linalg.norm(b - A @ x) / np.linalg.norm(b)) < 1e-15
+    assert its <= 60 if restart == 60 else its > 0
+
+
+def test_gmres_iteration_limit():
+    A, b = _system(40, 5)
+    x, its, rr, ok = O.gmres(lambda v: A @ v, b, tol=1e-14, restart=4, maxit=6)
+    assert not ok and its == 6
+    assert rr == pytest.approx(np.linalg.norm(b - A @ x) / np.linalg.norm(b), rel=1e-12)
+    assert rr > 1e-14
+
+
+def test_gmres_identity_and_zero_rhs():
+    b = np.random.default_rng(1).standard_normal(30)
+    x, its, rr, ok = O.gmres(lambda v: v, b, tol=1e-12)
+    assert ok and its == 1 and np.abs(x - b).max() < 1e-15
+    x, its, rr, ok = O.gmres(lambda v: v, b, x0=b, tol=1e-12)
+    assert ok and its == 0
+    x, its, rr, ok = O.gmres(lambda v: 2 * v, np.zeros(30), tol=1e-12)
+    assert ok and its == 0 and not x.any()
+
+
+def _small_sphere(level=1):
+    V, F = W.icosphere(level)
+    box = W.Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=24, Ny=25, Nz=24)
+    c = np.array([4.0, 0.1, 4.0])
+    return W.Suspension(box=box, x=V + c, tri=F, particle=np.zeros(len(V), np.int32),
+                        centres=c[None], radius=1.0)
+
+
+def test_kappa_zero_gives_b():
+    s = _small_sphere()
+    b = np.random.default_rng(2).standard_normal(s.x.shape)
+    q, its, rr, ok = O.bie_solve(s, np.zeros(len(s.x)), b, q0=b)
+    assert ok and its == 0 and np.array_equal(q, b)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("quadrature", ["nodal", "element"])
+def test_bie_solve_matches_dense_lu(quadrature):
+    s = _small_sphere()
+    n = s.x.shape[0]
+    rng = np.random.default_rng(4)
+    kappa = np.full(n, 2.0 / 3.0)              # viscosity ratio 5
+    b = rng.standard_normal((n, 3))
+    A = np.zeros((3 * n, 3 * n))
+    for c in range(3 * n):
+        e = np.zeros(3 * n)
+        e[c] = 1.0
+        A[:, c] = O.bie_operator(s, kappa, e.reshape(n, 3), quadrature).ravel()
+    qd = np.linalg.solve(A, b.ravel()).reshape(n, 3)
+    q, its, rr, ok = O.bie_solve(s, kappa, b, tol=1e-12, quadrature=quadrature)
+    assert ok and its < 3 * n
+    assert np.abs(q - qd).max() < 1e-9 * np.abs(qd).max()
+    # a Fredholm operator of the second kind with |kappa| < 1 is well conditioned
+    assert np.linalg.cond(A) < 20
+
+
+def test_normal_density_solution():
+    s = _small_sphere(2)
+    n = s.x.shape[0]
+    _, _, _, nb = O.geometry(s.x, s.tri)
+    kappa = np.full(n, -0.6)
+    Dn = O.double_layer(s, nb)
+    lam = np.einsum("ij,ij->i", Dn, nb).mean()
+    q, its, rr, ok = O.bie_solve(s, kappa, nb, tol=1e-10)
+    expect = nb / (1.0 + kappa[0] * lam / (4.0 * math.pi))
+    # D n = lam n holds up to the mesh/grid error of the operator (~1e-2 here)
+    assert ok and np.abs(q - expect).max() < 0.05 * np.abs(expect).max()
