@@ -156,6 +156,46 @@ ggem_status ggem_single_layer(ggem_plan_t *plan, const double *q, double *w);
 ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
 
 /*
+ * Fredholm solve of Sec. 5 (the linear system below Eq. (qa)):
+ *     (I + kappa/(4 pi) D) q = b   at the mesh nodes,
+ * D the double layer of ggem_double_layer, kappa the diagonal of per-node
+ * kappa_m = (lambda_m - 1)/(lambda_m + 1), Eq. (qa).
+ *   kappa   [n_nodes]
+ *   b       [n_nodes][3]
+ *   q       [n_nodes][3]; in: initial guess (e.g. the previous time step's
+ *           density, or b), out: the solution
+ *   tol     stop when the TRUE relative residual ||b - A q|| / ||b|| <= tol,
+ *           A applied in FP64 (the paper stops at 1e-4 on the residual)
+ *   restart GMRES cycle length m, 1..64
+ *   maxit   limit on Arnoldi steps (operator applications inside cycles)
+ *   use_mlp must be 0: no learned warm start is loaded in this library
+ *   iters, true_relres  (out, may be NULL) Arnoldi steps taken and the final
+ *           true relative residual
+ * Method: restarted GMRES with FP64 Arnoldi vectors (classical Gram-Schmidt
+ * applied twice); every cycle starts from the true residual.  An FP64 plan
+ * uses its own operator throughout.  A mixed plan refines: true residuals
+ * come from an FP64 twin plan on the same mesh (built by the first solve and
+ * kept in step with later ggem_mesh_set calls; it doubles the plan's device
+ * memory), and each correction is one GMRES cycle with the mixed operator,
+ * solved to max(tol ||b|| / (2 ||r||), 1e-4) relative to its residual r.
+ * Arrays may be device or host memory.  The first solve allocates the
+ * Krylov workspace ((restart + 1) x 3 max_points doubles); later solves with
+ * the same or a shorter restart allocate nothing.  Returns GGEM_OK,
+ * GGEM_OK_BREAKDOWN (converged after a cycle whose Krylov space became
+ * invariant), GGEM_ERR_NOT_CONVERGED (q holds the last iterate, iters and
+ * true_relres are filled), GGEM_ERR_NUMERICAL (non-finite residual) or an
+ * argument error.  ||b|| = 0 returns q = 0 with no iteration.
+ */
+ggem_status bie_solve(ggem_plan_t *plan, const double *kappa, const double *b, double *q,
+                      double tol, int restart, int maxit, int use_mlp, int *iters,
+                      double *true_relres);
+
+/* Work counts of the last bie_solve on this plan: GMRES cycles, operator
+ * applications in FP64 and with the mixed operator. */
+ggem_status ggem_solve_stats(const ggem_plan_t *plan, int *cycles, int *matvec_fp64,
+                             int *matvec_mixed);
+
+/*
  * Allocation-free local velocity sum (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc -- code recording a CUDA graph

@@ -151,6 +151,19 @@ struct ggem_plan {
     // tracing: per-stage device time (CUDA events on the plan's stream)
     bool prof = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // Fredholm solve workspace (allocated by the first solve)
+    int sol_m = 0;                     // restart length d_V holds
+    double* d_V = nullptr;             // [sol_m + 1][ld] Krylov basis, ld >= 3 cap
+    double* d_sv = nullptr;            // [ld] double-layer output
+    double* d_sb = nullptr;            // [ld] staged right-hand side
+    double* d_sk = nullptr;            // [cap] staged kappa
+    double* d_sx = nullptr;            // [ld] iterate when q is a host array
+    double* d_spart = nullptr;         // reduction partials
+    double* d_sh = nullptr;            // Arnoldi coefficients / correction weights
+    double* h_sh = nullptr;            // pinned host copy of d_sh
+    ggem_plan* twin = nullptr;         // FP64 plan on the same mesh (mixed plans)
+    int sol_iters = 0, sol_cycles = 0, sol_mv64 = 0, sol_mvmix = 0;
+    double sol_relres = 0.0;
     double prof_ms[16] = {0};
     long prof_calls[16] = {0};
     long launches = 0;                 // kernels launched by this plan

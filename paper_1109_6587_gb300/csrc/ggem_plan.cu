@@ -10,6 +10,7 @@
 #include <new>
 
 #include "ggem_internal.cuh"
+#include "ggem_host.cuh"
 
 using namespace ggem;
 
@@ -22,100 +23,10 @@ void ks_thomas_mode(int Ny, double lam, double* tab, double* isq);
 
 namespace {
 
-const double kPi = 3.14159265358979323846;
-
-struct Fail {
-    ggem_status s;
-};
-
-#define GG_CUDA(call)                                                                    \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess) {                                                          \
-            P->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
-            throw Fail{GGEM_ERR_CUDA};                                                    \
-        }                                                                                 \
-    } while (0)
-
-#define GG_CHECK(cond, code, msg)                                                         \
-    do {                                                                                  \
-        if (!(cond)) {                                                                    \
-            P->err = (msg);                                                               \
-            throw Fail{code};                                                             \
-        }                                                                                 \
-    } while (0)
-
-template <typename F>
-ggem_status guarded(ggem_plan_t* P, F&& f) {
-    try {
-        f();
-        return GGEM_OK;
-    } catch (const Fail& e) {
-        return e.s;
-    } catch (const std::bad_alloc&) {
-        if (P) P->err = "host allocation failed";
-        return GGEM_ERR_CAPACITY;
-    } catch (...) {
-        if (P) P->err = "unexpected host exception";
-        return GGEM_ERR_CUDA;
-    }
-}
-
 // message of the last failed ggem_plan call on this thread
 thread_local std::string g_create_error = "no plan";
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-template <typename X>
-void dalloc(ggem_plan_t* P, X** p, size_t n) {
-    GG_CUDA(cudaMalloc((void**)p, n * sizeof(X) + 16));
-}
-
-void dfree(void* p) {
-    if (p) cudaFree(p);
-}
-
-// Input staging: device pointers pass through; host pointers are copied into
-// the plan buffer `stage` (n doubles).
-const double* stage_in(ggem_plan_t* P, const double* p, double* stage, size_t n) {
-    if (!p) return nullptr;
-    if (is_device_ptr(p)) return p;
-    GG_CUDA(cudaMemcpyAsync(stage, p, n * sizeof(double), cudaMemcpyHostToDevice, P->st));
-    return stage;
-}
-
-struct OutMap {
-    double* user = nullptr;
-    double* dev = nullptr;
-    size_t n = 0;
-    bool host = false;
-};
-
-OutMap stage_out(double* user, double* stage, size_t n) {
-    OutMap m;
-    m.user = user;
-    m.n = n;
-    if (!user) return m;
-    m.host = !is_device_ptr(user);
-    m.dev = m.host ? stage : user;
-    return m;
-}
-
-void finish_out(ggem_plan_t* P, const OutMap& m) {
-    if (m.user && m.host)
-        GG_CUDA(cudaMemcpyAsync(m.user, m.dev, m.n * sizeof(double), cudaMemcpyDeviceToHost,
-                                P->st));
-}
 
 // ------------------------------------------------------------- geometry
 __global__ void k_tri_geom(int m, const double* __restrict__ x, const int* __restrict__ tri,
@@ -173,32 +84,6 @@ __global__ void k_check_inside(int n, const double* __restrict__ x, double y0, d
     double y = x[3 * i + 1];
     bool ok = (y > y0) && (y < y0 + W) && isfinite(x[3 * i]) && isfinite(x[3 * i + 2]);
     if (!ok) atomicAdd(bad, 1);
-}
-
-// ------------------------------------------------------------- tracing
-enum Stage {
-    ST_CELLS, ST_GATHER, ST_LOCAL, ST_WALL, ST_SPREAD, ST_FFT_FWD, ST_CHEB_FWD, ST_KS,
-    ST_CHEB_INV, ST_FFT_INV, ST_INTERP, ST_ELEM, ST_COUNT
-};
-const char* kStageNames[ST_COUNT] = {"cell_list", "gather", "local_sum", "wall_local_sum",
-                                     "spread", "fft_forward", "cheb_forward", "tau_solve",
-                                     "cheb_inverse", "fft_inverse", "interpolate",
-                                     "element_correction"};
-
-// Run one stage (nk kernel launches); with tracing on, time it with events.
-template <typename F>
-void stage(ggem_plan_t* P, int id, int nk, F&& f) {
-    if (P->prof) GG_CUDA(cudaEventRecord(P->ev0, P->st));
-    f();
-    P->launches += nk;
-    if (P->prof) {
-        GG_CUDA(cudaEventRecord(P->ev1, P->st));
-        GG_CUDA(cudaEventSynchronize(P->ev1));
-        float ms = 0.f;
-        GG_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-        P->prof_ms[id] += ms;
-        P->prof_calls[id] += 1;
-    }
 }
 
 // ------------------------------------------------------------ pipeline
@@ -409,6 +294,15 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         }
     });
 }
+
+}  // namespace
+
+void ggem::double_layer_dev(ggem_plan_t* P, const double* q, double* v) {
+    if (P->fp64) layer_impl<double>(P, 1, q, v);
+    else layer_impl<float>(P, 1, q, v);
+}
+
+namespace {
 
 template <typename T>
 void upload_tables(ggem_plan_t* P, const std::vector<double>& cf, const std::vector<double>& ci,
@@ -652,8 +546,11 @@ void plan_free(ggem_plan_t* P) {
                     P->d_mesh_start, P->d_mesh_pos, P->d_qx, P->d_qv, P->d_qw, P->d_qp_cell,
                     P->d_qp_perm, P->d_qp_start, P->d_qp_pos, P->d_qg, P->d_adj_cnt,
                     P->d_adj_start, P->d_adj_cur, P->d_adj, P->d_node_cell, P->d_node_pos,
-                    P->d_qv_sorted};
+                    P->d_qv_sorted, P->d_V, P->d_sv, P->d_sb, P->d_sk, P->d_sx,
+                    P->d_spart, P->d_sh};
     for (void* p : ptrs) dfree(p);
+    if (P->h_sh) cudaFreeHost(P->h_sh);
+    if (P->twin) ggem_plan_destroy(P->twin);
 }
 
 }  // namespace
@@ -792,6 +689,10 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
         P->n_tris = n_tris;
         P->mesh_ready = true;
         GG_CUDA(cudaStreamSynchronize(st));
+        if (P->twin) {                 // the FP64 twin of a mixed plan follows the mesh
+            ggem_status ts = ggem_mesh_set(P->twin, n_nodes, P->d_x, n_tris, P->d_tri);
+            GG_CHECK(ts == GGEM_OK, ts, std::string("FP64 twin: ") + ggem_last_error(P->twin));
+        }
     });
 }
 
@@ -898,6 +799,7 @@ ggem_status ggem_trace_enable(ggem_plan_t* P, int on) {
         P->prof_calls[i] = 0;
     }
     P->launches = 0;
+    if (P->twin) ggem_trace_enable(P->twin, on);
     return GGEM_OK;
 }
 
@@ -909,14 +811,15 @@ const char* ggem_trace_stage_name(int stage) {
 
 ggem_status ggem_trace_read(const ggem_plan_t* P, int stage, double* total_ms, long* calls) {
     if (!P || stage < 0 || stage >= ST_COUNT) return GGEM_ERR_INVALID_ARG;
-    if (total_ms) *total_ms = P->prof_ms[stage];
-    if (calls) *calls = P->prof_calls[stage];
+    // a mixed plan's FP64 twin (true residuals of the solve) is counted with it
+    if (total_ms) *total_ms = P->prof_ms[stage] + (P->twin ? P->twin->prof_ms[stage] : 0.0);
+    if (calls) *calls = P->prof_calls[stage] + (P->twin ? P->twin->prof_calls[stage] : 0);
     return GGEM_OK;
 }
 
 ggem_status ggem_launch_count(const ggem_plan_t* P, long* launches) {
     if (!P || !launches) return GGEM_ERR_INVALID_ARG;
-    *launches = P->launches;
+    *launches = P->launches + (P->twin ? P->twin->launches : 0);
     return GGEM_OK;
 }
 

@@ -1,0 +1,376 @@
+// Fredholm solve of Sec. 5: (I + kappa/(4 pi) D) q = b at the mesh nodes,
+// D the discretised double layer (Sec. 3.5), kappa_m = (lambda_m - 1)/(lambda_m
+// + 1) per node (Eq. qa).  Restarted GMRES (Saad) whose Arnoldi vectors live in
+// FP64 in HBM: classical Gram-Schmidt applied twice per step (two multi-dot
+// passes, each reading the basis once), deterministic two-stage reductions, and
+// the small Hessenberg least-squares problem (Givens rotations) on the host.
+//
+// FP64 plan: plain restarted GMRES with the FP64 operator.  Each cycle starts
+// from the true residual b - A q.
+// Mixed plan: iterative refinement.  The outer residual b - A64 q is formed
+// with an FP64 twin plan on the same mesh; each correction is one GMRES cycle
+// with the mixed operator, asked only for the accuracy that operator carries.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ggem.h"
+#include "ggem_host.cuh"
+
+using namespace ggem;
+
+namespace {
+
+constexpr int KB = 256;          // threads per block of the vector kernels
+constexpr int KNB = 2 * 152;     // blocks of one reduction pass (2 per SM)
+constexpr int KG = 8;            // basis vectors per sweep of the multi-dot
+constexpr int KMAXM = 64;        // longest restart cycle
+constexpr int KH = KMAXM + 2;    // stride of one coefficient array in d_sh
+
+// out = x + s kappa v (b == nullptr), or out = b - (x + s kappa v); s = 1/(4 pi)
+__global__ void k_bie_apply(int n, double s, const double* __restrict__ x,
+                            const double* __restrict__ v, const double* __restrict__ kappa,
+                            const double* __restrict__ b, double* __restrict__ out) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n) return;
+    double a = fma(s * kappa[e / 3], v[e], x[e]);
+    out[e] = b ? b[e] - a : a;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// part[i][blk] = the block's grid-stride share of <V_i, w>, i < k
+__global__ void __launch_bounds__(KB) k_mdot(size_t n, int k, const double* __restrict__ V,
+                                             size_t ldv, const double* __restrict__ w,
+                                             double* __restrict__ part) {
+    __shared__ double red[KG][KB / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < k; i0 += KG) {
+        const int kk = min(KG, k - i0);
+        double acc[KG];
+#pragma unroll
+        for (int g = 0; g < KG; ++g) acc[g] = 0.0;
+        for (size_t e = (size_t)blockIdx.x * KB + threadIdx.x; e < n;
+             e += (size_t)gridDim.x * KB) {
+            const double we = w[e];
+#pragma unroll
+            for (int g = 0; g < KG; ++g)
+                if (g < kk) acc[g] = fma(V[(size_t)(i0 + g) * ldv + e], we, acc[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < KG; ++g) {
+            double t = warp_sum(acc[g]);
+            if (lane == 0) red[g][wid] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < kk) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < KB / 32; ++q) t += red[threadIdx.x][q];
+            part[(size_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// h[i] = sum over blocks of part[i][.], one block per i, fixed summation order
+__global__ void __launch_bounds__(KB) k_mdot_final(int nb, const double* __restrict__ part,
+                                                   double* __restrict__ h) {
+    __shared__ double red[KB / 32];
+    const int i = blockIdx.x;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += KB) t += part[(size_t)i * nb + b];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < KB / 32; ++q) s += red[q];
+        h[i] = s;
+    }
+}
+
+// w += sgn * sum_{i<k} h[i] V_i
+__global__ void __launch_bounds__(KB) k_mupdate(size_t n, int k, const double* __restrict__ V,
+                                                size_t ldv, const double* __restrict__ h,
+                                                double sgn, double* __restrict__ w) {
+    __shared__ double sh[KMAXM + 2];
+    for (int i = threadIdx.x; i < k; i += KB) sh[i] = sgn * h[i];
+    __syncthreads();
+    for (size_t e = (size_t)blockIdx.x * KB + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * KB) {
+        double a = w[e];
+        for (int i = 0; i < k; ++i) a = fma(sh[i], V[(size_t)i * ldv + e], a);
+        w[e] = a;
+    }
+}
+
+// w /= sqrt(*nrm2) when *nrm2 > 0
+__global__ void k_scale(size_t n, const double* __restrict__ nrm2, double* __restrict__ w) {
+    const double s2 = *nrm2;
+    if (!(s2 > 0.0)) return;
+    const double s = 1.0 / sqrt(s2);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        w[e] *= s;
+}
+
+int grid_for(size_t n) {
+    return (int)std::min<size_t>(KNB, (n + KB - 1) / KB);
+}
+
+struct Solver {
+    ggem_plan_t* P;      // the plan the caller owns (error messages, stream)
+    ggem_plan_t* P64;    // plan whose operator gives true residuals (P or its twin)
+    int n;               // nodes
+    size_t n3, ld;
+    const double* kappa;
+    const double* b;
+    double* x;
+    double* hs;          // pinned host copy of d_sh
+
+    void launched(int k) { P->launches += k; }
+
+    // h_out[0..k) = V_i . w
+    void mdot(int k, const double* V, const double* w, double* h_out) {
+        int g = grid_for(n3);
+        k_mdot<<<g, KB, 0, P->st>>>(n3, k, V, ld, w, P->d_spart);
+        k_mdot_final<<<k, KB, 0, P->st>>>(g, P->d_spart, h_out);
+        GG_CUDA(cudaGetLastError());
+        launched(2);
+    }
+    void mupdate(int k, const double* h, double sgn, double* w) {
+        k_mupdate<<<grid_for(n3), KB, 0, P->st>>>(n3, k, P->d_V, ld, h, sgn, w);
+        GG_CUDA(cudaGetLastError());
+        launched(1);
+    }
+    // squared norm of w into *slot (device), then w /= norm
+    void normalize(double* w, double* slot) {
+        mdot(1, w, w, slot);
+        k_scale<<<grid_for(n3), KB, 0, P->st>>>(n3, slot, w);
+        GG_CUDA(cudaGetLastError());
+        launched(1);
+    }
+    // out = (I + kappa/(4 pi) D) in, or b - that when with_b
+    void apply(ggem_plan_t* Q, const double* in, double* out, bool with_b) {
+        double_layer_dev(Q, in, P->d_sv);
+        int nb = (int)((n3 + KB - 1) / KB);
+        k_bie_apply<<<nb, KB, 0, P->st>>>(n, 0.25 / kPi, in, P->d_sv, kappa,
+                                          with_b ? b : nullptr, out);
+        GG_CUDA(cudaGetLastError());
+        launched(1);
+        if (Q->fp64) P->sol_mv64++;
+        else P->sol_mvmix++;
+    }
+    void to_host(int count) {
+        GG_CUDA(cudaMemcpyAsync(hs, P->d_sh, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                P->st));
+        GG_CUDA(cudaStreamSynchronize(P->st));
+    }
+
+    // ||b||
+    double norm_b() {
+        mdot(1, b, b, P->d_sh);
+        to_host(1);
+        return std::sqrt(hs[0]);
+    }
+
+    // True residual r = b - A64 x into V_0, its norm returned, V_0 normalised.
+    double residual_into_v0() {
+        double* v0 = P->d_V;
+        apply(P64, x, v0, true);
+        normalize(v0, P->d_sh);
+        to_host(1);
+        return std::sqrt(hs[0]);
+    }
+
+    // One GMRES cycle on A_inner d = r, r = beta V_0 already in place, d = 0;
+    // x += d at the end.  Stops when |g_{j+1}| <= stop_abs or after m steps.
+    // Returns the operator applications made; *breakdown set when the Krylov
+    // space became invariant (the cycle's update is then exact).
+    int cycle(ggem_plan_t* Ainner, int m, double beta, double stop_abs, bool* breakdown) {
+        std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+        auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+        g[0] = beta;
+        double* hA = P->d_sh;
+        double* hB = P->d_sh + KH;
+        double* hN = P->d_sh + 2 * KH;
+        int k = 0, steps = 0;
+        *breakdown = false;
+        for (int j = 0; j < m; ++j) {
+            double* vj = P->d_V + (size_t)j * ld;
+            double* w = P->d_V + (size_t)(j + 1) * ld;
+            apply(Ainner, vj, w, false);
+            stage(P, ST_KRYLOV, 0, [&] {
+                mdot(j + 1, P->d_V, w, hA);          // classical Gram-Schmidt ...
+                mupdate(j + 1, hA, -1.0, w);
+                mdot(j + 1, P->d_V, w, hB);          // ... applied twice
+                mupdate(j + 1, hB, -1.0, w);
+                normalize(w, hN);
+                to_host(3 * KH);
+            });
+            double an = hs[2 * KH];                      // ||A v_j||^2
+            for (int i = 0; i <= j; ++i) {
+                Hij(i, j) = hs[i] + hs[KH + i];
+                an += Hij(i, j) * Hij(i, j);
+            }
+            double hn = std::sqrt(hs[2 * KH]);
+            Hij(j + 1, j) = hn;
+            for (int i = 0; i < j; ++i) {                // earlier rotations
+                double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+                Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+                Hij(i, j) = t;
+            }
+            double d = std::hypot(Hij(j, j), Hij(j + 1, j));
+            steps = j + 1;
+            if (d == 0.0) {                              // singular on the Krylov space
+                k = j;
+                break;
+            }
+            k = j + 1;
+            cs[j] = Hij(j, j) / d;
+            sn[j] = Hij(j + 1, j) / d;
+            Hij(j, j) = d;
+            Hij(j + 1, j) = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (hn <= 1e-14 * std::sqrt(an)) {           // happy breakdown: exact in the space
+                *breakdown = true;
+                break;
+            }
+            if (std::fabs(g[j + 1]) <= stop_abs) break;
+        }
+        if (k == 0) return steps;
+        std::vector<double> y(k);
+        for (int i = k - 1; i >= 0; --i) {               // back substitution
+            double t = g[i];
+            for (int c = i + 1; c < k; ++c) t -= Hij(i, c) * y[c];
+            y[i] = t / Hij(i, i);
+        }
+        GG_CUDA(cudaMemcpyAsync(P->d_sh, y.data(), k * sizeof(double), cudaMemcpyHostToDevice,
+                                P->st));
+        stage(P, ST_KRYLOV, 0, [&] { mupdate(k, P->d_sh, 1.0, x); });
+        GG_CUDA(cudaStreamSynchronize(P->st));           // y lives on this stack frame
+        return steps;
+    }
+};
+
+void ensure_solver_ws(ggem_plan_t* P, int m) {
+    size_t ld = ((size_t)3 * P->cap + 31) / 32 * 32;
+    if (!P->d_sv) {
+        dalloc(P, &P->d_sv, ld);
+        dalloc(P, &P->d_sb, ld);
+        dalloc(P, &P->d_sk, (size_t)P->cap);
+        dalloc(P, &P->d_sx, ld);
+        dalloc(P, &P->d_spart, (size_t)KH * KNB);
+        dalloc(P, &P->d_sh, (size_t)3 * KH);
+        GG_CUDA(cudaMallocHost((void**)&P->h_sh, (size_t)3 * KH * sizeof(double)));
+    }
+    if (P->sol_m < m) {
+        dfree(P->d_V);
+        P->d_V = nullptr;
+        dalloc(P, &P->d_V, (size_t)(m + 1) * ld);
+        P->sol_m = m;
+    }
+}
+
+void ensure_twin(ggem_plan_t* P) {
+    if (P->fp64 || P->twin) return;
+    ggem_params tp = P->prm;
+    tp.precision = GGEM_FP64;
+    ggem_plan_t* T = nullptr;
+    ggem_status s = ggem_plan(&tp, P->st, &T);
+    GG_CHECK(s == GGEM_OK, s, std::string("FP64 twin plan: ") + ggem_last_error(nullptr));
+    P->twin = T;
+    s = ggem_mesh_set(T, P->n_nodes, P->d_x, P->n_tris, P->d_tri);
+    GG_CHECK(s == GGEM_OK, s, std::string("FP64 twin mesh: ") + ggem_last_error(T));
+}
+
+}  // namespace
+
+ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, double* q,
+                      double tol, int restart, int maxit, int use_mlp, int* iters,
+                      double* true_relres) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    ggem_status result = GGEM_OK;
+    ggem_status s = guarded(P, [&] {
+        GG_CHECK(P->mesh_ready && P->n_tris > 0, GGEM_ERR_INVALID_ARG,
+                 "the solve needs a mesh with triangles");
+        GG_CHECK(kappa && b && q, GGEM_ERR_INVALID_ARG, "NULL kappa, b or q");
+        GG_CHECK(tol > 0.0 && std::isfinite(tol), GGEM_ERR_INVALID_ARG, "tol must be > 0");
+        GG_CHECK(restart >= 1 && restart <= KMAXM, GGEM_ERR_INVALID_ARG,
+                 "restart must be in 1..64");
+        GG_CHECK(maxit >= 0, GGEM_ERR_INVALID_ARG, "maxit must be >= 0");
+        GG_CHECK(!use_mlp, GGEM_ERR_INVALID_ARG, "no learned warm start is loaded");
+        ensure_solver_ws(P, restart);
+        ensure_twin(P);
+        P->sol_cycles = P->sol_mv64 = P->sol_mvmix = 0;
+        const int n = P->n_nodes;
+        const size_t n3 = (size_t)n * 3;
+        Solver S;
+        S.P = P;
+        S.P64 = P->fp64 ? P : P->twin;
+        S.n = n;
+        S.n3 = n3;
+        S.ld = ((size_t)3 * P->cap + 31) / 32 * 32;
+        S.hs = P->h_sh;
+        S.kappa = stage_in(P, kappa, P->d_sk, (size_t)n);
+        S.b = stage_in(P, b, P->d_sb, n3);
+        const bool q_host = !is_device_ptr(q);
+        S.x = q_host ? P->d_sx : q;
+        if (q_host)
+            GG_CUDA(cudaMemcpyAsync(S.x, q, n3 * sizeof(double), cudaMemcpyHostToDevice, P->st));
+        int its = 0;
+        double rel = 0.0;
+        bool last_breakdown = false;
+        const double nb = S.norm_b();
+        if (nb == 0.0) {
+            GG_CUDA(cudaMemsetAsync(S.x, 0, n3 * sizeof(double), P->st));
+        } else {
+            for (;;) {
+                double beta = S.residual_into_v0();
+                rel = beta / nb;
+                GG_CHECK(std::isfinite(rel), GGEM_ERR_NUMERICAL, "non-finite residual");
+                if (rel <= tol) {
+                    result = last_breakdown ? GGEM_OK_BREAKDOWN : GGEM_OK;
+                    break;
+                }
+                if (its >= maxit) {
+                    result = GGEM_ERR_NOT_CONVERGED;
+                    P->err = "iteration limit reached";
+                    break;
+                }
+                int m = std::min(restart, maxit - its);
+                // FP64: aim at the final tolerance.  Mixed: one correction gains at
+                // most ~4 digits (the mixed operator matches FP64 to ~1e-5 relative).
+                double eta = P->fp64 ? tol * nb / beta : std::max(0.5 * tol * nb / beta, 1e-4);
+                bool bd = false;
+                int steps = S.cycle(P, m, beta, eta * beta, &bd);
+                its += steps;
+                P->sol_cycles++;
+                last_breakdown = bd;
+            }
+        }
+        if (q_host)
+            GG_CUDA(cudaMemcpyAsync(q, S.x, n3 * sizeof(double), cudaMemcpyDeviceToHost, P->st));
+        GG_CUDA(cudaStreamSynchronize(P->st));
+        P->sol_iters = its;
+        P->sol_relres = rel;
+        if (iters) *iters = its;
+        if (true_relres) *true_relres = rel;
+    });
+    return s != GGEM_OK ? s : result;
+}
+
+ggem_status ggem_solve_stats(const ggem_plan_t* P, int* cycles, int* matvec_fp64,
+                             int* matvec_mixed) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    if (cycles) *cycles = P->sol_cycles;
+    if (matvec_fp64) *matvec_fp64 = P->sol_mv64;
+    if (matvec_mixed) *matvec_mixed = P->sol_mvmix;
+    return GGEM_OK;
+}

@@ -45,7 +45,7 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_single_layer",
            "ggem_double_layer", "ggem_trace_enable", "ggem_trace_stage_count",
            "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count",
-           "ggem_local_velocity_noalloc"]
+           "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats"]
 
 
 def lib():
@@ -68,6 +68,9 @@ def lib():
         L.ggem_local_sum.argtypes = [P, I, P, P, I, P, I, P, P]
         L.ggem_single_layer.argtypes = [P, P, P]
         L.ggem_double_layer.argtypes = [P, P, P]
+        L.bie_solve.argtypes = [P, P, P, P, D, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.ggem_solve_stats.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                       ctypes.POINTER(I)]
         L.ggem_trace_enable.argtypes = [P, I]
         L.ggem_trace_stage_count.argtypes = []
         L.ggem_trace_stage_name.argtypes = [I]
@@ -226,6 +229,35 @@ class Plan:
     def double_layer(self, q, out=None):
         return self._layer(lib().ggem_double_layer, q, out)
 
+    def bie_solve(self, kappa, b, q=None, tol=1e-6, restart=30, maxit=300, use_mlp=False,
+                  check=True):
+        """Solve (I + kappa/(4 pi) D) q = b (Sec. 5).  q (in: initial guess, b when
+        None; out: the solution) is updated in place when given.  Returns
+        (q, iterations, true relative residual, status); with check, an error
+        status other than GGEM_ERR_NOT_CONVERGED raises."""
+        if q is None:
+            q = b.clone() if hasattr(b, "clone") else np.array(b, dtype=np.float64, copy=True)
+        pk, kk = _ptr(kappa, np.float64)
+        pb, kb = _ptr(b, np.float64)
+        pq, kq = _ptr(q, np.float64)
+        its = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().bie_solve(self.h, pk, pb, pq, tol, restart, maxit, int(bool(use_mlp)),
+                             ctypes.byref(its), ctypes.byref(rr))
+        if check and st not in (0, 5, 6):
+            _check(st, self.h)
+        if kq is not q and not hasattr(q, "data_ptr"):
+            q[...] = kq
+        return q, its.value, rr.value, st
+
+    def solve_stats(self):
+        """(GMRES cycles, FP64 operator applications, mixed operator applications)
+        of the last bie_solve."""
+        c, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ggem_solve_stats(self.h, ctypes.byref(c), ctypes.byref(a),
+                                      ctypes.byref(b)), self.h)
+        return c.value, a.value, b.value
+
 
 # The C names, for callers that prefer them.
 def ggem_plan(box_or_params, **kw):
@@ -238,6 +270,10 @@ def ggem_single_layer(plan, q, out=None):
 
 def ggem_double_layer(plan, q, out=None):
     return plan.double_layer(q, out)
+
+
+def bie_solve(plan, kappa, b, q=None, tol=1e-6, restart=30, maxit=300, use_mlp=False):
+    return plan.bie_solve(kappa, b, q, tol, restart, maxit, use_mlp)
 
 
 def ggem_point_forces(plan, xs, g, xt=None, want_u=True, want_sigma=False):
