@@ -1,12 +1,16 @@
-"""Benchmark of the GGEM slit matvec (single + double layer) on GB300.
+"""Benchmark of the GGEM slit operators and Fredholm solve on GB300.
 
-Step: one pass of the hot path over the workload -- the single-layer and the
-double-layer operators evaluated at every node (Sec. 3.4, 3.5 of Kumar &
-Graham, arXiv 1109.6587) for fresh N(0,1) densities.
+Step: one pass of the matvec hot path over the workload -- the single-layer
+and the double-layer operators evaluated at every node (Sec. 3.4, 3.5 of
+Kumar & Graham, arXiv 1109.6587) for fresh N(0,1) densities.
 
 Workload (default): 100 spherical capsules x 642 nodes = 64,200 points in a
-40 x [-5,5] x 40 slit, grid 128 x 65 x 128, mixed precision, nodal quadrature.
+40 x [-5,5] x 40 slit, grid 128 x 65 x 128, mixed precision, element
+quadrature (the paper's layer rule; --quadrature nodal for point forces).
 Metric: Mpts/s = nodes / (time of one single + one double layer evaluation).
+The second half of the metric -- GMRES iterations and seconds per Fredholm
+solve at true relative residual 1e-6, FP64 against mixed -- is measured on
+the same workload and reported under "solve".
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
@@ -39,8 +43,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--quadrature", default="nodal", choices=["nodal", "element"])
+    ap.add_argument("--quadrature", default="element", choices=["nodal", "element"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     return ap.parse_args()
 
 
@@ -131,6 +136,38 @@ def _pair_count(susp, rcut):
     return 2 * len(tree.query_pairs(rcut, output_type="ndarray"))
 
 
+def _quad_points(susp):
+    """The 16 collapsed-Gauss points of every triangle (Sec. 3.4.1) and the
+    triangle each belongs to."""
+    t, w = np.polynomial.legendre.leggauss(4)
+    t = 0.5 * (t + 1.0)
+    eta = np.repeat(t, 4)
+    xi = (1.0 - eta) * np.tile(t, 4)
+    p = np.stack([1.0 - xi - eta, xi, eta], 1)                    # [16, 3]
+    X = susp.x[susp.tri]                                           # [m, 3, 3]
+    return np.einsum("qv,mvc->mqc", p, X).reshape(-1, 3), np.repeat(np.arange(len(susp.tri)), 16)
+
+
+def _elem_pair_count(susp, rcut):
+    """(node, quadrature point) pairs with 0 < r < r_cut, minimum image in x, z,
+    less the points of triangles that contain the node (polar rule instead)."""
+    from scipy.spatial import cKDTree
+    b = susp.box
+    qx, qt = _quad_points(susp)
+
+    def wrap(a):
+        a = a.copy()
+        a[:, 0] %= b.Lx
+        a[:, 2] %= b.Lz
+        a[:, 1] -= b.y0
+        return a
+    box = [b.Lx, 4 * b.W + 4 * rcut, b.Lz]
+    tq = cKDTree(wrap(qx), boxsize=box)
+    tn = cKDTree(wrap(susp.x), boxsize=box)
+    total = int(tn.count_neighbors(tq, rcut))
+    return total - 16 * 3 * len(susp.tri)
+
+
 def run_mine(args, rank, world):
     import torch
     from paper_1109_6587_gb300 import ggem
@@ -218,7 +255,7 @@ def roofline(res, args):
     esz = 4 if args.precision == "mixed" else 8
     plane = b.Nz * b.Nx
     if name == "local_sum":
-        pairs = _pair_count(susp, rc)
+        pairs = _elem_pair_count(susp, rc) if args.quadrature == "element" else _pair_count(susp, rc)
         # FLOPs per pair: single layer 52, double layer 70, averaged
         flops = pairs * 61.0
         sm_mhz = res["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
@@ -248,20 +285,71 @@ def roofline(res, args):
             "frac": ach / peak, "traffic": None, "peak_source": kind}
 
 
-def cpu_baseline(susp, args):
-    """The FP64 oracle as it stands on the host cores: one single- and one
-    double-layer evaluation (nodal quadrature) of the full workload."""
+def cpu_baseline(susp, args, stride=64):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample:
+    the single and double layer with their full global parts, the local part
+    at every stride-th node, scaled to all nodes."""
     from oracle import oracle as O
     q = np.random.default_rng(99).standard_normal((susp.x.shape[0], 3))
+    n = susp.x.shape[0]
+    idx = np.arange(0, n, stride)
+    a = O.default_alpha(susp.box)
+    rc = O.default_rcut(a)
+    _, _, _, nb = O.geometry(susp.x, susp.tri)
     t0 = time.perf_counter()
-    O.single_layer(susp, q, quadrature=args.quadrature)
-    O.double_layer(susp, q, quadrature=args.quadrature)
-    dt = time.perf_counter() - t0
+    O.single_layer(susp, q, quadrature=args.quadrature, targets=idx)
+    O.double_layer(susp, q, quadrature=args.quadrature, targets=idx)
+    t_sample = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if args.quadrature == "element":
+        O.local_elem(susp.box, a, rc, 0, susp.x, susp.tri, q, targets=idx)
+        O.local_elem(susp.box, a, rc, 1, susp.x, susp.tri, q, nrm=nb, targets=idx)
+    else:
+        g = 8.0 * math.pi * np.asarray(O.geometry(susp.x, susp.tri)[2])[:, None] * q
+        O.local_point(susp.box, a, rc, 1.0, susp.x, g, susp.x[idx], want_u=True,
+                      want_sig=True)
+    t_local = time.perf_counter() - t0
+    dt = t_sample + t_local * (n / len(idx) - 1.0)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": susp.x.shape[0] / dt / 1e6, "unit": "Mpts/s", "cores": cores,
-            "kind": "oracle", "seconds": dt,
-            "sample": "one FP64 single-layer + double-layer evaluation of the full workload "
-                      f"({args.quadrature} quadrature, OpenMP over targets/planes)"}
+    return {"value": n / dt / 1e6, "unit": "Mpts/s", "cores": cores,
+            "kind": "oracle", "seconds": dt, "measured_seconds": t_sample + t_local,
+            "sample": f"FP64 single + double layer ({args.quadrature} quadrature): both "
+                      f"global parts in full, the local part at every {stride}th node "
+                      f"({len(idx)} of {n}) scaled to all nodes; OpenMP over targets"}
+
+
+def solve_metrics(args, susp, dev):
+    """GMRES iterations and seconds per Fredholm solve (Sec. 5) at true relative
+    residual 1e-6 for an FP64 plan and a mixed plan on the workload:
+    kappa = 2/3 (viscosity ratio 5) on every node, b ~ N(0,1), guess q0 = b."""
+    import torch
+    from paper_1109_6587_gb300 import ggem
+    n = susp.x.shape[0]
+    rng = np.random.default_rng(77)
+    kappa = torch.full((n,), 2.0 / 3.0, dtype=torch.float64, device=dev)
+    b = torch.as_tensor(rng.standard_normal((n, 3)), device=dev)
+    x = torch.as_tensor(susp.x, device=dev)
+    tri = torch.as_tensor(susp.tri, device=dev)
+    out = {"tol": 1e-6, "kappa": 2.0 / 3.0, "rhs": "N(0,1)", "guess": "b", "restart": 30,
+           "quadrature": args.quadrature}
+    for prec in ("fp64", "mixed"):
+        P = ggem.Plan.for_box(susp.box, precision=prec, quadrature=args.quadrature,
+                              max_points=n, max_tris=susp.tri.shape[0])
+        P.mesh_set(x, tri)
+        P.bie_solve(kappa, b, q=b.clone(), tol=1e-6, maxit=1)      # workspace (+ FP64 twin)
+        torch.cuda.synchronize()
+        l0 = P.launch_count()
+        t0 = time.perf_counter()
+        q, its, rr, st = P.bie_solve(kappa, b, q=b.clone(), tol=1e-6)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        cyc, m64, mmix = P.solve_stats()
+        out[prec] = {"iters": its, "s_per_solve": dt, "true_relres": rr, "status": st,
+                     "cycles": cyc, "matvec_fp64": m64, "matvec_mixed": mmix,
+                     "gpu_launches": P.launch_count() - l0}
+        P.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_solve"] / out["mixed"]["s_per_solve"]
+    return out
 
 
 def main():
@@ -306,6 +394,9 @@ def main():
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "stages_ms": {k: v[0] / v[1] for k, v in res["stages"].items()}}
     line["roofline"] = roofline(res, args)
+    if not args.no_solve:
+        import torch
+        line["solve"] = solve_metrics(args, res["susp"], torch.device("cuda"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["susp"], args)
     if world > 1:

@@ -20,7 +20,8 @@
  *    asynchronous on the plan's stream.
  *  - The caller owns every input and output array; the plan owns all
  *    workspaces.  No entry point below allocates device memory except
- *    ggem_plan and ggem_mesh_set (which sizes its mesh tables once).
+ *    ggem_plan, ggem_mesh_set (which sizes its mesh tables once) and the
+ *    first bie_solve on a plan (Krylov workspace; FP64 twin of a mixed plan).
  *  - Every entry point returns a ggem_status; no C++ exception crosses the
  *    ABI.  On error ggem_last_error(plan) gives a message.
  */
@@ -177,7 +178,9 @@ ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
  * come from an FP64 twin plan on the same mesh (built by the first solve and
  * kept in step with later ggem_mesh_set calls; it doubles the plan's device
  * memory), and each correction is one GMRES cycle with the mixed operator,
- * solved to max(tol ||b|| / (2 ||r||), 1e-4) relative to its residual r.
+ * solved to max(tol ||b|| / (2 ||r||), 1e-4) relative to its residual r.  The
+ * residual of the initial guess is formed with the mixed operator (the first
+ * correction needs only ~1e-4) unless it is within 10 tol, when FP64 decides.
  * Arrays may be device or host memory.  The first solve allocates the
  * Krylov workspace ((restart + 1) x 3 max_points doubles); later solves with
  * the same or a shorter restart allocate nothing.  Returns GGEM_OK,

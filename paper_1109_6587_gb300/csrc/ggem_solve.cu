@@ -8,8 +8,10 @@
 // FP64 plan: plain restarted GMRES with the FP64 operator.  Each cycle starts
 // from the true residual b - A q.
 // Mixed plan: iterative refinement.  The outer residual b - A64 q is formed
-// with an FP64 twin plan on the same mesh; each correction is one GMRES cycle
-// with the mixed operator, asked only for the accuracy that operator carries.
+// with an FP64 twin plan on the same mesh (the first one of a solve with the
+// mixed operator, as the first correction needs only ~1e-4); each correction
+// is one GMRES cycle with the mixed operator, asked only for the accuracy that
+// operator carries.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -179,10 +181,11 @@ struct Solver {
         return std::sqrt(hs[0]);
     }
 
-    // True residual r = b - A64 x into V_0, its norm returned, V_0 normalised.
-    double residual_into_v0() {
+    // Residual r = b - A x into V_0 (A = Q's operator), its norm returned,
+    // V_0 normalised.
+    double residual_into_v0(ggem_plan_t* Q) {
         double* v0 = P->d_V;
-        apply(P64, x, v0, true);
+        apply(Q, x, v0, true);
         normalize(v0, P->d_sh);
         to_host(1);
         return std::sqrt(hs[0]);
@@ -331,11 +334,17 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
         if (nb == 0.0) {
             GG_CUDA(cudaMemsetAsync(S.x, 0, n3 * sizeof(double), P->st));
         } else {
+            // Mixed plan: the first correction needs only ~1e-4, so its residual
+            // comes from the mixed operator unless that already looks converged.
+            bool first_mixed = !P->fp64;
             for (;;) {
-                double beta = S.residual_into_v0();
+                double beta = S.residual_into_v0(first_mixed ? P : S.P64);
                 rel = beta / nb;
                 GG_CHECK(std::isfinite(rel), GGEM_ERR_NUMERICAL, "non-finite residual");
-                if (rel <= tol) {
+                if (first_mixed) {
+                    first_mixed = false;
+                    if (rel <= 10.0 * tol || its >= maxit) continue;   // decide in FP64
+                } else if (rel <= tol) {
                     result = last_breakdown ? GGEM_OK_BREAKDOWN : GGEM_OK;
                     break;
                 }
