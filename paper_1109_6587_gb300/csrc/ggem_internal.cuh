@@ -196,14 +196,15 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
                       const double* nrm_tgt, int out_mode, T* out, int out_stride,
                       cudaStream_t st);
 
-// element rule: local sum over sorted quadrature points at located mesh nodes
-// (caller index), skipping points of triangles that contain the target
-// (only tested when closer than `near`); layer 0 velocity, 1 double layer
+// element rule: local sum over sorted quadrature points at the sorted mesh
+// nodes tgt (output in caller order), skipping points of triangles that
+// contain the target (only tested when closer than `near`); layer 0
+// velocity, 1 double layer
 template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
-                           const int4* qvs, double near, int n_tgt, const int* tcell,
-                           const v4_t<T>* tpos, const double* nrm_tgt, int layer, T* out,
-                           int out_stride, cudaStream_t st);
+                           const int4* qvs, double near, const SortedSources<T>& tgt,
+                           const double* nrm_tgt, int layer, T* out, int out_stride,
+                           cudaStream_t st);
 cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st);
 
 // exclusive scan of count[0..n) into start[0..n] (start[n] = total)

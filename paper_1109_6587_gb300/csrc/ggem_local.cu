@@ -1,20 +1,17 @@
 // Cell list and GGEM local sums (paper Sec. 3.2.1, Eqs. (local), (u_loc)).
 //
-// Sources are binned into cells no smaller than r_cut and stored as offsets
+// Sources are binned into cells no smaller than r_cut/2 and stored as offsets
 // from their cell's corner, so every displacement is formed from small
 // numbers (integer cell shift + offset difference) and stays accurate in FP32
-// whatever the box size.  x and z are periodic: the neighbour shift of +-1
-// cell carries the minimum image (Sec. 3.2.2, alpha L > 8 makes r_cut < L/2).
+// whatever the box size.  x and z are periodic: the neighbour shift of up to
+// +-2 cells carries the image; as r_cut < L/2 (Sec. 3.2.2, alpha L > 8), at
+// most one image of a source lies within r_cut even where a small grid
+// visits a cell twice.
 #include "ggem_internal.cuh"
+#include "ggem_erfcx.cuh"
 
 namespace ggem {
 
-template <typename T> __device__ __forceinline__ T d_erfc(T x);
-template <> __device__ __forceinline__ float d_erfc<float>(float x) { return erfcf(x); }
-template <> __device__ __forceinline__ double d_erfc<double>(double x) { return erfc(x); }
-template <typename T> __device__ __forceinline__ T d_exp(T x);
-template <> __device__ __forceinline__ float d_exp<float>(float x) { return expf(x); }
-template <> __device__ __forceinline__ double d_exp<double>(double x) { return exp(x); }
 template <typename T> __device__ __forceinline__ T d_rsqrt(T x);
 template <> __device__ __forceinline__ float d_rsqrt<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double d_rsqrt<double>(double x) { return rsqrt(x); }
@@ -150,6 +147,7 @@ cudaError_t gather_strengths(int n, const int* perm, const double* q, const doub
 // FP64 instruction (GB300 issues FP64 at a small fraction of the FP32 rate).
 template <typename T> struct LocalConst {
     T al, al2, rc2, c1, c2, c3, c4, fU, fS, hx, hy, hz;
+    T ke;   // -alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(ke r^2)
 };
 
 template <typename T> LocalConst<T> local_const(const GridGeom& geo, const CellGrid& cg) {
@@ -161,6 +159,7 @@ template <typename T> LocalConst<T> local_const(const GridGeom& geo, const CellG
     k.c3 = (T)(8.0 * a * a * a / sp); k.c4 = (T)(4.0 * a * a * a / sp);
     k.fU = (T)(1.0 / (8.0 * pi * geo.mu)); k.fS = (T)(1.0 / (8.0 * pi));
     k.hx = (T)cg.hx; k.hy = (T)cg.hy; k.hz = (T)cg.hz;
+    k.ke = (T)(-a * a * 1.4426950408889634074);
     return k;
 }
 
@@ -174,6 +173,7 @@ template <typename T> struct LocalArgs {
     int n_tgt;
     const int* tcell;        // TK_POINTS / TK_WALL: located targets (cell, offsets)
     const v4_t<T>* tpos;
+    const int* tperm;        // TK_POINTS: caller index of target t (nullptr: t itself)
     const double* nrm;       // OUT_DBL: [n][3] target normals (caller order)
     T* out;
     int out_stride;
@@ -212,24 +212,102 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
     return cudaGetLastError();
 }
 
+// Pair arithmetic of Eq. (local), shared by the local-sum kernels.
+// exp(-alpha^2 r^2) and erfc(alpha r): in FP32 the exponential is 2^(ke r^2)
+// and erfc = exp(-x^2) erfcx(x) with the polynomial of ggem_erfcx.cuh, so the
+// pair needs one exponential and no erfc call; in FP64 CUDA's exp and erfc.
+template <typename T> struct PairAcc {
+    T ux = 0, uy = 0, uz = 0;
+    T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
+};
+
+__device__ __forceinline__ void exp_erfc(const LocalConst<float>& k, float r2, float x, float& ex,
+                                         float& ec) {
+    ex = exp2f(k.ke * r2);
+    ec = ex * erfcx_poly(x);
+}
+__device__ __forceinline__ void exp_erfc(const LocalConst<double>& k, double r2, double x,
+                                         double& ex, double& ec) {
+    ex = exp(-k.al2 * r2);
+    ec = erfc(x);
+}
+
+// adds G^l g (OUT_U), T^l g (OUT_S) or n . T^l g (OUT_DBL) for displacement
+// (dx, dy, dz) = target - source, 0 < r2 < rc2
+template <typename T, int MODE>
+__device__ __forceinline__ void pair_terms(const LocalConst<T>& k, T dx, T dy, T dz, T r2,
+                                           const v4_t<T>& g, T nx, T ny, T nz, PairAcc<T>& a) {
+    const T ir = d_rsqrt<T>(r2);
+    const T r = r2 * ir;
+    T ex, ec;
+    exp_erfc(k, r2, k.al * r, ex, ec);
+    const T xg = dx * g.x + dy * g.y + dz * g.z;
+    if (MODE & OUT_U) {
+        const T A = ec * ir - k.c1 * ex;
+        const T B = (ec * ir * ir * ir + k.c1 * ex * ir * ir) * xg;
+        a.ux += A * g.x + B * dx;
+        a.uy += A * g.y + B * dy;
+        a.uz += A * g.z + B * dz;
+    }
+    if (MODE & (OUT_S | OUT_DBL)) {
+        const T ir2 = ir * ir;
+        const T D = -(T)6 * ec * ir2 * ir2 * ir - k.c2 * ex * ir2 * ir2 - k.c3 * ex * ir2;
+        const T E = k.c4 * ex;
+        if (MODE & OUT_S) {
+            const T Dx = D * xg;
+            a.sxx += Dx * dx * dx + E * ((T)2 * g.x * dx + xg);
+            a.syy += Dx * dy * dy + E * ((T)2 * g.y * dy + xg);
+            a.szz += Dx * dz * dz + E * ((T)2 * g.z * dz + xg);
+            a.sxy += Dx * dx * dy + E * (g.y * dx + g.x * dy);
+            a.sxz += Dx * dx * dz + E * (g.z * dx + g.x * dz);
+            a.syz += Dx * dy * dz + E * (g.z * dy + g.y * dz);
+        } else {
+            const T xn = dx * nx + dy * ny + dz * nz;
+            const T gn = g.x * nx + g.y * ny + g.z * nz;
+            const T Dxn = D * xg * xn;
+            a.ux += Dxn * dx + E * (dx * gn + g.x * xn + nx * xg);
+            a.uy += Dxn * dy + E * (dy * gn + g.y * xn + ny * xg);
+            a.uz += Dxn * dz + E * (dz * gn + g.z * xn + nz * xg);
+        }
+    }
+}
+
+// scaled output of one target in caller order
+template <typename T, int MODE>
+__device__ __forceinline__ void store_target(const LocalConst<T>& k, const PairAcc<T>& a, T* o) {
+    int c = 0;
+    if (MODE & (OUT_U | OUT_DBL)) {
+        o[0] = k.fU * a.ux; o[1] = k.fU * a.uy; o[2] = k.fU * a.uz;
+        c = 3;
+    }
+    if (MODE & OUT_S) {
+        o[c] = k.fS * a.sxx; o[c + 1] = k.fS * a.sxy; o[c + 2] = k.fS * a.sxz;
+        o[c + 3] = k.fS * a.syy; o[c + 4] = k.fS * a.syz; o[c + 5] = k.fS * a.szz;
+    }
+}
+
 // u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
 // (unscaled in the loop; the caller-facing factors are applied at the end).
 //
-// One warp per target.  Lane c < 27 looks up neighbour cell c; a warp scan
-// concatenates the 27 source ranges, and the lanes stride over the
-// concatenated list, so consecutive lanes load consecutive sorted sources
-// (coalesced float4 loads) whatever the cell sizes.  Partial sums are reduced
-// with warp shuffles.
-constexpr int LW = 8;   // warps (targets) per block
+// One warp per target.  The warp lists the neighbour cells (offsets -2..2)
+// that come within r_cut of the target, then walks them one at a time with
+// consecutive lanes on consecutive sorted sources (coalesced float4 loads).
+// The hits are compacted into a per-warp queue and evaluated 32 at a time.
+// Partial sums are reduced with warp shuffles.
+constexpr int LW = 8;       // warps (targets) per block
+constexpr int kQueue = 64;  // hit queue per warp: < 32 left + <= 32 new always fit
+constexpr int kNb = 125;    // neighbour cell offsets -2..2 in each direction
 
 // ELEM: sources are element quadrature points and targets are mesh nodes
 // (caller index t); points of triangles having the target as a vertex are
 // skipped (their integral is done by the polar rule, Sec. 3.4.1).
 template <typename T, int KIND, int MODE, bool ELEM = false>
 __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
-    __shared__ int s_base[LW][32];
-    __shared__ int s_end[LW][32];
-    __shared__ T s_sh[LW][27][3];
+    __shared__ int s_cst[LW][kNb];            // this target's cells: first source,
+    __shared__ int s_cnt[LW][kNb];            //   source count,
+    __shared__ int s_off[LW][kNb];            //   neighbour offset index
+    __shared__ v4_t<T> s_qd[LW][kQueue];     // queued hits: displacement, r^2
+    __shared__ int s_qs[LW][kQueue];         // queued hits: sorted source index
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * LW + wid;
     if (t >= a.n_tgt) return;                     // warp-uniform
@@ -246,112 +324,134 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         } else {
             p = a.tpos[t];
             c = a.tcell[t];
+            if (a.tperm) oidx = a.tperm[t];
         }
         ox = p.x; oy = p.y; oz = p.z;
         cx = c % cg.ncx;
         cy = (c / cg.ncx) % cg.ncy;
         cz = c / (cg.ncx * cg.ncy);
     }
-    // neighbour cells: lane c < 27 -> offsets (c % 3 - 1, (c / 3) % 3 - 1, c / 9 - 1)
-    int cnt = 0, st = 0;
-    if (lane < 27) {
-        int dxc = lane % 3 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane / 9 - 1;
-        int cyy = cy + dyc;
-        if (cyy >= 0 && cyy < cg.ncy) {
-            int cxx = cx + dxc, czz = cz + dzc;
-            cxx += (cxx < 0) ? cg.ncx : 0;
-            cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
-            czz += (czz < 0) ? cg.ncz : 0;
-            czz -= (czz >= cg.ncz) ? cg.ncz : 0;
-            int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
-            st = a.src.cell_start[c];
-            cnt = a.src.cell_start[c + 1] - st;
-        }
-        s_sh[wid][lane][0] = -(T)dxc * a.k.hx + ox;
-        s_sh[wid][lane][1] = -(T)dyc * a.k.hy + oy;
-        s_sh[wid][lane][2] = -(T)dzc * a.k.hz + oz;
-    }
-    int inc = cnt;
+    // Neighbour cells at offsets -2..2 (cells are at least r_cut/2 wide); keep
+    // the non-empty ones whose nearest point lies within r_cut of the target
+    // (a slightly widened r_cut, so rounding can only keep more).
+    const unsigned lt = (1u << lane) - 1u;
+    const T reach2 = a.k.rc2 * (T)1.0001;
+    int nc = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
+    for (int r = 0; r < 4; ++r) {
+        const int oi = r * 32 + lane;
+        bool keep = false;
+        int st = 0, cnt = 0;
+        if (oi < kNb) {
+            const int ix = oi % 5 - 2, iy = (oi / 5) % 5 - 2, iz = oi / 25 - 2;
+            const int cyy = cy + iy;
+            if (cyy >= 0 && cyy < cg.ncy) {
+                const T gx = ix > 0 ? (T)ix * a.k.hx - ox : (ix < 0 ? ox - (T)(ix + 1) * a.k.hx : (T)0);
+                const T gy = iy > 0 ? (T)iy * a.k.hy - oy : (iy < 0 ? oy - (T)(iy + 1) * a.k.hy : (T)0);
+                const T gz = iz > 0 ? (T)iz * a.k.hz - oz : (iz < 0 ? oz - (T)(iz + 1) * a.k.hz : (T)0);
+                if (gx * gx + gy * gy + gz * gz <= reach2) {
+                    int cxx = cx + ix, czz = cz + iz;
+                    cxx += (cxx < 0) ? cg.ncx : 0;
+                    cxx += (cxx < 0) ? cg.ncx : 0;
+                    cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
+                    cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
+                    czz += (czz < 0) ? cg.ncz : 0;
+                    czz += (czz < 0) ? cg.ncz : 0;
+                    czz -= (czz >= cg.ncz) ? cg.ncz : 0;
+                    czz -= (czz >= cg.ncz) ? cg.ncz : 0;
+                    const int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
+                    st = a.src.cell_start[c];
+                    cnt = a.src.cell_start[c + 1] - st;
+                    keep = cnt > 0;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int slot = nc + __popc(m & lt);
+            s_cst[wid][slot] = st;
+            s_cnt[wid][slot] = cnt;
+            s_off[wid][slot] = oi;
+        }
+        nc += __popc(m);
     }
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
-    s_base[wid][lane] = st - (inc - cnt);         // source index = base + candidate index
-    s_end[wid][lane] = (lane < 27) ? inc : 0x7fffffff;
     __syncwarp();
 
     T nx = 0, ny = 0, nz = 0;
     if (MODE & OUT_DBL) {
         nx = (T)a.nrm[3 * oidx]; ny = (T)a.nrm[3 * oidx + 1]; nz = (T)a.nrm[3 * oidx + 2];
     }
-    const T al = a.k.al, al2 = a.k.al2, rc2 = a.k.rc2;
-    const T c1 = a.k.c1, c2 = a.k.c2, c3 = a.k.c3, c4 = a.k.c4;
-    T ux = 0, uy = 0, uz = 0;
-    T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
-    int cell = 0;
-    for (int idx = lane; idx < total; idx += 32) {
-        while (idx >= s_end[wid][cell]) ++cell;
-        const int s = s_base[wid][cell] + idx;
-        v4_t<T> p = a.src.pos[s];
-        T dx = s_sh[wid][cell][0] - p.x, dy = s_sh[wid][cell][1] - p.y,
-          dz = s_sh[wid][cell][2] - p.z;
-        T r2 = dx * dx + dy * dy + dz * dz;
-        if (!(r2 < rc2 && r2 > (T)0)) continue;
-        if (ELEM && r2 < a.near2) {
-            int4 v = a.qvs[s];
-            if (v.x == oidx || v.y == oidx || v.z == oidx) continue;
-        }
-        v4_t<T> g = a.src.g[s];
-        T ir = d_rsqrt<T>(r2);
-        T r = r2 * ir;
-        T ec = d_erfc<T>(al * r);
-        T ex = d_exp<T>(-al2 * r2);
-        T xg = dx * g.x + dy * g.y + dz * g.z;
-        if (MODE & OUT_U) {
-            T A = ec * ir - c1 * ex;
-            T B = (ec * ir * ir * ir + c1 * ex * ir * ir) * xg;
-            ux += A * g.x + B * dx;
-            uy += A * g.y + B * dy;
-            uz += A * g.z + B * dz;
-        }
-        if (MODE & (OUT_S | OUT_DBL)) {
-            T ir2 = ir * ir;
-            T D = -(T)6 * ec * ir2 * ir2 * ir - c2 * ex * ir2 * ir2 - c3 * ex * ir2;
-            T E = c4 * ex;
-            if (MODE & OUT_S) {
-                T Dx = D * xg;
-                sxx += Dx * dx * dx + E * ((T)2 * g.x * dx + xg);
-                syy += Dx * dy * dy + E * ((T)2 * g.y * dy + xg);
-                szz += Dx * dz * dz + E * ((T)2 * g.z * dz + xg);
-                sxy += Dx * dx * dy + E * (g.y * dx + g.x * dy);
-                sxz += Dx * dx * dz + E * (g.z * dx + g.x * dz);
-                syz += Dx * dy * dz + E * (g.z * dy + g.y * dz);
-            } else {
-                T xn = dx * nx + dy * ny + dz * nz;
-                T gn = g.x * nx + g.y * ny + g.z * nz;
-                T Dxn = D * xg * xn;
-                ux += Dxn * dx + E * (dx * gn + g.x * xn + nx * xg);
-                uy += Dxn * dy + E * (dy * gn + g.y * xn + ny * xg);
-                uz += Dxn * dz + E * (dz * gn + g.z * xn + nz * xg);
+    const T rc2 = a.k.rc2;
+    PairAcc<T> acc;
+    // Lanes test consecutive sources of one cell at a time; hits go to a
+    // per-warp ring queue (ballot + popc ranks) and the pair arithmetic runs on
+    // 32 queued hits at a time, so no lane idles through it on a miss.
+    int head = 0, qn = 0;                         // warp-uniform
+    for (int ci = 0; ci < nc; ++ci) {
+        const int st = s_cst[wid][ci], cnt = s_cnt[wid][ci], oi = s_off[wid][ci];
+        // target position in the frame of this source cell's corner
+        const T tx = ox - (T)(oi % 5 - 2) * a.k.hx;
+        const T ty = oy - (T)((oi / 5) % 5 - 2) * a.k.hy;
+        const T tz = oz - (T)(oi / 25 - 2) * a.k.hz;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            bool hit = false;
+            T dx = 0, dy = 0, dz = 0, r2 = 0;
+            int s = 0;
+            if (i < cnt) {
+                s = st + i;
+                const v4_t<T> p = a.src.pos[s];
+                dx = tx - p.x;
+                dy = ty - p.y;
+                dz = tz - p.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                hit = r2 < rc2 && r2 > (T)0;
+                if (ELEM && hit && r2 < a.near2) {
+                    const int4 v = a.qvs[s];
+                    hit = !(v.x == oidx || v.y == oidx || v.z == oidx);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const int slot = (head + qn + __popc(m & lt)) & (kQueue - 1);
+                v4_t<T> d;
+                d.x = dx; d.y = dy; d.z = dz; d.w = r2;
+                s_qd[wid][slot] = d;
+                s_qs[wid][slot] = s;
+            }
+            qn += __popc(m);
+            if (qn >= 32) {
+                __syncwarp();
+                const int slot = (head + lane) & (kQueue - 1);
+                const v4_t<T> d = s_qd[wid][slot];
+                pair_terms<T, MODE>(a.k, d.x, d.y, d.z, d.w, a.src.g[s_qs[wid][slot]], nx, ny,
+                                    nz, acc);
+                head = (head + 32) & (kQueue - 1);
+                qn -= 32;
+                __syncwarp();
             }
         }
+    }
+    __syncwarp();
+    if (lane < qn) {
+        const int slot = (head + lane) & (kQueue - 1);
+        const v4_t<T> d = s_qd[wid][slot];
+        pair_terms<T, MODE>(a.k, d.x, d.y, d.z, d.w, a.src.g[s_qs[wid][slot]], nx, ny, nz, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         if (MODE & (OUT_U | OUT_DBL)) {
-            ux += __shfl_xor_sync(0xffffffffu, ux, o);
-            uy += __shfl_xor_sync(0xffffffffu, uy, o);
-            uz += __shfl_xor_sync(0xffffffffu, uz, o);
+            acc.ux += __shfl_xor_sync(0xffffffffu, acc.ux, o);
+            acc.uy += __shfl_xor_sync(0xffffffffu, acc.uy, o);
+            acc.uz += __shfl_xor_sync(0xffffffffu, acc.uz, o);
         }
         if (MODE & OUT_S) {
-            sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
-            sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
-            sxz += __shfl_xor_sync(0xffffffffu, sxz, o);
-            syy += __shfl_xor_sync(0xffffffffu, syy, o);
-            syz += __shfl_xor_sync(0xffffffffu, syz, o);
-            szz += __shfl_xor_sync(0xffffffffu, szz, o);
+            acc.sxx += __shfl_xor_sync(0xffffffffu, acc.sxx, o);
+            acc.sxy += __shfl_xor_sync(0xffffffffu, acc.sxy, o);
+            acc.sxz += __shfl_xor_sync(0xffffffffu, acc.sxz, o);
+            acc.syy += __shfl_xor_sync(0xffffffffu, acc.syy, o);
+            acc.syz += __shfl_xor_sync(0xffffffffu, acc.syz, o);
+            acc.szz += __shfl_xor_sync(0xffffffffu, acc.szz, o);
         }
     }
     if (lane != 0) return;
@@ -361,23 +461,12 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         const int nxz = a.geo.Nz * a.geo.Nx;
         const int wall = t / nxz, rem = t - wall * nxz;
         T* o = a.out + (size_t)wall * 3 * nxz + rem;
-        o[0] = f * ux;
-        o[nxz] = f * uy;
-        o[2 * nxz] = f * uz;
+        o[0] = f * acc.ux;
+        o[nxz] = f * acc.uy;
+        o[2 * nxz] = f * acc.uz;
         return;
     }
-    T* o = a.out + (size_t)oidx * a.out_stride;
-    int k = 0;
-    if (MODE & (OUT_U | OUT_DBL)) {
-        const T f = a.k.fU;
-        o[0] = f * ux; o[1] = f * uy; o[2] = f * uz;
-        k = 3;
-    }
-    if (MODE & OUT_S) {
-        const T f = a.k.fS;
-        o[k] = f * sxx; o[k + 1] = f * sxy; o[k + 2] = f * sxz;
-        o[k + 3] = f * syy; o[k + 4] = f * syz; o[k + 5] = f * szz;
-    }
+    store_target<T, MODE>(a.k, acc, a.out + (size_t)oidx * a.out_stride);
 }
 
 template <typename T, int KIND>
@@ -394,13 +483,15 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
 
 template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
-                           const int4* qvs, double near, int n_tgt, const int* tcell,
-                           const v4_t<T>* tpos, const double* nrm_tgt, int layer, T* out,
-                           int out_stride, cudaStream_t st) {
-    if (n_tgt <= 0) return cudaSuccess;
-    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), n_tgt, tcell,
-                   tpos, nrm_tgt, out, out_stride};
-    dim3 b(LW * 32), g((n_tgt + LW - 1) / LW);
+                           const int4* qvs, double near, const SortedSources<T>& tgt,
+                           const double* nrm_tgt, int layer, T* out, int out_stride,
+                           cudaStream_t st) {
+    if (tgt.n <= 0) return cudaSuccess;
+    // targets: the mesh nodes in cell order, so the warps of a block mostly
+    // scan the same candidate cells (L1 reuse); output in caller order
+    LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
+                   tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
+    dim3 b(LW * 32), g((tgt.n + LW - 1) / LW);
     if (layer == 0) k_local<T, TK_POINTS, OUT_U, true><<<g, b, 0, st>>>(a);
     else k_local<T, TK_POINTS, OUT_DBL, true><<<g, b, 0, st>>>(a);
     return cudaGetLastError();
@@ -413,7 +504,7 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
                       cudaStream_t st) {
     if (n_tgt <= 0) return cudaSuccess;
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, nullptr, (T)0, n_tgt, tcell, tpos,
-                   nrm_tgt, out, out_stride};
+                   nullptr, nrm_tgt, out, out_stride};
     if (kind == TK_SORTED) launch_kind<T, TK_SORTED>(a, out_mode, st);
     else if (kind == TK_POINTS) launch_kind<T, TK_POINTS>(a, out_mode, st);
     else launch_kind<T, TK_WALL>(a, OUT_U, st);
@@ -432,9 +523,9 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
     template cudaError_t locate_targets<T>(const GridGeom&, const CellGrid&, int, int,        \
                                            const double*, int*, v4_t<T>*, cudaStream_t);       \
     template cudaError_t local_sum_elem<T>(const GridGeom&, const CellGrid&,                  \
-                                           const SortedSources<T>&, const int4*, double, int,   \
-                                           const int*, const v4_t<T>*, const double*, int, T*,  \
-                                           int, cudaStream_t);
+                                           const SortedSources<T>&, const int4*, double,        \
+                                           const SortedSources<T>&, const double*, int, T*, int, \
+                                           cudaStream_t);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

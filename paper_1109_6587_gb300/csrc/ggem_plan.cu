@@ -270,9 +270,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         qs.cell_start = P->d_qp_start;
         qs.n = P->n_qp;
         stage(P, ST_LOCAL, 1, [&] {
-            GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, n,
-                                      P->d_node_cell, (const v4_t<T>*)P->d_node_pos, P->d_nrm,
-                                      layer, loc, 3, st));
+            GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
+                                      P->d_nrm, layer, loc, 3, st));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
@@ -347,9 +346,11 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     P->fp64 = prm.precision == GGEM_FP64;
     P->nmodes = prm.Nz * g.nkx;
     CellGrid& cg = P->cg;
-    cg.ncx = std::max(1, (int)std::floor(prm.Lx / g.rcut));
-    cg.ncz = std::max(1, (int)std::floor(prm.Lz / g.rcut));
-    cg.ncy = std::max(1, (int)std::floor(prm.W / g.rcut));
+    // cells at least r_cut/2 wide: the local sums search +-2 cells and keep
+    // those within r_cut of each target
+    cg.ncx = std::max(1, (int)std::floor(prm.Lx / (0.5 * g.rcut)));
+    cg.ncz = std::max(1, (int)std::floor(prm.Lz / (0.5 * g.rcut)));
+    cg.ncy = std::max(1, (int)std::floor(prm.W / (0.5 * g.rcut)));
     cg.hx = prm.Lx / cg.ncx; cg.hz = prm.Lz / cg.ncz; cg.hy = prm.W / cg.ncy;
     cg.y0 = prm.y0;
     P->ncell = cg.ncx * cg.ncy * cg.ncz;

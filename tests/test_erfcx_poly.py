@@ -1,0 +1,39 @@
+"""The FP32 pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the degree-16
+polynomial of ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff).
+Its coefficients, read from the generated header, must approximate scipy's
+erfcx to 1e-8 relative in FP64 and to 4e-7 (a few FP32 ulps, like CUDA's
+erfcf) when evaluated in FP32 by the same Horner scheme."""
+import pathlib
+import re
+
+import numpy as np
+import pytest
+
+special = pytest.importorskip("scipy.special")
+
+HDR = pathlib.Path(__file__).resolve().parents[1] / "paper_1109_6587_gb300" / "csrc" / "ggem_erfcx.cuh"
+
+
+def _coefficients():
+    txt = HDR.read_text()
+    first = re.search(r"float p = ([-+0-9.eE]+)f;", txt).group(1)
+    rest = re.findall(r"p = fmaf\(p, u, ([-+0-9.eE]+)f\);", txt)
+    return [float(first)] + [float(v) for v in rest]    # highest degree first
+
+
+def test_polynomial_error():
+    c = _coefficients()
+    assert len(c) == 17
+    x = np.linspace(0.0, 4.0, 100001)
+    ref = special.erfcx(x)
+    u = x / 2 - 1
+    p = np.full_like(u, c[0])
+    for a in c[1:]:
+        p = p * u + a
+    assert np.abs(p / ref - 1).max() < 1e-8
+    x32 = x.astype(np.float32)
+    u32 = (x32 * np.float32(0.5) - np.float32(1)).astype(np.float32)
+    p32 = np.full_like(u32, np.float32(c[0]))
+    for a in c[1:]:
+        p32 = (p32 * u32 + np.float32(a)).astype(np.float32)
+    assert np.abs(p32.astype(np.float64) / ref - 1).max() < 4e-7
