@@ -169,7 +169,11 @@ ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
  *           A applied in FP64 (the paper stops at 1e-4 on the residual)
  *   restart GMRES cycle length m, 1..64
  *   maxit   limit on Arnoldi steps (operator applications inside cycles)
- *   use_mlp must be 0: no learned warm start is loaded in this library
+ *   use_mlp 0: start from q.  1: also form the learned guess q + delta,
+ *           delta the network's estimate of A^-1 r0 for r0 = b - A q, and
+ *           start from whichever of q and q + delta has the lower relative
+ *           residual under the plan's operator (needs ggem_mesh_particles and
+ *           a model from ggem_mlp_load or ggem_mlp_train).
  *   iters, true_relres  (out, may be NULL) Arnoldi steps taken and the final
  *           true relative residual
  * Method: restarted GMRES with FP64 Arnoldi vectors (classical Gram-Schmidt
@@ -192,6 +196,12 @@ ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
 ggem_status bie_solve(ggem_plan_t *plan, const double *kappa, const double *b, double *q,
                       double tol, int restart, int maxit, int use_mlp, int *iters,
                       double *true_relres);
+
+/* The last bie_solve's initial guess: used_mlp = 1 when it started from the
+ * learned guess, and the relative residuals of the caller's and the learned
+ * guess (0 when use_mlp was 0). */
+ggem_status ggem_solve_guess(const ggem_plan_t *plan, int *used_mlp, double *relres_plain,
+                             double *relres_mlp);
 
 /* Work counts of the last bie_solve on this plan: GMRES cycles, operator
  * applications in FP64 and with the mixed operator. */
@@ -229,6 +239,65 @@ ggem_status ggem_solve_stats(const ggem_plan_t *plan, int *cycles, int *matvec_f
 ggem_status ggem_local_velocity_noalloc(const ggem_params *params, void *stream, int n_src,
                                         const double *x_src, const double *g, int n_tgt,
                                         const double *x_tgt, int tgt_is_src, double *u);
+
+/* (I + kappa/(4 pi) D) q at the mesh nodes, D as in ggem_double_layer:
+ * kappa [n_nodes], q and out [n_nodes][3]. */
+ggem_status ggem_bie_operator(ggem_plan_t *plan, const double *kappa, const double *q,
+                              double *out);
+
+/*
+ * Learned warm start (no counterpart in the paper, which starts GMRES from the
+ * previous time step, Sec. 5).  A 12-128-128-128-3 ReLU network estimates
+ * A^-1 r - r node by node, A = I + kappa/(4 pi) D, for a right-hand side r
+ * (the residual of a guess), from 12 features:
+ *   0-2 r/s; 3-5 (kappa/4 pi)(D r)/s; 6-8 the node normal; 9 kappa;
+ *   10 min(y - y0, y0 + W - y); 11 nodes of other particles within r_cut
+ *   divided by the node count of the node's particle;
+ * s = rms(r) over all nodes and components, so the estimate scales with r.
+ * Inputs are standardised, (f - mu)/sigma; weights and hidden activations are
+ * bfloat16 (round to nearest even), products accumulate in FP32:
+ *   A^-1 r ~ r + s s_y MLP((f - mu)/sigma).
+ * A model is 25 + 35075 doubles: mu[12], sigma[12], s_y, then W1[12][128],
+ * b1[128], W2[128][128], b2[128], W3[128][128], b3[128], W4[128][3], b4[3]
+ * (W[fan_in][fan_out]).  The first call that needs the model's buffers
+ * allocates them.
+ */
+
+/* Particle id of each node (caller order), ids in [0, n_particles); needed
+ * by the features.  Call after ggem_mesh_set. */
+ggem_status ggem_mesh_particles(ggem_plan_t *plan, int n_particles, const int *particle);
+
+/* The 12 features [n_nodes][12] of the right-hand side r [n_nodes][3] on the
+ * current mesh (one double-layer evaluation), and s = rms(r) (may be NULL). */
+ggem_status ggem_mlp_features(ggem_plan_t *plan, const double *kappa, const double *r,
+                              double *feat, double *scale);
+
+/* delta [n_nodes][3] = the learned estimate of A^-1 r. */
+ggem_status ggem_mlp_guess(ggem_plan_t *plan, const double *kappa, const double *r,
+                           double *delta);
+
+/* Load / save a model (count = 25 + 35075 doubles, layout above). */
+ggem_status ggem_mlp_load(ggem_plan_t *plan, const double *model, size_t count);
+ggem_status ggem_mlp_save(ggem_plan_t *plan, double *model, size_t count);
+
+/* Raw network output [n][3] (units of s_y) for n feature rows [n][12]. */
+ggem_status ggem_mlp_forward(ggem_plan_t *plan, int n, const double *feat, double *out);
+
+/*
+ * Train on n samples: features [n][12] and targets (A^-1 r - r)/s [n][3].
+ * init != 0 starts a fresh model: mu, sigma (1 for a constant feature) and
+ * s_y = rms(target) from these samples, He-uniform weights from seed, zero
+ * biases.  Then `epochs` passes over minibatches of `batch` rows in an order
+ * shuffled from seed; loss = mean over rows and components of
+ * (output - target/s_y)^2; Adam (0.9, 0.999, 1e-8) at rate lr on FP32 master
+ * weights.  *loss (may be NULL) gets the mean minibatch loss of the last
+ * epoch.  With epochs = 0, one full-batch pass in row order computes *loss
+ * and, when grad_out is not NULL, the gradient [35075] without updating.
+ * Allocates and frees its own staging buffers.
+ */
+ggem_status ggem_mlp_train(ggem_plan_t *plan, int n, const double *feat, const double *target,
+                           int init, unsigned long long seed, int epochs, int batch, double lr,
+                           double *loss, double *grad_out);
 
 /*
  * Tracing (no counterpart in the paper).  With tracing enabled, each stage

@@ -5,25 +5,29 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 bench's CPU-baseline leg may import this module.  It shares no code with the
 CUDA library.
 
-The paper solves the Fredholm system of Sec. 5 by GMRES from the previous time
-step's density and uses no preconditioner.  The learned part predicts each
-node's density correction q - b from local geometry, to serve as a GMRES
-initial guess.  Its definitions (readings; the paper has no counterpart):
+The paper solves the Fredholm system of Sec. 5, A q = b with
+A = I + (kappa/4 pi) D, by GMRES from the previous time step's density and
+uses no preconditioner.  The learned part approximates A^-1 r - r node by node
+for a right-hand side r (b itself, or the residual b - A q_prev of a guess),
+to serve as a GMRES initial guess q_prev + A^-1 r.  Its definitions (readings;
+the paper has no counterpart):
 
+  scale s = rms(r) over all nodes and components; the network sees r / s and
+  predicts (A^-1 r - r) / (s s_y), so it applies to right-hand sides of any
+  size (A^-1 is linear).
   features, 12 per node (caller order):
-    0-2  b                                  right-hand side of the system
-    3-5  n                                  area-averaged unit node normal
-    6    H = -2 sum_j (x_j - x_b).n_b / sum_j |x_j - x_b|^2 over the distinct
-         1-ring neighbours j (= 1/a on a sphere of radius a, up to the mesh)
-    7-8  y - y0 and y0 + W - y              distances to the two walls
+    0-2  r / s
+    3-5  (kappa / 4 pi) (D r) / s           one application of the double layer
+    6-8  n                                  area-averaged unit node normal
     9    kappa                              (lambda - 1)/(lambda + 1) of the node
-    10   crowding: nodes of OTHER particles within r_cut (minimum image in
+    10   min(y - y0, y0 + W - y)            distance to the nearer wall
+    11   crowding: nodes of OTHER particles within r_cut (minimum image in
          x, z), divided by the node count of the node's own particle
-    11   mean over the 1-ring neighbours of q_prev_j . n_b (0 without q_prev)
   network: 12 -> 128 -> 128 -> 128 -> 3, ReLU on the hidden layers; inputs
     standardised by (f - mu)/sigma, outputs scaled by s_y:
-      q - b = s_y * MLP((f - mu)/sigma)
-  loss: mean over nodes and components of (pred - target)^2 in units of s_y.
+      A^-1 r - r ~ s * s_y * MLP((f - mu)/sigma)
+  loss: mean over nodes and components of (output - target / s_y)^2, target
+    (A^-1 r - r) / s.
   BF16 rounding points (when bf16=True): the standardised input, every weight
     matrix and every hidden activation are rounded to bfloat16 (round to
     nearest even); products accumulate without rounding.
@@ -45,32 +49,19 @@ def bf16(a):
     return (r.astype(np.uint32)).view(np.float32).astype(np.float64)
 
 
-def ring_neighbours(tri, n):
-    """Distinct 1-ring neighbour lists of the n nodes."""
-    nb = [set() for _ in range(n)]
-    for a, b, c in np.asarray(tri):
-        nb[a].update((b, c))
-        nb[b].update((a, c))
-        nb[c].update((a, b))
-    return [sorted(s) for s in nb]
-
-
-def features(box, x, tri, particle, kappa, b, rcut, normals, q_prev=None):
-    """The 12 features per node (module docstring), [n, 12] FP64."""
+def features(box, kappa, r, Dr, rcut, x, particle, normals):
+    """The 12 features per node (module docstring) for the right-hand side r
+    [n, 3] with its double layer Dr [n, 3]; returns (F [n, 12] FP64, s)."""
     x = np.asarray(x, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
     n = x.shape[0]
-    nb = ring_neighbours(tri, n)
+    s = math.sqrt((r * r).mean())
     F = np.zeros((n, NF))
-    F[:, 0:3] = b
-    F[:, 3:6] = normals
-    for i in range(n):
-        d = x[nb[i]] - x[i]
-        F[i, 6] = -2.0 * (d @ normals[i]).sum() / (d * d).sum()
-        if q_prev is not None:
-            F[i, 11] = (np.asarray(q_prev)[nb[i]] @ normals[i]).mean()
-    F[:, 7] = x[:, 1] - box.y0
-    F[:, 8] = box.y0 + box.W - x[:, 1]
+    F[:, 0:3] = r / s
+    F[:, 3:6] = (np.asarray(kappa)[:, None] / (4.0 * math.pi)) * np.asarray(Dr) / s
+    F[:, 6:9] = normals
     F[:, 9] = kappa
+    F[:, 10] = np.minimum(x[:, 1] - box.y0, box.y0 + box.W - x[:, 1])
     particle = np.asarray(particle)
     counts = np.bincount(particle)
     for i in range(n):
@@ -78,9 +69,9 @@ def features(box, x, tri, particle, kappa, b, rcut, normals, q_prev=None):
         d[:, 0] -= box.Lx * np.round(d[:, 0] / box.Lx)
         d[:, 2] -= box.Lz * np.round(d[:, 2] / box.Lz)
         r2 = (d * d).sum(1)
-        F[i, 10] = np.count_nonzero((r2 < rcut * rcut) & (particle != particle[i]))
-        F[i, 10] /= counts[particle[i]]
-    return F
+        F[i, 11] = np.count_nonzero((r2 < rcut * rcut) & (particle != particle[i]))
+        F[i, 11] /= counts[particle[i]]
+    return F, s
 
 
 def init_params(seed):

@@ -220,7 +220,8 @@ cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri
                        int* adj_cnt, int* adj_start, int* adj_cur, int* adj,
                        cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    k_qp_gen<T><<<(m * 16 + 255) / 256, 256, 0, st>>>(m, x, tri, tri_area, rule, xq, qv, qw);
+    if (xq)      // quadrature points (element rule only); the adjacency always
+        k_qp_gen<T><<<(m * 16 + 255) / 256, 256, 0, st>>>(m, x, tri, tri_area, rule, xq, qv, qw);
     cudaMemsetAsync(adj_cnt, 0, nnodes * sizeof(int), st);
     cudaMemsetAsync(adj_cur, 0, nnodes * sizeof(int), st);
     k_adj_count<<<(m + 255) / 256, 256, 0, st>>>(m, tri, adj_cnt);

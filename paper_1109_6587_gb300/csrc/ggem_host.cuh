@@ -131,4 +131,9 @@ void stage(ggem_plan_t* P, int id, int nk, F&& f) {
 // arrays [n_nodes][3]); defined with the layer pipeline
 void double_layer_dev(ggem_plan_t* P, const double* q, double* v);
 
+// out = base + A^-1 r estimated by the learned warm start (device arrays;
+// base may be NULL); defined with the network kernels
+void mlp_guess_dev(ggem_plan_t* P, const double* kappa, const double* r, const double* base,
+                   double* out);
+
 }  // namespace ggem

@@ -164,6 +164,27 @@ struct ggem_plan {
     ggem_plan* twin = nullptr;         // FP64 plan on the same mesh (mixed plans)
     int sol_iters = 0, sol_cycles = 0, sol_mv64 = 0, sol_mvmix = 0;
     double sol_relres = 0.0;
+    // learned warm start (allocated by its first use)
+    int* d_particle = nullptr;         // [cap] particle id of each node (caller order)
+    int* d_pcount = nullptr;           // [pcount_cap + 1] nodes per particle, error flag
+    int pcount_cap = 0, n_particles = 0;
+    float* d_feat = nullptr;           // [cap][12] features
+    float* d_mlp = nullptr;            // [35075] FP32 master parameters
+    float* d_mlp_grad = nullptr;       // gradient accumulator
+    float* d_mlp_m = nullptr;          // Adam first moments
+    float* d_mlp_v = nullptr;          // Adam second moments
+    unsigned short* d_mlp_wf = nullptr;  // bfloat16 weights [fan_in][fan_out]
+    unsigned short* d_mlp_wt = nullptr;  // bfloat16 weights [fan_out][fan_in]
+    float* d_mlp_stats = nullptr;      // mu[12], sigma[12], s_y
+    float* d_mlp_out = nullptr;        // [cap][3] network output
+    double* d_smlp = nullptr;          // [3 cap] learned guess of the solve
+    double* d_sres = nullptr;          // [3 cap] residual of the caller's guess
+    double* d_mlp_dr = nullptr;        // [3 cap] D r of the features
+    double* d_mlp_ssq = nullptr;       // sum of r^2 of the features
+    bool mlp_ready = false;
+    long mlp_step = 0;
+    int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
+    double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
     double prof_ms[16] = {0};
     long prof_calls[16] = {0};
     long launches = 0;                 // kernels launched by this plan

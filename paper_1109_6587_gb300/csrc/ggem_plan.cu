@@ -548,7 +548,10 @@ void plan_free(ggem_plan_t* P) {
                     P->d_qp_perm, P->d_qp_start, P->d_qp_pos, P->d_qg, P->d_adj_cnt,
                     P->d_adj_start, P->d_adj_cur, P->d_adj, P->d_node_cell, P->d_node_pos,
                     P->d_qv_sorted, P->d_V, P->d_sv, P->d_sb, P->d_sk, P->d_sx,
-                    P->d_spart, P->d_sh};
+                    P->d_spart, P->d_sh, P->d_particle, P->d_pcount, P->d_feat,
+                    P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
+                    P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
+                    P->d_sres, P->d_mlp_dr, P->d_mlp_ssq};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -646,20 +649,22 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                                           P->d_mesh_sdi, (float4*)P->d_mesh_sdf, st));
         }
         const bool elem = P->prm.quadrature == GGEM_ELEMENT && n_tris > 0;
-        if (elem) {
-            // the quadrature-point and adjacency buffers exist only in element-rule plans
-            GG_CHECK(P->d_qx && P->d_qv && P->d_qw && P->d_adj, GGEM_ERR_INVALID_ARG,
-                     "element buffers missing");
+        if (n_tris > 0) {
+            // node -> triangle adjacency (element correction, ring features) and,
+            // in element-rule plans, the quadrature points
+            if (elem)
+                GG_CHECK(P->d_qx && P->d_qv && P->d_qw, GGEM_ERR_INVALID_ARG,
+                         "element buffers missing");
             if (P->fp64)
                 GG_CUDA(elem_setup<double>(n_tris, P->d_x, P->d_tri, P->d_tri_area, P->rule,
-                                           P->d_qx, P->d_qv, (double4_32a*)P->d_qw, n_nodes,
-                                           P->d_adj_cnt, P->d_adj_start, P->d_adj_cur, P->d_adj,
-                                           st));
+                                           elem ? P->d_qx : nullptr, P->d_qv,
+                                           (double4_32a*)P->d_qw, n_nodes, P->d_adj_cnt,
+                                           P->d_adj_start, P->d_adj_cur, P->d_adj, st));
             else
                 GG_CUDA(elem_setup<float>(n_tris, P->d_x, P->d_tri, P->d_tri_area, P->rule,
-                                          P->d_qx, P->d_qv, (float4*)P->d_qw, n_nodes,
-                                          P->d_adj_cnt, P->d_adj_start, P->d_adj_cur, P->d_adj,
-                                          st));
+                                          elem ? P->d_qx : nullptr, P->d_qv, (float4*)P->d_qw,
+                                          n_nodes, P->d_adj_cnt, P->d_adj_start, P->d_adj_cur,
+                                          P->d_adj, st));
         }
         P->n_qp = 0;
         if (elem) {

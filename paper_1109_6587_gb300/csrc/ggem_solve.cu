@@ -308,7 +308,9 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
         GG_CHECK(restart >= 1 && restart <= KMAXM, GGEM_ERR_INVALID_ARG,
                  "restart must be in 1..64");
         GG_CHECK(maxit >= 0, GGEM_ERR_INVALID_ARG, "maxit must be >= 0");
-        GG_CHECK(!use_mlp, GGEM_ERR_INVALID_ARG, "no learned warm start is loaded");
+        GG_CHECK(use_mlp == 0 || use_mlp == 1, GGEM_ERR_INVALID_ARG, "use_mlp must be 0 or 1");
+        GG_CHECK(!use_mlp || (P->mlp_ready && P->d_particle), GGEM_ERR_INVALID_ARG,
+                 "the learned warm start needs a model and particle ids");
         ensure_solver_ws(P, restart);
         ensure_twin(P);
         P->sol_cycles = P->sol_mv64 = P->sol_mvmix = 0;
@@ -331,6 +333,40 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
         double rel = 0.0;
         bool last_breakdown = false;
         const double nb = S.norm_b();
+        bool have_v0 = false;                            // V_0 and beta0 already formed
+        double beta0 = 0.0;
+        P->sol_guess_mlp = 0;
+        P->sol_rel_plain = P->sol_rel_mlp = 0.0;
+        if (use_mlp && nb > 0.0) {
+            // r0 = b - A q; learned guess q + A^-1 r0; keep whichever of q and
+            // the learned guess has the lower residual under the plan's operator
+            if (!P->d_smlp) dalloc(P, &P->d_smlp, S.ld);
+            if (!P->d_sres) dalloc(P, &P->d_sres, S.ld);
+            S.apply(P, S.x, P->d_sres, true);
+            S.mdot(1, P->d_sres, P->d_sres, P->d_sh);
+            S.to_host(1);
+            const double r_plain = std::sqrt(S.hs[0]) / nb;
+            mlp_guess_dev(P, S.kappa, P->d_sres, S.x, P->d_smlp);
+            double* xs = S.x;
+            S.x = P->d_smlp;
+            const double r_mlp = S.residual_into_v0(P) / nb;
+            S.x = xs;
+            P->sol_rel_plain = r_plain;
+            P->sol_rel_mlp = r_mlp;
+            // the chosen guess's residual starts GMRES (V_0 = r / beta)
+            if (r_mlp < r_plain) {
+                GG_CUDA(cudaMemcpyAsync(S.x, P->d_smlp, n3 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, P->st));
+                P->sol_guess_mlp = 1;
+                beta0 = r_mlp * nb;                      // V_0 holds it already
+            } else {
+                beta0 = r_plain * nb;
+                GG_CUDA(cudaMemcpyAsync(P->d_V, P->d_sres, n3 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, P->st));
+                S.normalize(P->d_V, P->d_sh);
+            }
+            have_v0 = beta0 > 0.0;
+        }
         if (nb == 0.0) {
             GG_CUDA(cudaMemsetAsync(S.x, 0, n3 * sizeof(double), P->st));
         } else {
@@ -338,7 +374,8 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
             // comes from the mixed operator unless that already looks converged.
             bool first_mixed = !P->fp64;
             for (;;) {
-                double beta = S.residual_into_v0(first_mixed ? P : S.P64);
+                double beta = have_v0 ? beta0 : S.residual_into_v0(first_mixed ? P : S.P64);
+                have_v0 = false;
                 rel = beta / nb;
                 GG_CHECK(std::isfinite(rel), GGEM_ERR_NUMERICAL, "non-finite residual");
                 if (first_mixed) {
@@ -373,6 +410,37 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
         if (true_relres) *true_relres = rel;
     });
     return s != GGEM_OK ? s : result;
+}
+
+ggem_status ggem_bie_operator(ggem_plan_t* P, const double* kappa, const double* q,
+                              double* out) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(P->mesh_ready && P->n_tris > 0, GGEM_ERR_INVALID_ARG,
+                 "the operator needs a mesh with triangles");
+        GG_CHECK(kappa && q && out, GGEM_ERR_INVALID_ARG, "NULL argument");
+        const size_t n3 = (size_t)P->n_nodes * 3;
+        const double* kd = stage_in(P, kappa, P->d_in1, (size_t)P->n_nodes);
+        const double* qd = stage_in(P, q, P->d_in2, n3);
+        OutMap mo = stage_out(out, P->d_out0, n3);
+        double* v = P->d_out1;                       // [6 cap] staging: room for D q
+        double_layer_dev(P, qd, v);
+        k_bie_apply<<<(unsigned)((n3 + KB - 1) / KB), KB, 0, P->st>>>(
+            P->n_nodes, 0.25 / kPi, qd, v, kd, nullptr, mo.dev);
+        GG_CUDA(cudaGetLastError());
+        P->launches += 1;
+        finish_out(P, mo);
+        GG_CUDA(cudaStreamSynchronize(P->st));
+    });
+}
+
+ggem_status ggem_solve_guess(const ggem_plan_t* P, int* used_mlp, double* relres_plain,
+                             double* relres_mlp) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    if (used_mlp) *used_mlp = P->sol_guess_mlp;
+    if (relres_plain) *relres_plain = P->sol_rel_plain;
+    if (relres_mlp) *relres_mlp = P->sol_rel_mlp;
+    return GGEM_OK;
 }
 
 ggem_status ggem_solve_stats(const ggem_plan_t* P, int* cycles, int* matvec_fp64,

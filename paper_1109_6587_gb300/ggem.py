@@ -45,7 +45,11 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_single_layer",
            "ggem_double_layer", "ggem_trace_enable", "ggem_trace_stage_count",
            "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count",
-           "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats"]
+           "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats", "ggem_solve_guess",
+           "ggem_mesh_particles", "ggem_mlp_features", "ggem_mlp_load", "ggem_mlp_save",
+           "ggem_mlp_forward", "ggem_mlp_train", "ggem_mlp_guess", "ggem_bie_operator"]
+
+MLP_MODEL_SIZE = 25 + 35075
 
 
 def lib():
@@ -71,6 +75,17 @@ def lib():
         L.bie_solve.argtypes = [P, P, P, P, D, I, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]
         L.ggem_solve_stats.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I),
                                        ctypes.POINTER(I)]
+        L.ggem_solve_guess.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(D),
+                                       ctypes.POINTER(D)]
+        L.ggem_mesh_particles.argtypes = [P, I, P]
+        L.ggem_mlp_features.argtypes = [P, P, P, P, ctypes.POINTER(D)]
+        L.ggem_mlp_guess.argtypes = [P, P, P, P]
+        L.ggem_bie_operator.argtypes = [P, P, P, P]
+        L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
+        L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
+        L.ggem_mlp_forward.argtypes = [P, I, P, P]
+        L.ggem_mlp_train.argtypes = [P, I, P, P, I, ctypes.c_ulonglong, I, I, D,
+                                     ctypes.POINTER(D), P]
         L.ggem_trace_enable.argtypes = [P, I]
         L.ggem_trace_stage_count.argtypes = []
         L.ggem_trace_stage_name.argtypes = [I]
@@ -229,7 +244,7 @@ class Plan:
     def double_layer(self, q, out=None):
         return self._layer(lib().ggem_double_layer, q, out)
 
-    def bie_solve(self, kappa, b, q=None, tol=1e-6, restart=30, maxit=300, use_mlp=False,
+    def bie_solve(self, kappa, b, q=None, tol=1e-6, restart=30, maxit=300, use_mlp=0,
                   check=True):
         """Solve (I + kappa/(4 pi) D) q = b (Sec. 5).  q (in: initial guess, b when
         None; out: the solution) is updated in place when given.  Returns
@@ -242,13 +257,90 @@ class Plan:
         pq, kq = _ptr(q, np.float64)
         its = ctypes.c_int(0)
         rr = ctypes.c_double(0.0)
-        st = lib().bie_solve(self.h, pk, pb, pq, tol, restart, maxit, int(bool(use_mlp)),
+        st = lib().bie_solve(self.h, pk, pb, pq, tol, restart, maxit, int(use_mlp),
                              ctypes.byref(its), ctypes.byref(rr))
         if check and st not in (0, 5, 6):
             _check(st, self.h)
         if kq is not q and not hasattr(q, "data_ptr"):
             q[...] = kq
         return q, its.value, rr.value, st
+
+    def solve_guess(self):
+        """(started from the learned guess, relative residual of the caller's
+        guess, relative residual of the learned guess) of the last bie_solve."""
+        u, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().ggem_solve_guess(self.h, ctypes.byref(u), ctypes.byref(a),
+                                      ctypes.byref(b)), self.h)
+        return bool(u.value), a.value, b.value
+
+    # ---------------------------------------------------- learned warm start
+    def mesh_particles(self, particle, n_particles=None):
+        part = np.ascontiguousarray(np.asarray(particle.cpu() if hasattr(particle, "cpu")
+                                               else particle), dtype=np.int32)
+        n_p = int(part.max()) + 1 if n_particles is None else int(n_particles)
+        _check(lib().ggem_mesh_particles(self.h, n_p, part.ctypes.data_as(ctypes.c_void_p)),
+               self.h)
+
+    def mlp_features(self, kappa, r):
+        """(features [n, 12] numpy, s = rms(r)) of the right-hand side r."""
+        n = self.n_nodes
+        out = np.zeros((n, 12))
+        pk, kk = _ptr(kappa, np.float64)
+        pr, kr = _ptr(r, np.float64)
+        sc = ctypes.c_double(0.0)
+        _check(lib().ggem_mlp_features(self.h, pk, pr, out.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(sc)), self.h)
+        return out, sc.value
+
+    def mlp_guess(self, kappa, r, out=None):
+        """The learned estimate of A^-1 r."""
+        return self._apply3(lib().ggem_mlp_guess, kappa, r, out)
+
+    def bie_operator(self, kappa, q, out=None):
+        """(I + kappa/(4 pi) D) q."""
+        return self._apply3(lib().ggem_bie_operator, kappa, q, out)
+
+    def _apply3(self, fn, kappa, v, out):
+        if out is None:
+            out = _zeros_like_target(v, (self.n_nodes, 3))
+        pk, kk = _ptr(kappa, np.float64)
+        pv, kv = _ptr(v, np.float64)
+        po, ko = _ptr(out, np.float64)
+        _check(fn(self.h, pk, pv, po), self.h)
+        if ko is not out and not hasattr(out, "data_ptr"):
+            out[...] = ko
+        return out
+
+    def mlp_load(self, model):
+        m = np.ascontiguousarray(np.asarray(model), dtype=np.float64)
+        _check(lib().ggem_mlp_load(self.h, m.ctypes.data_as(ctypes.c_void_p), m.size), self.h)
+
+    def mlp_save(self):
+        m = np.zeros(MLP_MODEL_SIZE)
+        _check(lib().ggem_mlp_save(self.h, m.ctypes.data_as(ctypes.c_void_p), m.size), self.h)
+        return m
+
+    def mlp_forward(self, feat):
+        f = np.ascontiguousarray(np.asarray(feat.cpu() if hasattr(feat, "cpu") else feat),
+                                 dtype=np.float64)
+        out = np.zeros((f.shape[0], 3))
+        _check(lib().ggem_mlp_forward(self.h, f.shape[0], f.ctypes.data_as(ctypes.c_void_p),
+                                      out.ctypes.data_as(ctypes.c_void_p)), self.h)
+        return out
+
+    def mlp_train(self, feat, target, init=True, seed=0, epochs=10, batch=2048, lr=1e-3,
+                  want_grad=False):
+        """Train (or, with epochs=0, evaluate the full-batch loss and gradient).
+        Returns loss, or (loss, gradient) with want_grad."""
+        pf, kf = _ptr(feat, np.float64)
+        pt, kt = _ptr(target, np.float64)
+        n = int(feat.shape[0])
+        loss = ctypes.c_double(0.0)
+        grad = np.zeros(35075) if want_grad else None
+        pg = grad.ctypes.data_as(ctypes.c_void_p) if want_grad else None
+        _check(lib().ggem_mlp_train(self.h, n, pf, pt, int(bool(init)), int(seed), int(epochs),
+                                    int(batch), float(lr), ctypes.byref(loss), pg), self.h)
+        return (loss.value, grad) if want_grad else loss.value
 
     def solve_stats(self):
         """(GMRES cycles, FP64 operator applications, mixed operator applications)

@@ -201,3 +201,45 @@ def box_1000_capsules():
 def capsules_1000(seed=0):
     """1000 capsules x 642 nodes (642,000 points)."""
     return suspension(1000, box_1000_capsules(), level=3, radius=1.0, seed=seed)
+
+
+# ---- Fredholm-solve inputs and emulated time steps ------------------------
+
+def bie_rhs(susp: Suspension, lam=5.0, gamma=1.0, seed=0, step=0, mu=1.0):
+    """Synthetic right-hand side of the Fredholm system, Eq. (qa):
+        b = -(dF / (lam + 1) + kappa f_inf) / (4 pi mu),  kappa = (lam-1)/(lam+1),
+    with f_inf = mu gamma (r_y, r_x, 0) the traction of the shear flow
+    u_inf = (gamma y, 0, 0) on the undeformed spheres (r the unit radial
+    vector from each capsule's centre), and dF a smooth random membrane load
+    per capsule, dF = a_p + B_p r with a_p ~ N(0, 1/4), B_p ~ N(0, 1) per
+    entry; `step` drifts the load by 0.05 * step of a second random field.
+    Returns (kappa [N], b [N, 3])."""
+    rng = np.random.default_rng(seed)
+    n_p = len(susp.centres)
+    a0, B0 = 0.5 * rng.standard_normal((n_p, 3)), rng.standard_normal((n_p, 3, 3))
+    a1, B1 = 0.5 * rng.standard_normal((n_p, 3)), rng.standard_normal((n_p, 3, 3))
+    a = a0 + 0.05 * step * a1
+    B = B0 + 0.05 * step * B1
+    p = susp.particle
+    r = susp.x - susp.centres[p]
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    dF = a[p] + np.einsum("nij,nj->ni", B[p], r)
+    f_inf = mu * gamma * np.stack([r[:, 1], r[:, 0], np.zeros(len(r))], 1)
+    kappa = (lam - 1.0) / (lam + 1.0)
+    b = -(dF / (lam + 1.0) + kappa * f_inf) / (4.0 * math.pi * mu)
+    return np.full(len(r), kappa), b
+
+
+def rigid_step(susp: Suspension, seed=0, step=1, amp=0.01):
+    """The suspension after `step` emulated time steps: every capsule moved
+    rigidly by the sum of `step` random displacements of size amp * radius
+    (standing in for the membrane mechanics and time stepper)."""
+    rng = np.random.default_rng(seed)
+    n_p = len(susp.centres)
+    shift = np.zeros((n_p, 3))
+    for _ in range(step):
+        d = rng.standard_normal((n_p, 3))
+        shift += amp * susp.radius * d / np.linalg.norm(d, axis=1, keepdims=True)
+    c = susp.centres + shift
+    return Suspension(susp.box, np.ascontiguousarray(susp.x + shift[susp.particle]),
+                      susp.tri, susp.particle, c, susp.radius)

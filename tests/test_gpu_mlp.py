@@ -1,0 +1,159 @@
+"""Learned warm start on the GPU against its oracle (oracle/mlp.py), and what
+it gains in the Fredholm solve.
+
+  * features: FP32 copies of the oracle's FP64 values (1e-6 relative), the
+    double-layer columns at the mixed parity (1e-5); the crowding count, an
+    integer decided in FP64 on both sides, exactly;
+  * forward: the bfloat16 network against the oracle with the same rounding
+    points (FP32 vs FP64 accumulation can move a hidden activation by one
+    bfloat16 step: 1e-2 of the output scale);
+  * gradient of one full-batch pass against the oracle's backpropagation
+    (2e-2 relative per parameter tensor), and the loss (1e-3);
+  * one Adam step moves the parameters in the oracle's direction;
+  * the Fredholm operator (I + kappa/4 pi D) against the oracle's;
+  * warm start: trained on emulated time-step series of suspensions, on a
+    held-out series the learned guess has a lower residual than the caller's
+    guess (b at the first step, the previous density after it) by 2x or more,
+    and the solves take fewer GMRES iterations over the series.  (The system
+    is of the second kind: GMRES itself reduces the residual about 3x per
+    iteration, so a guess 3x better saves about one iteration.)
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from oracle import oracle as O
+from paper_1109_6587_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ggem():
+    from paper_1109_6587_gb300 import _build
+    _build.build()
+    from paper_1109_6587_gb300 import ggem as G
+    return G
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _box():
+    return W.Box(Lx=16.0, Lz=16.0, W=6.0, y0=-3.0, Nx=32, Ny=33, Nz=32)
+
+
+def _plan(ggem, s, prec="mixed", quad="nodal"):
+    P = ggem.Plan.for_box(s.box, precision=prec, quadrature=quad, max_points=s.x.shape[0],
+                          max_tris=s.tri.shape[0])
+    P.mesh_set(_dev(s.x), torch.as_tensor(s.tri, device="cuda"))
+    P.mesh_particles(s.particle, len(s.centres))
+    return P
+
+
+@pytest.fixture(scope="module")
+def susp():
+    return W.suspension(8, _box(), level=2, seed=3)
+
+
+def test_features_match_oracle(ggem, susp):
+    s = susp
+    P = _plan(ggem, s)
+    kappa, b = W.bie_rhs(s, seed=4)
+    r = np.random.default_rng(5).standard_normal(s.x.shape)
+    f, sc = P.mlp_features(_dev(kappa), _dev(r))
+    a, rc = P.info()
+    _, _, _, nrm = O.geometry(s.x, s.tri)
+    Dr = O.double_layer(s, r, quadrature="nodal")
+    ref, sref = M.features(s.box, kappa, r, Dr, rc, s.x, s.particle, nrm)
+    assert abs(sc - sref) < 1e-14 * sref
+    cols = [c for c in range(12) if c not in (3, 4, 5, 11)]
+    scale = np.abs(ref[:, cols]).max(0)
+    assert (np.abs(f[:, cols] - ref[:, cols]) / scale).max() < 1e-6
+    # (kappa/4 pi) D r / s: the mixed double layer (1e-5 parity)
+    assert np.abs(f[:, 3:6] - ref[:, 3:6]).max() < 1e-5 * np.abs(ref[:, 3:6]).max()
+    assert np.array_equal(f[:, 11], ref[:, 11].astype(np.float32).astype(np.float64))
+    assert ref[:, 11].max() > 0          # the case has crowded nodes
+
+
+def test_bie_operator_matches_oracle(ggem, susp):
+    s = susp
+    P = _plan(ggem, s, prec="fp64")
+    kappa, _ = W.bie_rhs(s, seed=4)
+    q = np.random.default_rng(6).standard_normal(s.x.shape)
+    out = P.bie_operator(_dev(kappa), _dev(q)).cpu().numpy()
+    ref = O.bie_operator(s, kappa, q, quadrature="nodal")
+    assert np.abs(out - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def _model(seed):
+    rng = np.random.default_rng(seed)
+    params = M.init_params(seed)
+    params = [p + 0.05 * rng.standard_normal(p.shape) if p.ndim == 1 else p for p in params]
+    mu = rng.standard_normal(12) * 0.1
+    sigma = 0.5 + rng.random(12)
+    s_y = 0.7
+    blob = np.concatenate([mu, sigma, [s_y]] + [p.ravel() for p in params])
+    return params, mu, sigma, s_y, blob
+
+
+def test_forward_matches_oracle(ggem, susp):
+    P = _plan(ggem, susp)
+    params, mu, sigma, s_y, blob = _model(11)
+    P.mlp_load(blob)
+    assert np.array_equal(P.mlp_save(), blob.astype(np.float32).astype(np.float64))
+    X = np.random.default_rng(12).standard_normal((1000, 12))
+    out = P.mlp_forward(X)
+    _, ref = M.forward(params, (X - mu) / sigma, bf16_round=True)
+    assert np.abs(out - ref).max() < 1e-2 * np.abs(ref).max()
+
+
+def test_gradient_and_adam_match_oracle(ggem, susp):
+    P = _plan(ggem, susp)
+    params, mu, sigma, s_y, blob = _model(21)
+    P.mlp_load(blob)
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((700, 12))
+    T = rng.standard_normal((700, 3)) * 0.3
+    loss, g = P.mlp_train(X, T, init=False, epochs=0, want_grad=True)
+    pf = [p.astype(np.float32).astype(np.float64) for p in params]
+    ref_loss, ref_g = M.loss_and_grads(pf, (X - mu) / sigma, T / s_y, bf16_round=True)
+    assert abs(loss - ref_loss) < 1e-3 * ref_loss
+    off = 0
+    for rg in ref_g:
+        gg = g[off:off + rg.size].reshape(rg.shape)
+        off += rg.size
+        assert np.linalg.norm(gg - rg) < 2e-2 * np.linalg.norm(rg)
+    # one Adam step on the same full batch
+    P.mlp_load(blob)
+    P.mlp_train(X, T, init=False, epochs=1, batch=700, lr=1e-3)
+    new = P.mlp_save()[25:]
+    state = []
+    M.adam_step(pf, ref_g, state, lr=1e-3, step=1)
+    moved_gpu = new - blob[25:].astype(np.float32).astype(np.float64)
+    moved_ref = np.concatenate([p.ravel() for p in pf]) - blob[25:].astype(np.float32)
+    big = np.abs(np.concatenate([x.ravel() for x in ref_g])) > 1e-6
+    assert (np.sign(moved_gpu[big]) == np.sign(moved_ref[big])).mean() > 0.99
+
+
+def test_learned_warm_start_reduces_iterations(ggem):
+    from paper_1109_6587_gb300 import warmstart as WS
+    box = _box()
+    train_s = [W.suspension(8, box, level=2, seed=100 + i) for i in range(3)]
+    P = _plan(ggem, train_s[0])
+    F, T = WS.training_set(P, train_s, n_steps=5, seed=200)
+    loss = WS.train(P, F, T, seed=1, epochs=150, batch=512, lr=1e-3)
+    assert loss < 0.5                     # in units of rms(target)^2
+    test_s = W.suspension(8, box, level=2, seed=999)
+    plain = WS.solve_series(P, test_s, 4, seed=300, use_mlp=0)
+    learned = WS.solve_series(P, test_s, 4, seed=300, use_mlp=1)
+    # every step: the learned guess has at most half the residual of the
+    # caller's guess (b at step 0, the previous density after it), the solve
+    # never takes more GMRES iterations, and over the series it takes fewer
+    for p, l in zip(plain, learned):
+        assert l["used_mlp"] and l["relres_mlp"] < 0.5 * l["relres_guess"]
+        assert l["iters"] <= p["iters"]
+        assert l["relres"] <= 1e-6
+    assert sum(l["iters"] for l in learned) < sum(p["iters"] for p in plain)

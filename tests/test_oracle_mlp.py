@@ -5,9 +5,9 @@
   * backpropagation: gradients of the loss equal central finite differences
     (exact arithmetic, no rounding) for every parameter tensor;
   * Adam: the first step moves each parameter by lr * g / (|g| + eps);
-  * features: on a sphere of radius a the 1-ring curvature is ~1/a, the wall
-    distances are exact, b, n and kappa are copied, a constant q_prev = v
-    gives v . n_b; crowding is 0 for a particle out of reach and
+  * features: r and its double layer enter divided by rms(r) (so the
+    features of c r equal those of r), n and kappa are copied, the wall
+    distance is exact; crowding is 0 for a particle out of reach and
     n_other / n_own when every node of the other particle is within r_cut;
   * training: Adam on a target the network can represent lowers the loss by
     more than 100x.
@@ -71,8 +71,7 @@ def _sphere(centre, radius, level=2):
 
 def test_features_on_spheres():
     box = W.Box(Lx=16.0, Lz=16.0, W=6.0, y0=-3.0, Nx=32, Ny=33, Nz=32)
-    a = 1.3
-    x1, F1 = _sphere(np.array([4.0, 0.2, 4.0]), a)
+    x1, F1 = _sphere(np.array([4.0, 0.2, 4.0]), 1.3)
     n1 = len(x1)
     rcut = 2.0
     # second particle: far away (no node within r_cut)
@@ -81,27 +80,29 @@ def test_features_on_spheres():
     tri = np.vstack([F1, F2 + n1])
     part = np.r_[np.zeros(n1, int), np.ones(len(x2), int)]
     kappa = np.r_[np.full(n1, 0.6), np.full(len(x2), -0.2)]
-    b = np.random.default_rng(2).standard_normal(x.shape)
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(x.shape)
+    Dr = rng.standard_normal(x.shape)
     _, _, _, nrm = O.geometry(x, tri)
-    v = np.array([0.3, -0.7, 0.2])
-    f = M.features(box, x, tri, part, kappa, b, rcut, nrm, q_prev=np.tile(v, (len(x), 1)))
-    assert np.array_equal(f[:, 0:3], b) and np.array_equal(f[:, 3:6], nrm)
-    assert np.abs(f[:n1, 6] - 1.0 / a).max() < 0.03 / a
-    assert np.allclose(f[:, 7], x[:, 1] - box.y0, rtol=0, atol=1e-14)
-    assert np.allclose(f[:, 8], box.y0 + box.W - x[:, 1], rtol=0, atol=1e-14)
-    assert np.array_equal(f[:, 9], kappa)
-    assert np.allclose(f[:, 11], nrm @ v, rtol=0, atol=1e-14)
-    assert not f[:, 10].any()
+    f, s = M.features(box, kappa, r, Dr, rcut, x, part, nrm)
+    assert s == pytest.approx(np.sqrt((r * r).mean()), rel=1e-15)
+    assert np.allclose(f[:, 0:3] * s, r, rtol=1e-15, atol=0)
+    assert np.allclose(f[:, 3:6] * s, kappa[:, None] / (4 * math.pi) * Dr, rtol=1e-15, atol=0)
+    f2, s2 = M.features(box, kappa, 7.0 * r, 7.0 * Dr, rcut, x, part, nrm)
+    assert s2 == pytest.approx(7.0 * s) and np.allclose(f2, f, rtol=1e-14, atol=1e-14)
+    assert np.array_equal(f[:, 6:9], nrm) and np.array_equal(f[:, 9], kappa)
+    assert np.allclose(f[:, 10], np.minimum(x[:, 1] + 3.0, 3.0 - x[:, 1]), rtol=0, atol=1e-14)
+    assert not f[:, 11].any()
     # a small particle next to the first: all its nodes within r_cut of the
     # nearest node of the first one
-    x3, F3 = _sphere(x1[0] + 0.8 * (x1[0] - np.array([4.0, 0.2, 4.0])) / a, 0.2, level=1)
+    x3, F3 = _sphere(x1[0] + 0.8 * (x1[0] - np.array([4.0, 0.2, 4.0])) / 1.3, 0.2, level=1)
     x = np.vstack([x1, x3])
     tri = np.vstack([F1, F3 + n1])
     part = np.r_[np.zeros(n1, int), np.ones(len(x3), int)]
     _, _, _, nrm = O.geometry(x, tri)
-    f = M.features(box, x, tri, part, np.zeros(len(x)), np.zeros(x.shape), rcut, nrm)
-    assert f[0, 10] == len(x3) / n1
-    assert not f[:, 11].any()
+    f, _ = M.features(box, np.zeros(len(x)), np.ones(x.shape), np.zeros(x.shape), rcut, x,
+                      part, nrm)
+    assert f[0, 11] == len(x3) / n1
 
 
 def test_training_reduces_loss():
