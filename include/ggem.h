@@ -299,6 +299,12 @@ ggem_status ggem_mlp_train(ggem_plan_t *plan, int n, const double *feat, const d
                            int init, unsigned long long seed, int epochs, int batch, double lr,
                            double *loss, double *grad_out);
 
+/* Device-side status of the plan's kernels: waits with an iteration limit
+ * (the tensor-core transforms' mbarrier waits) record a failure instead of
+ * hanging; GGEM_ERR_CUDA here means results since the plan was created are
+ * invalid.  Synchronises the plan's stream. */
+ggem_status ggem_check(ggem_plan_t *plan);
+
 /*
  * Tracing (no counterpart in the paper).  With tracing enabled, each stage
  * of an evaluation is bracketed by CUDA events on the plan's stream and the

@@ -228,8 +228,18 @@ __global__ void __launch_bounds__(256) k_cheb(int Ny, const T* __restrict__ M,
     }
 }
 
+cudaError_t cheb_apply_tc(int Ny, const float* M, const float* in, float* out, long cols,
+                          int* err, int nsm, cudaStream_t st);
+
 template <typename T>
-cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st) {
+cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st,
+                       int* tc_err, int nsm) {
+    if (sizeof(T) == 4 && tc_err) {
+        // FP32 data: split-BF16 contraction on the tensor cores when it fits
+        cudaError_t e = cheb_apply_tc(Ny, (const float*)M, (const float*)in, (float*)out, cols,
+                                      tc_err, nsm, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     size_t smem = (size_t)Ny * Ny * sizeof(T);
     cudaFuncSetAttribute(k_cheb<T, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_cheb<T, 24><<<(unsigned)((cols + 255) / 256), 256, smem, st>>>(Ny, M, in, out, cols);
@@ -368,7 +378,8 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
                                         cudaStream_t);                                         \
     template cudaError_t fft_inverse<T>(const GridGeom&, T*, int, const void*, const void*,    \
                                         cudaStream_t);                                         \
-    template cudaError_t cheb_apply<T>(int, const T*, const T*, T*, long, cudaStream_t);       \
+    template cudaError_t cheb_apply<T>(int, const T*, const T*, T*, long, cudaStream_t, int*,  \
+                                       int);                                                   \
     template cudaError_t interp_combine<T>(const GridGeom&, const double*, const T*, int, int, \
                                            int, const double*, const T*, int, const double*,   \
                                            const double*, const double*, double, int, double*, \

@@ -185,6 +185,8 @@ struct ggem_plan {
     long mlp_step = 0;
     int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
+    int* d_tc_err = nullptr;           // tensor-core kernels: expired waits
+    int nsm = 0;                       // multiprocessors of the plan's device
     double prof_ms[16] = {0};
     long prof_calls[16] = {0};
     long launches = 0;                 // kernels launched by this plan
@@ -272,7 +274,8 @@ cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* t
                         const void* tw_z, cudaStream_t st);
 
 template <typename T>
-cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st);
+cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st,
+                       int* tc_err = nullptr, int nsm = 0);
 
 // per-mode tau solves; coef = mode-independent recurrence table [3][Ny];
 // thom = per-mode Thomas factors [4][Ny][nmodes], isq = [2][nmodes];

@@ -125,7 +125,7 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
     });
     stage(P, ST_CHEB_FWD, 1, [&] {
         GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_fwd, A, B, (long)3 * P->nmodes * 2,
-                              st));
+                              st, P->d_tc_err, P->nsm));
     });
     stage(P, ST_KS, 1, [&] {
         GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom, P->d_isq,
@@ -134,7 +134,7 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
     int nout = nout_of(out_sel);
     stage(P, ST_CHEB_INV, 1, [&] {
         GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
-                              (long)nout * P->nmodes * 2, st));
+                              (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm));
     });
     stage(P, ST_FFT_INV, 2, [&] {
         GG_CUDA(fft_inverse<T>(geo, B, geo.Ny * nout, P->d_tw_x, P->d_tw_z, st));
@@ -464,6 +464,13 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     P->cap = cap;
     dalloc(P, &P->d_cell_count, P->ncell);
     dalloc(P, &P->d_cell_start, P->ncell + 1);
+    dalloc(P, &P->d_tc_err, 1);
+    GG_CUDA(cudaMemset(P->d_tc_err, 0, sizeof(int)));
+    {
+        int dev = 0;
+        GG_CUDA(cudaGetDevice(&dev));
+        GG_CUDA(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     dalloc(P, &P->d_cursor, (size_t)P->ncell + std::max<size_t>(cap, (size_t)16 * prm.max_tris));
     dalloc(P, &P->d_src_cell, cap);
     dalloc(P, &P->d_perm, cap);
@@ -551,7 +558,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_spart, P->d_sh, P->d_particle, P->d_pcount, P->d_feat,
                     P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
                     P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
-                    P->d_sres, P->d_mlp_dr, P->d_mlp_ssq};
+                    P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -795,6 +802,17 @@ ggem_status ggem_single_layer(ggem_plan_t* P, const double* q, double* w) {
 
 ggem_status ggem_double_layer(ggem_plan_t* P, const double* q, double* v) {
     return layer_entry(P, 1, q, v);
+}
+
+ggem_status ggem_check(ggem_plan_t* P) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        int h = 0;
+        GG_CUDA(cudaMemcpyAsync(&h, P->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+        GG_CUDA(cudaStreamSynchronize(P->st));
+        GG_CHECK(h == 0, GGEM_ERR_CUDA,
+                 "a tensor-core kernel gave up waiting for its MMAs (results invalid)");
+    });
 }
 
 ggem_status ggem_trace_enable(ggem_plan_t* P, int on) {

@@ -47,7 +47,8 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_trace_stage_name", "ggem_trace_read", "ggem_launch_count",
            "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats", "ggem_solve_guess",
            "ggem_mesh_particles", "ggem_mlp_features", "ggem_mlp_load", "ggem_mlp_save",
-           "ggem_mlp_forward", "ggem_mlp_train", "ggem_mlp_guess", "ggem_bie_operator"]
+           "ggem_mlp_forward", "ggem_mlp_train", "ggem_mlp_guess", "ggem_bie_operator",
+           "ggem_check"]
 
 MLP_MODEL_SIZE = 25 + 35075
 
@@ -81,6 +82,7 @@ def lib():
         L.ggem_mlp_features.argtypes = [P, P, P, P, ctypes.POINTER(D)]
         L.ggem_mlp_guess.argtypes = [P, P, P, P]
         L.ggem_bie_operator.argtypes = [P, P, P, P]
+        L.ggem_check.argtypes = [P]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -264,6 +266,10 @@ class Plan:
         if kq is not q and not hasattr(q, "data_ptr"):
             q[...] = kq
         return q, its.value, rr.value, st
+
+    def check(self):
+        """Raise if a device-side wait of the plan's kernels expired."""
+        _check(lib().ggem_check(self.h), self.h)
 
     def solve_guess(self):
         """(started from the learned guess, relative residual of the caller's
