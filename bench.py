@@ -9,8 +9,9 @@ Workload (default): 100 spherical capsules x 642 nodes = 64,200 points in a
 quadrature (the paper's layer rule; --quadrature nodal for point forces).
 Metric: Mpts/s = nodes / (time of one single + one double layer evaluation).
 The second half of the metric -- GMRES iterations and seconds per Fredholm
-solve at true relative residual 1e-6, FP64 against mixed -- is measured on
-the same workload and reported under "solve".
+solve at true relative residual 1e-6, per emulated time step, for the plain
+FP64 solve, the mixed solve and the mixed solve with the learned warm start
+-- is measured on the same workload and reported under "solve".
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
@@ -318,38 +319,90 @@ def cpu_baseline(susp, args, stride=64):
                       f"({len(idx)} of {n}) scaled to all nodes; OpenMP over targets"}
 
 
-def solve_metrics(args, susp, dev):
+def solve_metrics(args, susp, dev, train_steps=3, timed_steps=2):
     """GMRES iterations and seconds per Fredholm solve (Sec. 5) at true relative
-    residual 1e-6 for an FP64 plan and a mixed plan on the workload:
-    kappa = 2/3 (viscosity ratio 5) on every node, b ~ N(0,1), guess q0 = b."""
+    residual 1e-6, per emulated time step of the workload (capsules moved
+    rigidly by 0.01 radius per step, membrane load drifting; kappa = 2/3,
+    viscosity ratio 5; b from Eq. (qa)), each step solved from the previous
+    step's density:
+      fp64   plain GMRES with the FP64 operator;
+      mixed  mixed operator with FP64 refinement;
+      mixed_learned  mixed, starting from the learned guess when its residual
+             is lower (the network trained on steps 0..train_steps-1 of the
+             same run, as a running simulation would).
+    Steps train_steps .. train_steps + timed_steps - 1 are timed."""
     import torch
     from paper_1109_6587_gb300 import ggem
+    from paper_1109_6587_gb300 import warmstart as WS
+
     n = susp.x.shape[0]
-    rng = np.random.default_rng(77)
-    kappa = torch.full((n,), 2.0 / 3.0, dtype=torch.float64, device=dev)
-    b = torch.as_tensor(rng.standard_normal((n, 3)), device=dev)
-    x = torch.as_tensor(susp.x, device=dev)
-    tri = torch.as_tensor(susp.tri, device=dev)
-    out = {"tol": 1e-6, "kappa": 2.0 / 3.0, "rhs": "N(0,1)", "guess": "b", "restart": 30,
-           "quadrature": args.quadrature}
-    for prec in ("fp64", "mixed"):
-        P = ggem.Plan.for_box(susp.box, precision=prec, quadrature=args.quadrature,
-                              max_points=n, max_tris=susp.tri.shape[0])
-        P.mesh_set(x, tri)
-        P.bie_solve(kappa, b, q=b.clone(), tol=1e-6, maxit=1)      # workspace (+ FP64 twin)
-        torch.cuda.synchronize()
-        l0 = P.launch_count()
-        t0 = time.perf_counter()
-        q, its, rr, st = P.bie_solve(kappa, b, q=b.clone(), tol=1e-6)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+    mk = lambda prec: ggem.Plan.for_box(susp.box, precision=prec, quadrature=args.quadrature,
+                                        max_points=n, max_tris=susp.tri.shape[0])
+    Pm = mk("mixed")
+    t0 = time.perf_counter()
+    recs = WS.solve_series(Pm, susp, train_steps, seed=500, collect=True)
+    F = np.concatenate([f for r in recs for f, _ in r["samples"]])
+    T = np.concatenate([t for r in recs for _, t in r["samples"]])
+    t1 = time.perf_counter()
+    loss = WS.train(Pm, F, T, seed=1, epochs=20, batch=2048, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"tol": 1e-6, "kappa": 2.0 / 3.0, "rhs": "Eq. (qa), synthetic membrane load + shear",
+           "guess": "previous step's density", "restart": 30, "quadrature": args.quadrature,
+           "steps_timed": timed_steps,
+           "training": {"samples": int(F.shape[0]), "data_s": t1 - t0, "train_s": t2 - t1,
+                        "loss": loss, "epochs": 20}}
+    P64 = mk("fp64")
+    variants = (("fp64", P64, 0), ("mixed", Pm, 0), ("mixed_learned", Pm, 1))
+    for name, P, use in variants:
+        total = train_steps + timed_steps
+        # the series up to the last training step, untimed (warm state), then timed steps
+        q_prev = None
+        tri = torch.as_tensor(susp.tri, device=dev)
+        times, its, rrs, used = [], [], [], []
+        for t in range(total):
+            s = W_rigid(susp, t)
+            kappa, b = W_rhs(s, t)
+            P.mesh_set(torch.as_tensor(s.x, device=dev), tri)
+            P.mesh_particles(s.particle, len(s.centres))
+            kd = torch.as_tensor(kappa, device=dev)
+            bd = torch.as_tensor(b, device=dev)
+            q0 = bd.clone() if q_prev is None else q_prev.clone()
+            timed = t >= train_steps
+            if name == "fp64" and not timed and t < train_steps - 1:
+                q_prev = None          # FP64 plain: only the last untimed step is needed
+                continue
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            q, it, rr, st = P.bie_solve(kd, bd, q=q0, tol=1e-6, use_mlp=use if timed else 0)
+            torch.cuda.synchronize()
+            if timed:
+                times.append(time.perf_counter() - a)
+                its.append(it)
+                rrs.append(rr)
+                used.append(P.solve_guess()[0])
+            q_prev = q
         cyc, m64, mmix = P.solve_stats()
-        out[prec] = {"iters": its, "s_per_solve": dt, "true_relres": rr, "status": st,
-                     "cycles": cyc, "matvec_fp64": m64, "matvec_mixed": mmix,
-                     "gpu_launches": P.launch_count() - l0}
-        P.close()
+        out[name] = {"iters": float(np.mean(its)), "s_per_solve": float(np.mean(times)),
+                     "true_relres_max": float(np.max(rrs)), "learned_guess_used": used,
+                     "last_solve_matvec_fp64": m64, "last_solve_matvec_mixed": mmix}
+        P.check()
+    Pm.close()
+    P64.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_solve"] / out["mixed"]["s_per_solve"]
+    out["speedup_learned_vs_fp64"] = (out["fp64"]["s_per_solve"] /
+                                      out["mixed_learned"]["s_per_solve"])
     return out
+
+
+def W_rigid(susp, t):
+    from paper_1109_6587_gb300 import workloads as W
+    return W.rigid_step(susp, seed=500, step=t) if t else susp
+
+
+def W_rhs(s, t):
+    from paper_1109_6587_gb300 import workloads as W
+    return W.bie_rhs(s, seed=500, step=t)
 
 
 def main():

@@ -213,9 +213,9 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
 }
 
 // Pair arithmetic of Eq. (local), shared by the local-sum kernels.
-// exp(-alpha^2 r^2) and erfc(alpha r): in FP32 the exponential is 2^(ke r^2)
-// and erfc = exp(-x^2) erfcx(x) with the polynomial of ggem_erfcx.cuh, so the
-// pair needs one exponential and no erfc call; in FP64 CUDA's exp and erfc.
+// exp(-alpha^2 r^2) and erfc(alpha r) = exp(-x^2) erfcx(x) with the
+// polynomials of ggem_erfcx.cuh (degree 16 in FP32, 26 in FP64), so the pair
+// needs one exponential and no erfc call; the FP32 exponential is 2^(ke r^2).
 template <typename T> struct PairAcc {
     T ux = 0, uy = 0, uz = 0;
     T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
@@ -229,7 +229,7 @@ __device__ __forceinline__ void exp_erfc(const LocalConst<float>& k, float r2, f
 __device__ __forceinline__ void exp_erfc(const LocalConst<double>& k, double r2, double x,
                                          double& ex, double& ec) {
     ex = exp(-k.al2 * r2);
-    ec = erfc(x);
+    ec = ex * erfcx_poly(x);
 }
 
 // adds G^l g (OUT_U), T^l g (OUT_S) or n . T^l g (OUT_DBL) for displacement

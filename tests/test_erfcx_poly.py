@@ -1,5 +1,6 @@
-"""The FP32 pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the degree-16
-polynomial of ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff).
+"""The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the polynomials of
+ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff): degree 16 (FP32),
+degree 26 (FP64).  FP32:
 Its coefficients, read from the generated header, must approximate scipy's
 erfcx to 1e-8 relative in FP64 and to 4e-7 (a few FP32 ulps, like CUDA's
 erfcf) when evaluated in FP32 by the same Horner scheme."""
@@ -21,6 +22,13 @@ def _coefficients():
     return [float(first)] + [float(v) for v in rest]    # highest degree first
 
 
+def _coefficients64():
+    txt = HDR.read_text()
+    first = re.search(r"double p = ([-+0-9.eE]+);", txt).group(1)
+    rest = re.findall(r"p = fma\(p, u, ([-+0-9.eE]+)\);", txt)
+    return [float(first)] + [float(v) for v in rest]
+
+
 def test_polynomial_error():
     c = _coefficients()
     assert len(c) == 17
@@ -37,3 +45,19 @@ def test_polynomial_error():
     for a in c[1:]:
         p32 = (p32 * u32 + np.float32(a)).astype(np.float32)
     assert np.abs(p32.astype(np.float64) / ref - 1).max() < 4e-7
+
+
+def test_polynomial_error_fp64():
+    """The FP64 kernels' degree-26 polynomial against mpmath at 40 digits:
+    1e-14 relative (FP64 parity of the pair sums is 1e-10)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    c = _coefficients64()
+    assert len(c) == 27
+    x = np.linspace(0.0, 4.0, 801)
+    ref = np.array([float(mp.exp(mp.mpf(v) ** 2) * mp.erfc(mp.mpf(v))) for v in x])
+    u = x / 2 - 1
+    p = np.full_like(u, c[0])
+    for a in c[1:]:
+        p = p * u + a
+    assert np.abs(p / ref - 1).max() < 1e-14
