@@ -257,15 +257,21 @@ def roofline(res, args):
     plane = b.Nz * b.Nx
     if name == "local_sum":
         pairs = _elem_pair_count(susp, rc) if args.quadrature == "element" else _pair_count(susp, rc)
-        # FLOPs per pair: single layer 52, double layer 70, averaged
-        flops = pairs * 61.0
+        # FP32 operations per pair of the kernel's formula (distance, rsqrt and
+        # exp2 as one each, the 17-FMA erfcx polynomial, the G^l or n.T^l
+        # contraction): single layer 74, double layer 99; the stage averages
+        # one launch of each
+        flops = pairs * (74.0 + 99.0) / 2.0
         sm_mhz = res["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = flops / avg_s / 1e12
         if args.precision == "fp64":
             peak = 1.25
+        # dram read + write bytes of one double-layer launch, ncu capture of this
+        # kernel on this workload (profiles/k_local_elem_dbl_capsules100_mixed.md)
+        traffic = 119.2e6 if (args.quadrature, args.precision) == ("element", "mixed") else None
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
                 if args.precision == "mixed" else "nominal FP64"}
     # memory-bound stages: algorithmic bytes per launch
