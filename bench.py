@@ -169,6 +169,21 @@ def _elem_pair_count(susp, rcut):
     return total - 16 * 3 * len(susp.tri)
 
 
+def aggregate(t_ms, steps, n_points, world, device):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (max over ranks) and the points of all ranks.  Returns (ms per step,
+    Mpts/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+    ms_step = t_ms / steps
+    return ms_step, world * n_points / (ms_step * 1e-3) / 1e6
+
+
 def run_mine(args, rank, world):
     import torch
     from paper_1109_6587_gb300 import ggem
@@ -210,14 +225,7 @@ def run_mine(args, rank, world):
         torch.cuda.synchronize()
     launches = P.launch_count() - l0
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        dist.barrier()
-    ms_step = t_ms / args.steps
-    value = world * n / (ms_step * 1e-3) / 1e6
+    ms_step, value = aggregate(t_ms, args.steps, n, world, dev)
 
     # per-stage device times (traced pass, same stream)
     P.trace(True)
