@@ -187,6 +187,8 @@ struct ggem_plan {
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
     int* d_tc_err = nullptr;           // tensor-core kernels: expired waits
     int nsm = 0;                       // multiprocessors of the plan's device
+    cudaStream_t st2 = nullptr;        // second stream: local part beside the global part
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double prof_ms[16] = {0};
     long prof_calls[16] = {0};
     long launches = 0;                 // kernels launched by this plan

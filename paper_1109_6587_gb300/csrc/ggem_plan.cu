@@ -251,14 +251,24 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
     T* loc = (T*)P->d_local;
+    // The local part and the global part are independent until the combine:
+    // the local kernels run on the plan's second stream, forked after the
+    // strengths are gathered and joined before the interpolation (both on one
+    // stream when tracing, so that stage times stay separable).
+    const bool overlap = !P->prof && P->st2;
+    cudaStream_t ls = overlap ? P->st2 : st;
+    if (overlap) {
+        GG_CUDA(cudaEventRecord(P->ev_fork, st));
+        GG_CUDA(cudaStreamWaitEvent(ls, P->ev_fork, 0));
+    }
     if (!elem) {
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum<T>(geo, P->cg, src, TK_SORTED, n, nullptr, nullptr, P->d_nrm,
-                                 layer == 0 ? OUT_U : OUT_DBL, loc, 3, st));
+                                 layer == 0 ? OUT_U : OUT_DBL, loc, 3, ls));
         });
     } else if (P->n_qp == 0) {
         // no triangles: every element integral is empty
-        GG_CUDA(cudaMemsetAsync(loc, 0, (size_t)n * 3 * sizeof(T), st));
+        GG_CUDA(cudaMemsetAsync(loc, 0, (size_t)n * 3 * sizeof(T), ls));
     } else {
         // local part by the element rule: all quadrature points, then the polar
         // rule on the triangles that touch each node (Sec. 3.4.1, 3.5.2)
@@ -271,14 +281,16 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         qs.n = P->n_qp;
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
-                                      P->d_nrm, layer, loc, 3, st));
+                                      P->d_nrm, layer, loc, 3, ls));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
-                                    P->d_adj_start, P->d_adj, q, P->rule, loc, 3, st));
+                                    P->d_adj_start, P->d_adj, q, P->rule, loc, 3, ls));
         });
     }
+    if (overlap) GG_CUDA(cudaEventRecord(P->ev_join, ls));
     run_global<T>(P, src, true, layer == 0 ? 1 : 2);
+    if (overlap) GG_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
             // nodal form: remove the free-space global self term (4 alpha/sqrt(pi)) A_b q_b;
@@ -537,12 +549,21 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
     GG_CUDA(cudaEventCreate(&P->ev1));
+    GG_CUDA(cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking));
+    GG_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    GG_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     GG_CUDA(cudaDeviceSynchronize());
 }
 
 void plan_free(ggem_plan_t* P) {
     if (P->ev0) cudaEventDestroy(P->ev0);
     if (P->ev1) cudaEventDestroy(P->ev1);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->st2) {
+        cudaStreamSynchronize(P->st2);
+        cudaStreamDestroy(P->st2);
+    }
     void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
                     P->d_minv, P->d_ydiff, P->d_sdi, P->d_sdf, P->d_mesh_sdi, P->d_mesh_sdf,
                     P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall,
