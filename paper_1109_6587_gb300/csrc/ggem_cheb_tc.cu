@@ -11,8 +11,10 @@
 // accumulated in FP32 in tensor memory (the dropped M_lo in_lo and the split
 // remainders are ~2^-16 of each product).
 //
-// One CTA per SM (persistent over 128-column tiles).  M's split is staged in
-// shared memory once; each tile of `in` is split while it is staged.  Both
+// Persistent CTAs over 128-column tiles, two per SM when their shared memory
+// fits.  M's split is prepared once per plan (k_cheb_tc_prep) and copied into
+// shared memory with 16-byte loads; each tile of `in` is split while it is
+// staged, one 16-byte core-matrix row per thread and item.  Both
 // operands use the K-major no-swizzle canonical layout: core matrices of 8
 // rows x 16 bytes (8 bf16 along K), the next core matrix along K 128 bytes
 // away, the next 8-row group along M/N (Kp/8) * 128 bytes away.  One thread
@@ -87,8 +89,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(TCT, 1)
-    k_cheb_tc(int Ny, int Kp, int MB, int NT, uint32_t tcols, const float* __restrict__ Mx,
+__global__ void __launch_bounds__(TCT)
+    k_cheb_tc(int Ny, int Kp, int MB, int NT, uint32_t tcols, const uint4* __restrict__ Mprep,
               const float* __restrict__ in, float* __restrict__ out, long cols, long ntiles,
               int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -101,21 +103,11 @@ __global__ void __launch_bounds__(TCT, 1)
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // M split, zero padded to MB*128 rows and Kp columns
-    for (int e = tid; e < MB * 128 * Kp; e += TCT) {
-        const int r = e / Kp, k = e - r * Kp;
-        const float v = (r < Ny && k < Ny) ? Mx[r * Ny + k] : 0.f;
-        __nv_bfloat16 h, l;
-        split(v, h, l);
-        const int o = (r >> 7) * 128 * Kp + canon(r & 127, k, Kp);
-        Ah[o] = h;
-        Al[o] = l;
-    }
-    // B rows k in [Ny, Kp) stay zero for every tile
-    for (int e = tid; e < NT * (Kp - Ny); e += TCT) {
-        const int n = e / (Kp - Ny), k = Ny + (e - n * (Kp - Ny));
-        Bh[canon(n, k, Kp)] = __float2bfloat16_rn(0.f);
-        Bl[canon(n, k, Kp)] = __float2bfloat16_rn(0.f);
+    // M split (hi then lo, canonical layout), prepared once per plan
+    {
+        uint4* dst = reinterpret_cast<uint4*>(Ah);
+        const int n16 = 2 * MB * 128 * Kp / 8;
+        for (int e = tid; e < n16; e += TCT) dst[e] = Mprep[e];
     }
     if (tid == 0) {
         s_fail = 0;
@@ -140,15 +132,29 @@ __global__ void __launch_bounds__(TCT, 1)
     uint32_t parity = 0;
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long c0 = tile * NT;
-        for (int e = tid; e < Ny * NT; e += TCT) {
-            const int k = e / NT, n = e - k * NT;
+        // one core-matrix row per item: column n, rows 8 kg .. 8 kg + 7 (zero past Ny),
+        // consecutive threads on consecutive columns (coalesced loads), one
+        // 16-byte store each for hi and lo
+        for (int e = tid; e < NT * (Kp / 8); e += TCT) {
+            const int kg = e / NT, n = e - kg * NT;
             const long c = c0 + n;
-            const float v = c < cols ? in[(long)k * cols + c] : 0.f;
-            __nv_bfloat16 h, l;
-            split(v, h, l);
-            const int o = canon(n, k, Kp);
-            Bh[o] = h;
-            Bl[o] = l;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                const int k = kg * 8 + j;
+                const float v0 = (k < Ny && c < cols) ? in[(long)k * cols + c] : 0.f;
+                const float v1 = (k + 1 < Ny && c < cols) ? in[(long)(k + 1) * cols + c] : 0.f;
+                __nv_bfloat16 h0, l0, h1, l1;
+                split(v0, h0, l0);
+                split(v1, h1, l1);
+                hw[j / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
+                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                lw[j / 2] = (uint32_t)__bfloat16_as_ushort(l0) |
+                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const int o = canon(n, kg * 8, Kp);
+            *reinterpret_cast<uint4*>(Bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(Bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -216,7 +222,35 @@ __global__ void __launch_bounds__(TCT, 1)
                      "r"(tcols));
 }
 
+// M split into hi and lo, zero padded to MB*128 rows and Kp columns, in the
+// canonical layout (hi block then lo block)
+__global__ void k_cheb_tc_prep(int Ny, int Kp, int MB, const float* __restrict__ Mx,
+                               __nv_bfloat16* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= MB * 128 * Kp) return;
+    const int r = e / Kp, k = e - r * Kp;
+    const float v = (r < Ny && k < Ny) ? Mx[r * Ny + k] : 0.f;
+    __nv_bfloat16 h, l;
+    split(v, h, l);
+    const int o = (r >> 7) * 128 * Kp + canon(r & 127, k, Kp);
+    out[o] = h;
+    out[(size_t)MB * 128 * Kp + o] = l;
+}
+
 }  // namespace
+
+size_t cheb_tc_prep_bytes(int Ny) {
+    const int Kp = (Ny + 15) / 16 * 16, MB = (Ny + 127) / 128;
+    return (size_t)2 * MB * 128 * Kp * 2;
+}
+
+cudaError_t cheb_tc_prepare(int Ny, const float* M, void* prep, cudaStream_t st) {
+    const int Kp = (Ny + 15) / 16 * 16, MB = (Ny + 127) / 128;
+    const int n = MB * 128 * Kp;
+    k_cheb_tc_prep<<<(n + 255) / 256, 256, 0, st>>>(Ny, Kp, MB, M,
+                                                    static_cast<__nv_bfloat16*>(prep));
+    return cudaGetLastError();
+}
 
 // Shared memory of the tensor-core transform for Ny rows and tile width NT.
 static size_t cheb_tc_smem(int Ny, int NT) {
@@ -227,10 +261,11 @@ static size_t cheb_tc_smem(int Ny, int NT) {
 // out = M in on the tensor cores when the operands fit in shared memory;
 // returns cudaErrorNotSupported otherwise (the caller uses the FP32 kernel).
 // Requires cols % 4 == 0 and 16-byte aligned rows for the vector stores.
-cudaError_t cheb_apply_tc(int Ny, const float* M, const float* in, float* out, long cols,
+cudaError_t cheb_apply_tc(int Ny, const void* prep, const float* in, float* out, long cols,
                           int* err, int nsm, cudaStream_t st) {
     if (Ny < 1 || cols <= 0) return cudaSuccess;
-    if (cols % 4 != 0 || ((uintptr_t)out & 15) != 0) return cudaErrorNotSupported;
+    if (!prep || cols % 4 != 0 || ((uintptr_t)out & 15) != 0 || ((uintptr_t)prep & 15) != 0)
+        return cudaErrorNotSupported;
     const int Kp = (Ny + 15) / 16 * 16, MB = (Ny + 127) / 128;
     int NT = 128;
     size_t smem = cheb_tc_smem(Ny, NT);
@@ -245,9 +280,13 @@ cudaError_t cheb_apply_tc(int Ny, const float* M, const float* in, float* out, l
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const long ntiles = (cols + NT - 1) / NT;
-    const long grid = ntiles < nsm ? ntiles : nsm;
-    k_cheb_tc<<<(unsigned)grid, TCT, smem, st>>>(Ny, Kp, MB, NT, tcols, M, in, out, cols, ntiles,
-                                                 err);
+    // two CTAs per SM when their shared memory fits (one stages while the other
+    // computes); each holds at most 256 of the SM's 512 tensor-memory columns
+    const long per_sm = (2 * smem <= 227 * 1024) ? 2 : 1;
+    const long grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
+    k_cheb_tc<<<(unsigned)grid, TCT, smem, st>>>(Ny, Kp, MB, NT, tcols,
+                                                 static_cast<const uint4*>(prep), in, out, cols,
+                                                 ntiles, err);
     return cudaGetLastError();
 }
 

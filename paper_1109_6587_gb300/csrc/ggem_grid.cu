@@ -228,16 +228,16 @@ __global__ void __launch_bounds__(256) k_cheb(int Ny, const T* __restrict__ M,
     }
 }
 
-cudaError_t cheb_apply_tc(int Ny, const float* M, const float* in, float* out, long cols,
+cudaError_t cheb_apply_tc(int Ny, const void* prep, const float* in, float* out, long cols,
                           int* err, int nsm, cudaStream_t st);
 
 template <typename T>
 cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st,
-                       int* tc_err, int nsm) {
-    if (sizeof(T) == 4 && tc_err) {
+                       int* tc_err, int nsm, const void* tc_prep) {
+    if (sizeof(T) == 4 && tc_err && tc_prep) {
         // FP32 data: split-BF16 contraction on the tensor cores when it fits
-        cudaError_t e = cheb_apply_tc(Ny, (const float*)M, (const float*)in, (float*)out, cols,
-                                      tc_err, nsm, st);
+        cudaError_t e = cheb_apply_tc(Ny, tc_prep, (const float*)in, (float*)out, cols, tc_err,
+                                      nsm, st);
         if (e != cudaErrorNotSupported) return e;
     }
     size_t smem = (size_t)Ny * Ny * sizeof(T);
@@ -379,7 +379,7 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
     template cudaError_t fft_inverse<T>(const GridGeom&, T*, int, const void*, const void*,    \
                                         cudaStream_t);                                         \
     template cudaError_t cheb_apply<T>(int, const T*, const T*, T*, long, cudaStream_t, int*,  \
-                                       int);                                                   \
+                                       int, const void*);                                      \
     template cudaError_t interp_combine<T>(const GridGeom&, const double*, const T*, int, int, \
                                            int, const double*, const T*, int, const double*,   \
                                            const double*, const double*, double, int, double*, \

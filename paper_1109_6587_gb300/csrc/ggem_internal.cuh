@@ -186,6 +186,8 @@ struct ggem_plan {
     int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
     int* d_tc_err = nullptr;           // tensor-core kernels: expired waits
+    void* d_tc_fwd = nullptr;          // split-bf16 Chebyshev matrices (mixed plans)
+    void* d_tc_inv = nullptr;
     int nsm = 0;                       // multiprocessors of the plan's device
     cudaStream_t st2 = nullptr;        // second stream: local part beside the global part
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -277,7 +279,10 @@ cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* t
 
 template <typename T>
 cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st,
-                       int* tc_err = nullptr, int nsm = 0);
+                       int* tc_err = nullptr, int nsm = 0, const void* tc_prep = nullptr);
+// split-bf16 copy of an Ny x Ny FP32 matrix for the tensor-core transform
+size_t cheb_tc_prep_bytes(int Ny);
+cudaError_t cheb_tc_prepare(int Ny, const float* M, void* prep, cudaStream_t st);
 
 // per-mode tau solves; coef = mode-independent recurrence table [3][Ny];
 // thom = per-mode Thomas factors [4][Ny][nmodes], isq = [2][nmodes];

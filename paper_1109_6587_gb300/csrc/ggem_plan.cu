@@ -125,7 +125,7 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
     });
     stage(P, ST_CHEB_FWD, 1, [&] {
         GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_fwd, A, B, (long)3 * P->nmodes * 2,
-                              st, P->d_tc_err, P->nsm));
+                              st, P->d_tc_err, P->nsm, P->d_tc_fwd));
     });
     stage(P, ST_KS, 1, [&] {
         GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom, P->d_isq,
@@ -134,7 +134,7 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
     int nout = nout_of(out_sel);
     stage(P, ST_CHEB_INV, 1, [&] {
         GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
-                              (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm));
+                              (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm, P->d_tc_inv));
     });
     stage(P, ST_FFT_INV, 2, [&] {
         GG_CUDA(fft_inverse<T>(geo, B, geo.Ny * nout, P->d_tw_x, P->d_tw_z, st));
@@ -326,6 +326,16 @@ void upload_tables(ggem_plan_t* P, const std::vector<double>& cf, const std::vec
     dalloc(P, (T**)&P->d_tw_z, d.size());
     GG_CUDA(cudaMemcpy(P->d_cheb_fwd, a.data(), a.size() * sizeof(T), cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_cheb_inv, b.data(), b.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (sizeof(T) == 4) {
+        // split-bf16 copies for the tensor-core transforms
+        const int Ny = P->prm.Ny;
+        const size_t nb = cheb_tc_prep_bytes(Ny);
+        GG_CUDA(cudaMalloc(&P->d_tc_fwd, nb));
+        GG_CUDA(cudaMalloc(&P->d_tc_inv, nb));
+        GG_CUDA(cheb_tc_prepare(Ny, (const float*)P->d_cheb_fwd, P->d_tc_fwd, 0));
+        GG_CUDA(cheb_tc_prepare(Ny, (const float*)P->d_cheb_inv, P->d_tc_inv, 0));
+        GG_CUDA(cudaDeviceSynchronize());
+    }
     GG_CUDA(cudaMemcpy(P->d_tw_x, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_tw_z, d.data(), d.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
@@ -579,7 +589,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_spart, P->d_sh, P->d_particle, P->d_pcount, P->d_feat,
                     P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
                     P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
-                    P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err};
+                    P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err,
+                    P->d_tc_fwd, P->d_tc_inv};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
