@@ -13,7 +13,13 @@
 namespace ggem {
 
 template <typename T> __device__ __forceinline__ T d_rsqrt(T x);
-template <> __device__ __forceinline__ float d_rsqrt<float>(float x) { return rsqrtf(x); }
+// FP32: the hardware approximations (about 2 ulp); r^2 lies in (0, r_cut^2) and
+// the exponent in (-23, 0], far from denormal inputs and results
+template <> __device__ __forceinline__ float d_rsqrt<float>(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <> __device__ __forceinline__ double d_rsqrt<double>(double x) { return rsqrt(x); }
 
 // locate a point: cell coordinates and offsets from the cell corner
@@ -223,7 +229,7 @@ template <typename T> struct PairAcc {
 
 __device__ __forceinline__ void exp_erfc(const LocalConst<float>& k, float r2, float x, float& ex,
                                          float& ec) {
-    ex = exp2f(k.ke * r2);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(k.ke * r2));
     ec = ex * erfcx_poly(x);
 }
 __device__ __forceinline__ void exp_erfc(const LocalConst<double>& k, double r2, double x,
