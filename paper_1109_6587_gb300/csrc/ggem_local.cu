@@ -220,33 +220,35 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
 
 // Pair arithmetic of Eq. (local), shared by the local-sum kernels.
 // exp(-alpha^2 r^2) and erfc(alpha r) = exp(-x^2) erfcx(x) with the
-// polynomials of ggem_erfcx.cuh (degree 16 in FP32, 26 in FP64), so the pair
-// needs one exponential and no erfc call; the FP32 exponential is 2^(ke r^2).
+// polynomials of ggem_erfcx.cuh (FP32: degree 16; FP64: 8 pieces of degree 12,
+// coefficients in shared memory), so the pair needs one exponential and no
+// erfc call; the FP32 exponential is 2^(ke r^2).
 template <typename T> struct PairAcc {
     T ux = 0, uy = 0, uz = 0;
     T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
 };
 
 __device__ __forceinline__ void exp_erfc(const LocalConst<float>& k, float r2, float x, float& ex,
-                                         float& ec) {
+                                         float& ec, const double*) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(k.ke * r2));
     ec = ex * erfcx_poly(x);
 }
 __device__ __forceinline__ void exp_erfc(const LocalConst<double>& k, double r2, double x,
-                                         double& ex, double& ec) {
+                                         double& ex, double& ec, const double* tab) {
     ex = exp(-k.al2 * r2);
-    ec = ex * erfcx_poly(x);
+    ec = ex * erfcx_poly(x, tab);
 }
 
 // adds G^l g (OUT_U), T^l g (OUT_S) or n . T^l g (OUT_DBL) for displacement
 // (dx, dy, dz) = target - source, 0 < r2 < rc2
 template <typename T, int MODE>
 __device__ __forceinline__ void pair_terms(const LocalConst<T>& k, T dx, T dy, T dz, T r2,
-                                           const v4_t<T>& g, T nx, T ny, T nz, PairAcc<T>& a) {
+                                           const v4_t<T>& g, T nx, T ny, T nz, PairAcc<T>& a,
+                                           const double* tab) {
     const T ir = d_rsqrt<T>(r2);
     const T r = r2 * ir;
     T ex, ec;
-    exp_erfc(k, r2, k.al * r, ex, ec);
+    exp_erfc(k, r2, k.al * r, ex, ec, tab);
     const T xg = dx * g.x + dy * g.y + dz * g.z;
     if (MODE & OUT_U) {
         const T A = ec * ir - k.c1 * ex;
@@ -314,6 +316,12 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     __shared__ int s_off[LW][kNb];            //   neighbour offset index
     __shared__ v4_t<T> s_qd[LW][kQueue];     // queued hits: displacement, r^2
     __shared__ int s_qs[LW][kQueue];         // queued hits: sorted source index
+    __shared__ double s_tab[sizeof(T) == 8 ? (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT : 1];
+    if (sizeof(T) == 8) {
+        for (int e = threadIdx.x; e < (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT; e += blockDim.x)
+            s_tab[e] = kErfcxTab64[e];
+        __syncthreads();
+    }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * LW + wid;
     if (t >= a.n_tgt) return;                     // warp-uniform
@@ -431,7 +439,7 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
                 const int slot = (head + lane) & (kQueue - 1);
                 const v4_t<T> d = s_qd[wid][slot];
                 pair_terms<T, MODE>(a.k, d.x, d.y, d.z, d.w, a.src.g[s_qs[wid][slot]], nx, ny,
-                                    nz, acc);
+                                    nz, acc, s_tab);
                 head = (head + 32) & (kQueue - 1);
                 qn -= 32;
                 __syncwarp();
@@ -442,7 +450,8 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     if (lane < qn) {
         const int slot = (head + lane) & (kQueue - 1);
         const v4_t<T> d = s_qd[wid][slot];
-        pair_terms<T, MODE>(a.k, d.x, d.y, d.z, d.w, a.src.g[s_qs[wid][slot]], nx, ny, nz, acc);
+        pair_terms<T, MODE>(a.k, d.x, d.y, d.z, d.w, a.src.g[s_qs[wid][slot]], nx, ny, nz, acc,
+                            s_tab);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -1,6 +1,6 @@
 """The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the polynomials of
 ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff): degree 16 (FP32),
-degree 26 (FP64).  FP32:
+8 pieces of degree 12 (FP64).  FP32:
 Its coefficients, read from the generated header, must approximate scipy's
 erfcx to 1e-8 relative in FP64 and to 4e-7 (a few FP32 ulps, like CUDA's
 erfcf) when evaluated in FP32 by the same Horner scheme."""
@@ -22,12 +22,11 @@ def _coefficients():
     return [float(first)] + [float(v) for v in rest]    # highest degree first
 
 
-def _coefficients64():
+def _table64():
     txt = HDR.read_text()
-    first = re.search(r"double p = ([-+0-9.eE]+);", txt).group(1)
-    rest = re.findall(r"p = fma\(p, u, ([-+0-9.eE]+)\);", txt)
-    return [float(first)] + [float(v) for v in rest]
-
+    body = re.search(r"kErfcxTab64\[\d+\] = \{(.*?)\};", txt, re.S).group(1)
+    vals = [float(v) for v in re.findall(r"[-+]?\d\.\d+e[-+]\d+", body)]
+    return np.array(vals).reshape(13, 8)          # [power][interval]
 
 def test_polynomial_error():
     c = _coefficients()
@@ -48,16 +47,17 @@ def test_polynomial_error():
 
 
 def test_polynomial_error_fp64():
-    """The FP64 kernels' degree-26 polynomial against mpmath at 40 digits:
-    1e-14 relative (FP64 parity of the pair sums is 1e-10)."""
+    """The FP64 kernels' 8 pieces of degree 12 ([i/2, (i+1)/2], u = 4x - 2i - 1)
+    against mpmath at 40 digits: 3e-15 relative (FP64 parity of the pair sums
+    is 1e-10)."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
-    c = _coefficients64()
-    assert len(c) == 27
+    tab = _table64()
     x = np.linspace(0.0, 4.0, 801)
     ref = np.array([float(mp.exp(mp.mpf(v) ** 2) * mp.erfc(mp.mpf(v))) for v in x])
-    u = x / 2 - 1
-    p = np.full_like(u, c[0])
-    for a in c[1:]:
-        p = p * u + a
-    assert np.abs(p / ref - 1).max() < 1e-14
+    i = np.minimum((x * 2.0).astype(int), 7)
+    u = 4.0 * x - (2.0 * i + 1.0)
+    p = tab[12, i]
+    for j in range(11, -1, -1):
+        p = p * u + tab[j, i]
+    assert np.abs(p / ref - 1).max() < 3e-15
