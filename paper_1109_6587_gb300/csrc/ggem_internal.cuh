@@ -145,8 +145,6 @@ struct ggem_plan {
     int* d_adj_start = nullptr;
     int* d_adj_cur = nullptr;
     int* d_adj = nullptr;
-    int* d_node_cell = nullptr;        // mesh nodes located in caller order
-    void* d_node_pos = nullptr;
 
     // tracing: per-stage device time (CUDA events on the plan's stream)
     bool prof = false;

@@ -541,8 +541,6 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
         dalloc(P, &P->d_adj, (size_t)prm.max_tris * 3);
     }
     P->rule = make_quad_rule();
-    dalloc(P, &P->d_node_cell, cap);
-    GG_CUDA(cudaMalloc(&P->d_node_pos, cap * v4 + 32));
     if (prm.quadrature == GGEM_ELEMENT && prm.max_tris > 0) {
         size_t cq = (size_t)16 * prm.max_tris;
         GG_CHECK(cq < (size_t)1 << 31, GGEM_ERR_CAPACITY, "too many quadrature points");
@@ -584,7 +582,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_tri_area, P->d_tri_nrm, P->d_mesh_cell, P->d_mesh_perm,
                     P->d_mesh_start, P->d_mesh_pos, P->d_qx, P->d_qv, P->d_qw, P->d_qp_cell,
                     P->d_qp_perm, P->d_qp_start, P->d_qp_pos, P->d_qg, P->d_adj_cnt,
-                    P->d_adj_start, P->d_adj_cur, P->d_adj, P->d_node_cell, P->d_node_pos,
+                    P->d_adj_start, P->d_adj_cur, P->d_adj,
                     P->d_qv_sorted, P->d_V, P->d_sv, P->d_sb, P->d_sk, P->d_sx,
                     P->d_spart, P->d_sh, P->d_particle, P->d_pcount, P->d_feat,
                     P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
@@ -718,14 +716,10 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 GG_CUDA(build_cells<double>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                             P->d_qp_start, P->d_cursor, P->d_qp_cell,
                                             P->d_qp_perm, (double4_32a*)P->d_qp_pos, st));
-                GG_CUDA(locate_targets<double>(P->geo, P->cg, n_nodes, TK_POINTS, P->d_x,
-                                               P->d_node_cell, (double4_32a*)P->d_node_pos, st));
             } else {
                 GG_CUDA(build_cells<float>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                            P->d_qp_start, P->d_cursor, P->d_qp_cell,
                                            P->d_qp_perm, (float4*)P->d_qp_pos, st));
-                GG_CUDA(locate_targets<float>(P->geo, P->cg, n_nodes, TK_POINTS, P->d_x,
-                                              P->d_node_cell, (float4*)P->d_node_pos, st));
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
             P->n_qp = nq;
