@@ -184,6 +184,7 @@ struct ggem_plan {
     int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
     int* d_tc_err = nullptr;           // tensor-core kernels: expired waits
+    int* d_spread_list = nullptr;      // [cap + 1] sources the paired spread hands back
     void* d_tc_fwd = nullptr;          // split-bf16 Chebyshev matrices (mixed plans)
     void* d_tc_inv = nullptr;
     int nsm = 0;                       // multiprocessors of the plan's device
@@ -266,7 +267,7 @@ cudaError_t spread_prepare(const GridGeom& geo, const double* yj, int n, const i
 template <typename T>
 cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, const T* ydiff,
                    const SortedSources<T>& src, const int4* di, const v4_t<T>* df, T* grid,
-                   T* work, cudaStream_t st);
+                   T* work, int* list, cudaStream_t st);
 
 template <typename T>
 cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* tw_x,

@@ -114,10 +114,11 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
         GG_CUDA(local_sum<T>(geo, P->cg, src, TK_WALL, 2 * geo.Nz * geo.Nx, P->d_wall_cell,
                              (const v4_t<T>*)P->d_wall_pos, nullptr, OUT_U, Wl, 0, st));
     });
-    stage(P, ST_SPREAD, 2, [&] {
+    stage(P, ST_SPREAD, sizeof(T) == 4 ? 3 : 2, [&] {
         GG_CUDA(spread<T>(geo, P->cg, P->d_yj, (const T*)P->d_ydiff, src,
                           mesh ? P->d_mesh_sdi : P->d_sdi,
-                          (const v4_t<T>*)(mesh ? P->d_mesh_sdf : P->d_sdf), A, B, st));
+                          (const v4_t<T>*)(mesh ? P->d_mesh_sdf : P->d_sdf), A, B,
+                          P->d_spread_list, st));
     });
     stage(P, ST_FFT_FWD, 4, [&] {
         GG_CUDA(fft_forward<T>(geo, A, geo.Ny * 3, P->d_tw_x, P->d_tw_z, st));
@@ -487,6 +488,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     dalloc(P, &P->d_cell_count, P->ncell);
     dalloc(P, &P->d_cell_start, P->ncell + 1);
     dalloc(P, &P->d_tc_err, 1);
+    dalloc(P, &P->d_spread_list, (size_t)cap + 1);
     GG_CUDA(cudaMemset(P->d_tc_err, 0, sizeof(int)));
     {
         int dev = 0;
@@ -588,7 +590,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
                     P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
                     P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err,
-                    P->d_tc_fwd, P->d_tc_inv};
+                    P->d_tc_fwd, P->d_tc_inv, P->d_spread_list};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);

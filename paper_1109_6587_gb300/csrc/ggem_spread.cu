@@ -81,17 +81,25 @@ __device__ __forceinline__ void red4(double* p, double a, double b, double c) {
 // the (column, row) pairs of the disc; each lane runs the planes of its pair
 // with dy^2 < rc^2 - dx^2 - dz^2 and adds into the interleaved buffer with one
 // vector reduction per node.
+// With `list`, warp i handles source list[i] for i < *nlist (the sources the
+// paired kernel handed back); otherwise source i for i < n.
 template <typename T>
 __global__ void __launch_bounds__(SW * 32) k_spread_scatter(
     GridGeom geo, SpreadConst<T> kc, const T* __restrict__ ydiff, int n, int R,
     const int4* __restrict__ sdi, const v4_t<T>* __restrict__ sdf,
-    const v4_t<T>* __restrict__ gsrc, T* __restrict__ f4) {
+    const v4_t<T>* __restrict__ gsrc, T* __restrict__ f4, const int* __restrict__ list,
+    const int* __restrict__ nlist) {
     __shared__ T s_xd2[SW][MAXR], s_xe[SW][MAXR], s_zd2[SW][MAXR], s_ze[SW][MAXR];
     __shared__ int s_xi[SW][MAXR], s_zi[SW][MAXR];
     __shared__ T s_yd2[SW][MAXJ], s_ye[SW][MAXJ];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * SW + wid;
-    if (s >= n) return;                            // warp-uniform
+    int s = blockIdx.x * SW + wid;
+    if (list) {
+        if (s >= *nlist) return;                   // warp-uniform
+        s = list[s];
+    } else if (s >= n) {
+        return;                                    // warp-uniform
+    }
     const T rc2 = kc.rc2, al2 = kc.al2;
     const int4 di = sdi[s];
     const v4_t<T> df = sdf[s];
@@ -151,6 +159,113 @@ __global__ void __launch_bounds__(SW * 32) k_spread_scatter(
     }
 }
 
+// Two consecutive sorted sources per warp (FP32).  Neighbouring sources share
+// most of their stencils, so the warp walks the union of the two stencils,
+// evaluates both weights at every node and issues one vector reduction with
+// their sum: fewer reductions, which bound this kernel.  A pair whose union
+// does not fit 32 columns or 32 rows (sources far apart in the sorted order)
+// is handed to the single-source path.
+constexpr int PMAXJ = 272;
+__global__ void __launch_bounds__(SW * 32) k_spread_pair(
+    GridGeom geo, SpreadConst<float> kc, const float* __restrict__ ydiff, int n, int R,
+    const int4* __restrict__ sdi, const float4* __restrict__ sdf,
+    const float4* __restrict__ gsrc, float* __restrict__ f4, int* __restrict__ leftover,
+    int* __restrict__ nleft) {
+    __shared__ float s_xd2[SW][2][32], s_xe[SW][2][32], s_zd2[SW][2][32], s_ze[SW][2][32];
+    __shared__ int s_xi[SW][32], s_zi[SW][32];
+    __shared__ float s_yd2[SW][2][PMAXJ], s_ye[SW][2][PMAXJ];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s0 = 2 * (blockIdx.x * SW + wid);
+    if (s0 >= n) return;                                    // warp-uniform
+    const bool two = s0 + 1 < n;
+    const int4 d0 = sdi[s0];
+    const int4 d1 = two ? sdi[s0 + 1] : d0;
+    const int Nx = geo.Nx, Nz = geo.Nz;
+    // signed periodic offsets of source 1's base column/row from source 0's
+    int ox = d1.x - d0.x, oz = d1.y - d0.y;
+    ox -= (ox > Nx / 2) ? Nx : 0;
+    ox += (ox < -Nx / 2) ? Nx : 0;
+    oz -= (oz > Nz / 2) ? Nz : 0;
+    oz += (oz < -Nz / 2) ? Nz : 0;
+    const int nr = 2 * R + 2;
+    // the union of offsets [-R, R+1] (source 0) and [o - R, o + R + 1] (source 1),
+    // relative to source 0's base column / row
+    const int bx = min(0, ox) - R, bz = min(0, oz) - R;
+    const int spx = max(0, ox) - min(0, ox) + nr, spz = max(0, oz) - min(0, oz) + nr;
+    if (!two || spx > 32 || spz > 32) {
+        if (lane == 0) {
+            leftover[atomicAdd(nleft, 1)] = s0;
+            if (two) leftover[atomicAdd(nleft, 1)] = s0 + 1;
+        }
+        return;
+    }
+    const float rc2 = kc.rc2, al2 = kc.al2;
+    const float4 f0 = sdf[s0], f1 = sdf[s0 + 1];
+    // columns and rows of the union: lane = union offset
+    {
+        const int c = bx + lane;                              // column offset from s0's base
+        float v0x = 1e30f, v1x = 1e30f;
+        if (lane < spx) {
+            const int o0 = c + R, o1 = c - ox + R;            // offsets into each stencil
+            if (o0 >= 0 && o0 < nr) { float v = fmaf((float)(o0 - R), kc.dx, -f0.x); v0x = v * v; }
+            if (o1 >= 0 && o1 < nr) { float v = fmaf((float)(o1 - R), kc.dx, -f1.x); v1x = v * v; }
+        }
+        s_xd2[wid][0][lane] = v0x;
+        s_xd2[wid][1][lane] = v1x;
+        s_xe[wid][0][lane] = v0x < rc2 ? expf(-al2 * v0x) : 0.f;
+        s_xe[wid][1][lane] = v1x < rc2 ? expf(-al2 * v1x) : 0.f;
+        s_xi[wid][lane] = (d0.x + c) & (Nx - 1);
+        const int r = bz + lane;
+        float v0z = 1e30f, v1z = 1e30f;
+        if (lane < spz) {
+            const int o0 = r + R, o1 = r - oz + R;
+            if (o0 >= 0 && o0 < nr) { float v = fmaf((float)(o0 - R), kc.dz, -f0.y); v0z = v * v; }
+            if (o1 >= 0 && o1 < nr) { float v = fmaf((float)(o1 - R), kc.dz, -f1.y); v1z = v * v; }
+        }
+        s_zd2[wid][0][lane] = v0z;
+        s_zd2[wid][1][lane] = v1z;
+        s_ze[wid][0][lane] = v0z < rc2 ? expf(-al2 * v0z) : 0.f;
+        s_ze[wid][1][lane] = v1z < rc2 ? expf(-al2 * v1z) : 0.f;
+        s_zi[wid][lane] = (d0.y + r) & (Nz - 1);
+    }
+    // planes: union of the two y-ranges
+    const int jlo = min(d0.w & 0xffff, d1.w & 0xffff), jhi = max(d0.w >> 16, d1.w >> 16);
+    const int ny = jhi - jlo + 1;
+    for (int q = lane; q < ny; q += 32) {
+        const float a0 = ydiff[(size_t)(jlo + q) * geo.Ny + d0.z] - f0.z;
+        const float a1 = ydiff[(size_t)(jlo + q) * geo.Ny + d1.z] - f1.z;
+        s_yd2[wid][0][q] = a0 * a0;
+        s_yd2[wid][1][q] = a1 * a1;
+        s_ye[wid][0][q] = expf(-al2 * a0 * a0);
+        s_ye[wid][1][q] = expf(-al2 * a1 * a1);
+    }
+    __syncwarp();
+    const float4 g0 = gsrc[s0], g1 = gsrc[s0 + 1];
+    const float ax = -kc.cn * g0.x, ay = -kc.cn * g0.y, az = -kc.cn * g0.z;
+    const float bxg = -kc.cn * g1.x, byg = -kc.cn * g1.y, bzg = -kc.cn * g1.z;
+    const int npair = spx * spz;
+    const float inx = 1.0f / (float)spx;
+    const size_t rowst = (size_t)Nx * 4, planest = (size_t)Nz * Nx * 4;
+    for (int pi = lane; pi < npair; pi += 32) {
+        const int b = (int)(((float)pi + 0.5f) * inx);
+        const int a = pi - b * spx;
+        const float e0 = s_xd2[wid][0][a] + s_zd2[wid][0][b];
+        const float e1 = s_xd2[wid][1][a] + s_zd2[wid][1][b];
+        if (!(e0 < rc2) && !(e1 < rc2)) continue;
+        const float x0 = s_xe[wid][0][a] * s_ze[wid][0][b];
+        const float x1 = s_xe[wid][1][a] * s_ze[wid][1][b];
+        float* col = f4 + (size_t)s_zi[wid][b] * rowst + (size_t)s_xi[wid][a] * 4;
+        for (int q = 0; q < ny; ++q) {
+            const float r0 = e0 + s_yd2[wid][0][q], r1 = e1 + s_yd2[wid][1][q];
+            const float w0 = r0 < rc2 ? x0 * s_ye[wid][0][q] * (2.5f - al2 * r0) : 0.f;
+            const float w1 = r1 < rc2 ? x1 * s_ye[wid][1][q] * (2.5f - al2 * r1) : 0.f;
+            if (w0 == 0.f && w1 == 0.f) continue;
+            red4(col + (size_t)(jlo + q) * planest, fmaf(ax, w0, bxg * w1),
+                 fmaf(ay, w0, byg * w1), fmaf(az, w0, bzg * w1));
+        }
+    }
+}
+
 // interleaved [Ny][Nz][Nx][4] -> planar [Ny][3][Nz][Nx]
 template <typename T>
 __global__ void k_deinterleave(int Ny, int Nz, int Nx, const T* __restrict__ f4,
@@ -177,7 +292,7 @@ cudaError_t spread_prepare(const GridGeom& geo, const double* yj, int n, const i
 template <typename T>
 cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, const T* ydiff,
                    const SortedSources<T>& src, const int4* di, const v4_t<T>* df, T* grid,
-                   T* work, cudaStream_t st) {
+                   T* work, int* list, cudaStream_t st) {
     (void)cg; (void)yj;
     int R = (int)std::ceil(std::max(geo.rcut / geo.dx, geo.rcut / geo.dz)) + 1;
     if (2 * R + 2 > MAXR || geo.Ny > MAXJ) return cudaErrorInvalidConfiguration;
@@ -189,9 +304,22 @@ cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, co
     kc.cn = (T)(geo.alpha * geo.alpha * geo.alpha / (pi * std::sqrt(pi)));
     size_t nodes = (size_t)geo.Ny * geo.Nz * geo.Nx;
     cudaMemsetAsync(work, 0, nodes * 4 * sizeof(T), st);
-    if (src.n > 0)
-        k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(geo, kc, ydiff, src.n, R,
-                                                                      di, df, src.g, work);
+    if (src.n > 0) {
+        if (sizeof(T) == 4 && list && geo.Ny <= PMAXJ) {
+            // pairs of sources; the pairs that do not fit go back to the single path
+            int* nleft = list + src.n;
+            cudaMemsetAsync(nleft, 0, sizeof(int), st);
+            const int npairs = (src.n + 1) / 2;
+            k_spread_pair<<<(npairs + SW - 1) / SW, SW * 32, 0, st>>>(
+                geo, *reinterpret_cast<const SpreadConst<float>*>(&kc), (const float*)ydiff,
+                src.n, R, di, (const float4*)df, (const float4*)src.g, (float*)work, list, nleft);
+            k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(
+                geo, kc, ydiff, src.n, R, di, df, src.g, work, list, nleft);
+        } else {
+            k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(
+                geo, kc, ydiff, src.n, R, di, df, src.g, work, nullptr, nullptr);
+        }
+    }
     k_deinterleave<T><<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(geo.Ny, geo.Nz, geo.Nx,
                                                                        work, grid);
     return cudaGetLastError();
@@ -202,7 +330,7 @@ cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, co
                                            const double*, int4*, v4_t<T>*, cudaStream_t);       \
     template cudaError_t spread<T>(const GridGeom&, const CellGrid&, const double*, const T*,   \
                                    const SortedSources<T>&, const int4*, const v4_t<T>*, T*,    \
-                                   T*, cudaStream_t);
+                                   T*, int*, cudaStream_t);
 GGEM_INST_SPREAD(float)
 GGEM_INST_SPREAD(double)
 
