@@ -409,6 +409,41 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         const T tz = oz - (T)(oi / 25 - 2) * a.k.hz;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
+            if (ELEM && sizeof(T) == 4) {
+                // Element rule in FP32: about 70 % of the candidates are inside
+                // r_cut and cells hold ~1,500 points, so every lane evaluates its
+                // candidate and a miss contributes nothing (its strength is
+                // zeroed; every term carries a factor g, and the arithmetic stays
+                // finite for r < 2 r_cut).  Quadrature points never sit on a node
+                // (r > 0).  In FP64 the pair arithmetic is the scarce resource and
+                // the hit queue below is kept.
+                bool hit = false;
+                T dx = 0, dy = 0, dz = 0, r2 = 0;
+                int s = st;
+                if (i < cnt) {
+                    s = st + i;
+                    const v4_t<T> p = a.src.pos[s];
+                    dx = tx - p.x;
+                    dy = ty - p.y;
+                    dz = tz - p.z;
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    hit = r2 < rc2;
+                    if (hit && r2 < a.near2) {
+                        const int4 v = a.qvs[s];
+                        hit = !(v.x == oidx || v.y == oidx || v.z == oidx);
+                    }
+                }
+                if (!__any_sync(0xffffffffu, hit)) continue;
+                if (i < cnt) {
+                    v4_t<T> g = a.src.g[s];
+                    if (!hit) {
+                        g.x = 0; g.y = 0; g.z = 0;
+                        r2 = rc2;               // any in-range value: the terms vanish
+                    }
+                    pair_terms<T, MODE>(a.k, dx, dy, dz, r2, g, nx, ny, nz, acc, s_tab);
+                }
+                continue;
+            }
             bool hit = false;
             T dx = 0, dy = 0, dz = 0, r2 = 0;
             int s = 0;
