@@ -26,6 +26,7 @@ struct CellGrid {
     int ncx, ncy, ncz;
     double hx, hy, hz;
     double y0;
+    int reach = 3;   // cells are at least r_cut / reach wide; searches span +-reach cells (2 or 3)
 };
 
 // Geometry and GGEM constants handed to kernels by value.

@@ -1,10 +1,11 @@
 // Cell list and GGEM local sums (paper Sec. 3.2.1, Eqs. (local), (u_loc)).
 //
-// Sources are binned into cells no smaller than r_cut/2 and stored as offsets
+// Sources are binned into cells no smaller than r_cut/R (R = 2 or 3, the
+// grid's search reach) and stored as offsets
 // from their cell's corner, so every displacement is formed from small
 // numbers (integer cell shift + offset difference) and stays accurate in FP32
 // whatever the box size.  x and z are periodic: the neighbour shift of up to
-// +-2 cells carries the image; as r_cut < L/2 (Sec. 3.2.2, alpha L > 8), at
+// +-R cells carries the image; as r_cut < L/2 (Sec. 3.2.2, alpha L > 8), at
 // most one image of a source lies within r_cut even where a small grid
 // visits a cell twice.
 #include "ggem_internal.cuh"
@@ -297,23 +298,23 @@ __device__ __forceinline__ void store_target(const LocalConst<T>& k, const PairA
 // u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
 // (unscaled in the loop; the caller-facing factors are applied at the end).
 //
-// One warp per target.  The warp lists the neighbour cells (offsets -2..2)
+// One warp per target.  The warp lists the neighbour cells (offsets -R..R)
 // that come within r_cut of the target, then walks them one at a time with
 // consecutive lanes on consecutive sorted sources (coalesced float4 loads).
 // The hits are compacted into a per-warp queue and evaluated 32 at a time.
 // Partial sums are reduced with warp shuffles.
 constexpr int LW = 8;       // warps (targets) per block
 constexpr int kQueue = 64;  // hit queue per warp: < 32 left + <= 32 new always fit
-constexpr int kNb = 125;    // neighbour cell offsets -2..2 in each direction
+constexpr int kNb = 7 * 7 * 7;   // neighbour cell offsets for the largest reach (3)
 
 // ELEM: sources are element quadrature points and targets are mesh nodes
 // (caller index t); points of triangles having the target as a vertex are
 // skipped (their integral is done by the polar rule, Sec. 3.4.1).
-template <typename T, int KIND, int MODE, bool ELEM = false>
+template <typename T, int KIND, int MODE, bool ELEM, int REACH>
 __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     __shared__ int s_cst[LW][kNb];            // this target's cells: first source,
     __shared__ int s_cnt[LW][kNb];            //   source count,
-    __shared__ int s_off[LW][kNb];            //   neighbour offset index
+    __shared__ unsigned short s_off[LW][kNb]; //   neighbour offset index
     __shared__ v4_t<T> s_qd[LW][kQueue];     // queued hits: displacement, r^2
     __shared__ int s_qs[LW][kQueue];         // queued hits: sorted source index
     __shared__ double s_tab[sizeof(T) == 8 ? (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT : 1];
@@ -345,33 +346,30 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         cy = (c / cg.ncx) % cg.ncy;
         cz = c / (cg.ncx * cg.ncy);
     }
-    // Neighbour cells at offsets -2..2 (cells are at least r_cut/2 wide); keep
-    // the non-empty ones whose nearest point lies within r_cut of the target
-    // (a slightly widened r_cut, so rounding can only keep more).
+    // Neighbour cells at offsets -R..R (cells are at least r_cut/R wide, R =
+    // REACH = cg.reach); keep the non-empty ones whose nearest point lies within r_cut
+    // of the target (a slightly widened r_cut, so rounding can only keep more).
     const unsigned lt = (1u << lane) - 1u;
     const T reach2 = a.k.rc2 * (T)1.0001;
+    constexpr int R = REACH, side = 2 * R + 1, nb = side * side * side;
     int nc = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < (nb + 31) / 32; ++r) {
         const int oi = r * 32 + lane;
         bool keep = false;
         int st = 0, cnt = 0;
-        if (oi < kNb) {
-            const int ix = oi % 5 - 2, iy = (oi / 5) % 5 - 2, iz = oi / 25 - 2;
+        if (oi < nb) {
+            const int ix = oi % side - R, iy = (oi / side) % side - R, iz = oi / (side * side) - R;
             const int cyy = cy + iy;
             if (cyy >= 0 && cyy < cg.ncy) {
                 const T gx = ix > 0 ? (T)ix * a.k.hx - ox : (ix < 0 ? ox - (T)(ix + 1) * a.k.hx : (T)0);
                 const T gy = iy > 0 ? (T)iy * a.k.hy - oy : (iy < 0 ? oy - (T)(iy + 1) * a.k.hy : (T)0);
                 const T gz = iz > 0 ? (T)iz * a.k.hz - oz : (iz < 0 ? oz - (T)(iz + 1) * a.k.hz : (T)0);
                 if (gx * gx + gy * gy + gz * gz <= reach2) {
+                    // ncx, ncz >= 2 R (L > 2 r_cut): one wrap suffices for |i| <= R
                     int cxx = cx + ix, czz = cz + iz;
                     cxx += (cxx < 0) ? cg.ncx : 0;
-                    cxx += (cxx < 0) ? cg.ncx : 0;
-                    cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
                     cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
                     czz += (czz < 0) ? cg.ncz : 0;
-                    czz += (czz < 0) ? cg.ncz : 0;
-                    czz -= (czz >= cg.ncz) ? cg.ncz : 0;
                     czz -= (czz >= cg.ncz) ? cg.ncz : 0;
                     const int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
                     st = a.src.cell_start[c];
@@ -404,9 +402,9 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     for (int ci = 0; ci < nc; ++ci) {
         const int st = s_cst[wid][ci], cnt = s_cnt[wid][ci], oi = s_off[wid][ci];
         // target position in the frame of this source cell's corner
-        const T tx = ox - (T)(oi % 5 - 2) * a.k.hx;
-        const T ty = oy - (T)((oi / 5) % 5 - 2) * a.k.hy;
-        const T tz = oz - (T)(oi / 25 - 2) * a.k.hz;
+        const T tx = ox - (T)(oi % side - R) * a.k.hx;
+        const T ty = oy - (T)((oi / side) % side - R) * a.k.hy;
+        const T tz = oz - (T)(oi / (side * side) - R) * a.k.hz;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
             if (ELEM && sizeof(T) == 4) {
@@ -519,16 +517,26 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     store_target<T, MODE>(a.k, acc, a.out + (size_t)oidx * a.out_stride);
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, int REACH>
 static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     dim3 b(LW * 32), g((a.n_tgt + LW - 1) / LW);
     switch (mode) {
-        case OUT_U: k_local<T, KIND, OUT_U><<<g, b, 0, st>>>(a); break;
-        case OUT_S: k_local<T, KIND, OUT_S><<<g, b, 0, st>>>(a); break;
-        case OUT_U | OUT_S: k_local<T, KIND, OUT_U | OUT_S><<<g, b, 0, st>>>(a); break;
-        case OUT_DBL: k_local<T, KIND, OUT_DBL><<<g, b, 0, st>>>(a); break;
+        case OUT_U: k_local<T, KIND, OUT_U, false, REACH><<<g, b, 0, st>>>(a); break;
+        case OUT_S: k_local<T, KIND, OUT_S, false, REACH><<<g, b, 0, st>>>(a); break;
+        case OUT_U | OUT_S:
+            k_local<T, KIND, OUT_U | OUT_S, false, REACH><<<g, b, 0, st>>>(a);
+            break;
+        case OUT_DBL: k_local<T, KIND, OUT_DBL, false, REACH><<<g, b, 0, st>>>(a); break;
         default: break;
     }
+}
+
+// the grid's search reach as a compile-time constant (cells >= r_cut/2 or
+// r_cut/3; grids of larger cells use reach 2)
+template <typename T, int KIND>
+static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
+    if (a.cg.reach == 3) launch_kind<T, KIND, 3>(a, mode, st);
+    else launch_kind<T, KIND, 2>(a, mode, st);
 }
 
 template <typename T>
@@ -542,8 +550,13 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
                    tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
     dim3 b(LW * 32), g((tgt.n + LW - 1) / LW);
-    if (layer == 0) k_local<T, TK_POINTS, OUT_U, true><<<g, b, 0, st>>>(a);
-    else k_local<T, TK_POINTS, OUT_DBL, true><<<g, b, 0, st>>>(a);
+    if (cg.reach == 3) {
+        if (layer == 0) k_local<T, TK_POINTS, OUT_U, true, 3><<<g, b, 0, st>>>(a);
+        else k_local<T, TK_POINTS, OUT_DBL, true, 3><<<g, b, 0, st>>>(a);
+    } else {
+        if (layer == 0) k_local<T, TK_POINTS, OUT_U, true, 2><<<g, b, 0, st>>>(a);
+        else k_local<T, TK_POINTS, OUT_DBL, true, 2><<<g, b, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

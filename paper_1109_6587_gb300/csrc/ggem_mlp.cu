@@ -79,7 +79,7 @@ __global__ void k_feat_local(int n, const double* __restrict__ x, const double* 
 }
 
 // Crowding: nodes of other particles within r_cut (minimum image), one warp
-// per node over the mesh cell list (cells at least r_cut/2 wide).  The
+// per node over the mesh cell list (cells at least r_cut/R wide, R = reach).  The
 // distance is formed in FP64 with every product and sum rounded separately,
 // the same operations in the same order as the oracle, so the integer count
 // does not depend on contraction into FMAs.
@@ -95,13 +95,14 @@ __global__ void k_feat_crowd(int n, GridGeom geo, CellGrid cg, const double* __r
     const int cx = c % cg.ncx, cy = (c / cg.ncx) % cg.ncy, cz = c / (cg.ncx * cg.ncy);
     const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
     const int pi = particle[i];
-    // distinct cells within +-2 in x and z (all of them on a grid narrower
-    // than 5 cells), +-2 in y; each node is met once
-    const int nxo = min(5, cg.ncx), nzo = min(5, cg.ncz);
-    const int x0 = cg.ncx >= 5 ? cx - 2 : 0, z0 = cg.ncz >= 5 ? cz - 2 : 0;
+    // distinct cells within +-R in x and z (all of them on a grid narrower
+    // than 2R + 1 cells), +-R in y; each node is met once
+    const int R = cg.reach, side = 2 * R + 1;
+    const int nxo = min(side, cg.ncx), nzo = min(side, cg.ncz);
+    const int x0 = cg.ncx >= side ? cx - R : 0, z0 = cg.ncz >= side ? cz - R : 0;
     int count = 0;
     for (int a = 0; a < nzo; ++a)
-        for (int dy = -2; dy <= 2; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             const int cyy = cy + dy;
             if (cyy < 0 || cyy >= cg.ncy) continue;
             const int czz = ((z0 + a) % cg.ncz + cg.ncz) % cg.ncz;

@@ -110,6 +110,7 @@ extern "C" ggem_status ggem_local_velocity_noalloc(const ggem_params* prm, void*
     cg.ncz = (int)fmax(1.0, floor(prm->Lz / geo.rcut));
     cg.ncy = (int)fmax(1.0, floor(prm->W / geo.rcut));
     cg.hx = prm->Lx / cg.ncx; cg.hz = prm->Lz / cg.ncz; cg.hy = prm->W / cg.ncy;
+    cg.reach = 2;                                   // cells at least r_cut wide (>= r_cut/2)
     cg.y0 = prm->y0;
     if ((long)cg.ncx * cg.ncy * cg.ncz > kMaxCells) return GGEM_ERR_CAPACITY;
 

@@ -369,11 +369,13 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     P->fp64 = prm.precision == GGEM_FP64;
     P->nmodes = prm.Nz * g.nkx;
     CellGrid& cg = P->cg;
-    // cells at least r_cut/2 wide: the local sums search +-2 cells and keep
-    // those within r_cut of each target
-    cg.ncx = std::max(1, (int)std::floor(prm.Lx / (0.5 * g.rcut)));
-    cg.ncz = std::max(1, (int)std::floor(prm.Lz / (0.5 * g.rcut)));
-    cg.ncy = std::max(1, (int)std::floor(prm.W / (0.5 * g.rcut)));
+    // cells at least r_cut/R wide; the local sums search +-R cells and keep
+    // those within r_cut of each target.  R = 3 for the element rule (dense
+    // quadrature points: smaller cells cut the candidates), 2 for nodal sources
+    cg.reach = prm.quadrature == GGEM_ELEMENT ? 3 : 2;
+    cg.ncx = std::max(1, (int)std::floor(prm.Lx / (g.rcut / cg.reach)));
+    cg.ncz = std::max(1, (int)std::floor(prm.Lz / (g.rcut / cg.reach)));
+    cg.ncy = std::max(1, (int)std::floor(prm.W / (g.rcut / cg.reach)));
     cg.hx = prm.Lx / cg.ncx; cg.hz = prm.Lz / cg.ncz; cg.hy = prm.W / cg.ncy;
     cg.y0 = prm.y0;
     P->ncell = cg.ncx * cg.ncy * cg.ncz;
