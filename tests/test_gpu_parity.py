@@ -237,3 +237,28 @@ def test_element_100_capsules_sampled(ggem, prec):
     torch.cuda.synchronize()
     assert _rel(w[idx], w_ref) < TOL[prec]
     assert _rel(v[idx], v_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(32, 17, 64), (64, 9, 32)])
+def test_point_forces_anisotropic_grids(ggem, prec, shape):
+    """Grids with Nx != Nz and the smallest Chebyshev order (Ny = 9): random
+    point forces, velocity and stress at separate random targets."""
+    nx, ny, nz = shape
+    dx = 0.25
+    box = W.Box(Lx=nx * dx, Lz=nz * dx, W=(ny - 1) * dx, y0=-0.5 * (ny - 1) * dx,
+                Nx=nx, Ny=ny, Nz=nz)
+    rng = np.random.default_rng(nx + ny)
+    def pts(k):
+        return np.stack([rng.uniform(0, box.Lx, k),
+                         rng.uniform(box.y0 + 0.05, box.y0 + box.W - 0.05, k),
+                         rng.uniform(0, box.Lz, k)], 1)
+    xs, xt = pts(300), pts(200)
+    g = rng.standard_normal((300, 3))
+    u_ref, s_ref = O.point_forces(box, xs, g, xt, want_sig=True)
+    P = ggem.Plan.for_box(box, precision=prec, max_points=300)
+    u, sig = P.point_forces(_dev(xs), _dev(g), _dev(xt), want_sigma=True)
+    torch.cuda.synchronize()
+    assert _rel(u, u_ref) < TOL[prec]
+    assert _rel(sig, _sym6(s_ref)) < TOL[prec]
+    P.check()
