@@ -252,7 +252,10 @@ def run_mine(args, rank, world):
 
 
 def roofline(res, args):
-    """Dominant stage against its bound (roofline accounting)."""
+    """The stage with the most device time against the bound of its kernel:
+    the local sum against the FP32 issue rate (algorithmic flops per pair x
+    the pairs within r_cut), the other stages against HBM bandwidth
+    (algorithmic bytes of one launch)."""
     peaks, kind = _peaks()
     stages = res["stages"]
     name, (tot, calls) = max(stages.items(), key=lambda kv: kv[1][0])
@@ -275,9 +278,12 @@ def roofline(res, args):
         ach = flops / avg_s / 1e12
         if args.precision == "fp64":
             peak = 1.25
-        # dram read + write bytes of one double-layer launch, ncu capture of this
-        # kernel on this workload (profiles/k_local_elem_dbl_capsules100_mixed.md)
-        traffic = None        # re-captured with ncu after each change of the kernel
+        # dram read + write bytes of one double-layer launch of the mixed
+        # element-rule kernel on this workload, from one ncu capture of that
+        # launch (its ncu summary is kept with the profiles); other
+        # configurations have no capture
+        traffic = (114.4e6 + 4.5e6) if (args.precision == "mixed"
+                                        and args.quadrature == "element") else None
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
