@@ -15,8 +15,9 @@ Paper: Kumar & Graham, arXiv 1109.6587.  Steps, in the paper's order:
   6. stress sigma^g = -p + mu (grad u + grad u^T) ..... Sec. 3.5.1
   7. 4th-order (5-point) Lagrange interpolation ....... Sec. 3.2.2
   8. u = u^l + u^g ..................................... Eq. (tot_l_g)
-Boundary integral operators (Sec. 3.4, 3.5) and the Fredholm solve (Sec. 5,
-restarted GMRES with modified Gram-Schmidt) are built on top.
+Boundary integral operators (Sec. 3.4, 3.5), the Fredholm solve (Sec. 5,
+restarted GMRES with modified Gram-Schmidt) and the rigid-particle solve
+(Sec. 6.1, Eq. (sl_r) with force and torque balance) are built on top.
 
 Readings (the paper is silent, ambiguous or garbled here):
   * alpha = 1/(2 h), h = max(Lx/Nx, W/(Ny-1), Lz/Nz); r_cut = 4/alpha.
@@ -640,3 +641,81 @@ def bie_solve(susp, kappa, b, q0=None, tol=1e-6, restart=30, maxit=300,
     x, its, rr, ok = gmres(apply, np.asarray(b).ravel(), None if q0 is None else np.asarray(q0).ravel(),
                            tol, restart, maxit)
     return x.reshape(n, 3), its, rr, ok
+
+
+# ------------------------------------------- rigid particles (Sec. 6.1)
+
+def rigid_scales(susp, mu=1.0):
+    """Per particle: surface area S_p = sum of its nodal areas and the radius
+    R_p = sqrt(S_p / 4 pi) of the sphere with that area."""
+    _, _, Ab, _ = geometry(susp.x, susp.tri)
+    n_p = int(susp.particle.max()) + 1
+    S = np.zeros(n_p)
+    np.add.at(S, susp.particle, Ab)
+    return S, np.sqrt(S / (4.0 * math.pi))
+
+
+def rigid_operator(susp, centres, f, UO, quadrature="element", mu=1.0, alpha=None, rcut=None):
+    """The rigid-particle system of Sec. 6.1 applied to (f, U, Omega).
+
+    Velocity rows, one per node b of particle p (Eq. (sl_r) with the surface
+    velocity U_p + Omega_p x (x_b - c_p) of a rigid body moved to the left):
+        U_p + Omega_p x (x_b - c_p) + 1/(8 pi mu) int f_i G_ji dS
+    Balance rows, per particle, in velocity units (reading: the paper states
+    the force- and torque-free conditions but no discrete form or scaling):
+        -(1/(6 pi mu R_p))   sum_b A_b f_b
+        -(1/(8 pi mu R_p^2)) sum_b A_b (x_b - c_p) x f_b
+    with the trapezoidal nodal areas A_b.  f [N, 3], UO [P, 6] (U, Omega).
+    Returns (rows [N, 3], balance [P, 6])."""
+    f = _f64(f)
+    UO = _f64(UO).reshape(-1, 6)
+    c = _f64(centres).reshape(-1, 3)
+    p = susp.particle
+    r = susp.x - c[p]
+    w = single_layer(susp, f, quadrature, mu, alpha, rcut)
+    rows = UO[p, :3] + np.cross(UO[p, 3:], r) + w / (8.0 * math.pi * mu)
+    _, _, Ab, _ = geometry(susp.x, susp.tri)
+    _, R = rigid_scales(susp, mu)
+    n_p = UO.shape[0]
+    F = np.zeros((n_p, 3))
+    T = np.zeros((n_p, 3))
+    np.add.at(F, p, Ab[:, None] * f)
+    np.add.at(T, p, Ab[:, None] * np.cross(r, f))
+    bal = np.hstack([-F / (6.0 * math.pi * mu * R[:, None]),
+                     -T / (8.0 * math.pi * mu * R[:, None] ** 2)])
+    return rows, bal
+
+
+def rigid_rhs(susp, u_inf, ext=None, mu=1.0):
+    """Right side of the rigid-particle system: u_inf at the nodes, and the
+    external force and torque ext [P, 6] (None: force- and torque-free) in
+    the balance rows' units, so that the solution has
+    sum_b A_b f_b = -F_ext and sum_b A_b (x_b - c) x f_b = -T_ext."""
+    n_p = int(susp.particle.max()) + 1
+    _, R = rigid_scales(susp, mu)
+    bal = np.zeros((n_p, 6))
+    if ext is not None:
+        e = _f64(ext).reshape(n_p, 6)
+        bal[:, :3] = e[:, :3] / (6.0 * math.pi * mu * R[:, None])
+        bal[:, 3:] = e[:, 3:] / (8.0 * math.pi * mu * R[:, None] ** 2)
+    return _f64(u_inf).reshape(-1, 3), bal
+
+
+def rigid_solve(susp, centres, u_inf, ext=None, tol=1e-6, restart=30, maxit=300,
+                quadrature="element", mu=1.0, alpha=None, rcut=None, x0=None):
+    """Tractions and rigid-body velocities of force- and torque-free (or
+    externally loaded) rigid particles in the undisturbed flow u_inf
+    (Sec. 6.1), by restarted GMRES on the unknowns (f [N, 3], U, Omega [P, 6]).
+    Returns (f, UO, iterations, true relative residual, converged)."""
+    n = susp.x.shape[0]
+    n_p = int(susp.particle.max()) + 1
+    rows_b, bal_b = rigid_rhs(susp, u_inf, ext, mu)
+    b = np.concatenate([rows_b.ravel(), bal_b.ravel()])
+
+    def apply(z):
+        rows, bal = rigid_operator(susp, centres, z[:3 * n].reshape(n, 3),
+                                   z[3 * n:].reshape(n_p, 6), quadrature, mu, alpha, rcut)
+        return np.concatenate([rows.ravel(), bal.ravel()])
+
+    z, its, rr, ok = gmres(apply, b, x0, tol, restart, maxit)
+    return z[:3 * n].reshape(n, 3), z[3 * n:].reshape(n_p, 6), its, rr, ok
