@@ -203,10 +203,45 @@ ggem_status bie_solve(ggem_plan_t *plan, const double *kappa, const double *b, d
 ggem_status ggem_solve_guess(const ggem_plan_t *plan, int *used_mlp, double *relres_plain,
                              double *relres_mlp);
 
-/* Work counts of the last bie_solve on this plan: GMRES cycles, operator
- * applications in FP64 and with the mixed operator. */
+/* Work counts of the last bie_solve or ggem_rigid_solve on this plan: GMRES
+ * cycles, operator applications in FP64 and with the mixed operator. */
 ggem_status ggem_solve_stats(const ggem_plan_t *plan, int *cycles, int *matvec_fp64,
                              int *matvec_mixed);
+
+/*
+ * Rigid particles in the slit (Sec. 6.1, Eq. (sl_r)): the surface tractions f
+ * and the translational and angular velocities U_p, Omega_p of rigid
+ * particles that move freely in an undisturbed flow u_inf, or under an
+ * external force and torque.  At every node b of particle p
+ *   U_p + Omega_p x (x_b - c_p) + 1/(8 pi mu) int_S f_i G_ji(x_b, x) dS = u_inf(x_b),
+ * the integral being ggem_single_layer of f, and for every particle
+ *   sum_{b in p} A_b f_b = -F_p,   sum_{b in p} A_b (x_b - c_p) x f_b = -T_p,
+ * A_b the nodal areas (f is the traction the fluid exerts on the particle).
+ * The balance rows enter the system scaled by 1/(6 pi mu R_p) and
+ * 1/(8 pi mu R_p^2), R_p = sqrt(S_p / (4 pi)), S_p = sum A_b over the particle,
+ * so that every residual entry is a velocity.
+ *   n_particles  must equal the count given to ggem_mesh_particles, whose ids
+ *                (set for the current mesh) assign the nodes to particles
+ *   centres      [n_particles][3] reference points c_p (e.g. the centres)
+ *   u_inf        [n_nodes][3] undisturbed velocity at the nodes, or NULL (0)
+ *   ext          [n_particles][6] external force F_p and torque T_p about c_p,
+ *                or NULL (force- and torque-free)
+ *   f            [n_nodes][3]; in: initial guess (zeros if unknown), out: f
+ *   uo           [n_particles][6]; in: guess, out: U_p (3), Omega_p (3)
+ *   tol, restart, maxit, iters, true_relres  as for bie_solve; the residual
+ *                is that of the whole system [rows | balance rows]
+ * The tractions of a closed surface are fixed only up to a multiple of the
+ * normal (a uniform pressure exerts no force and moves no fluid), so the
+ * velocities are the well-determined output.  Method, precision handling
+ * and workspace as for bie_solve (the first call also builds the node lists
+ * of the particles, once per ggem_mesh_particles).  Arrays may be device or
+ * host memory.  Returns GGEM_OK, GGEM_OK_BREAKDOWN, GGEM_ERR_NOT_CONVERGED
+ * (f and uo hold the last iterate), GGEM_ERR_NUMERICAL or an argument error.
+ */
+ggem_status ggem_rigid_solve(ggem_plan_t *plan, int n_particles, const double *centres,
+                             const double *u_inf, const double *ext, double *f, double *uo,
+                             double tol, int restart, int maxit, int *iters,
+                             double *true_relres);
 
 /*
  * Allocation-free local velocity sum (no counterpart in the paper).

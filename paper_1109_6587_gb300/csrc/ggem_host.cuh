@@ -127,8 +127,10 @@ void stage(ggem_plan_t* P, int id, int nk, F&& f) {
     }
 }
 
-// v = D q at the mesh nodes with the plan's precision and quadrature (device
-// arrays [n_nodes][3]); defined with the layer pipeline
+// w = S q (single layer) and v = D q (double layer) at the mesh nodes with the
+// plan's precision and quadrature (device arrays [n_nodes][3]); defined with
+// the layer pipeline
+void single_layer_dev(ggem_plan_t* P, const double* q, double* w);
 void double_layer_dev(ggem_plan_t* P, const double* q, double* v);
 
 // out = base + A^-1 r estimated by the learned warm start (device arrays;

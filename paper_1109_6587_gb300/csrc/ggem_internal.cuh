@@ -152,7 +152,8 @@ struct ggem_plan {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // Fredholm solve workspace (allocated by the first solve)
     int sol_m = 0;                     // restart length d_V holds
-    double* d_V = nullptr;             // [sol_m + 1][ld] Krylov basis, ld >= 3 cap
+    size_t sol_ld = 0;                 // stride of the solver vectors (>= 3 cap)
+    double* d_V = nullptr;             // [sol_m + 1][sol_ld] Krylov basis
     double* d_sv = nullptr;            // [ld] double-layer output
     double* d_sb = nullptr;            // [ld] staged right-hand side
     double* d_sk = nullptr;            // [cap] staged kappa
@@ -167,6 +168,14 @@ struct ggem_plan {
     int* d_particle = nullptr;         // [cap] particle id of each node (caller order)
     int* d_pcount = nullptr;           // [pcount_cap + 1] nodes per particle, error flag
     int pcount_cap = 0, n_particles = 0;
+    // rigid-particle solve (allocated by its first use)
+    bool pcsr_ready = false;           // d_pstart / d_pnodes match d_particle
+    int particles_n = 0;               // n_nodes when the particle ids were set
+    int* d_pstart = nullptr;           // [pcount_cap + 1] CSR of the nodes of each particle
+    int* d_pnodes = nullptr;           // [cap] node indices grouped by particle, ascending
+    double* d_rc = nullptr;            // [pcount_cap][3] reference points c_p
+    double* d_rscale = nullptr;        // [pcount_cap][2] 1/(6 pi mu R_p), 1/(8 pi mu R_p^2)
+    int rig_cap = 0;                   // particles d_pstart / d_rc / d_rscale hold
     float* d_feat = nullptr;           // [cap][12] features
     float* d_mlp = nullptr;            // [35075] FP32 master parameters
     float* d_mlp_grad = nullptr;       // gradient accumulator

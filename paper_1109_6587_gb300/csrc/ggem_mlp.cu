@@ -508,6 +508,8 @@ ggem_status ggem_mesh_particles(ggem_plan_t* P, int n_particles, const int* part
         GG_CUDA(cudaStreamSynchronize(P->st));
         GG_CHECK(hbad == 0, GGEM_ERR_INVALID_ARG, "particle ids must lie in [0, n_particles)");
         P->n_particles = n_particles;
+        P->particles_n = n;
+        P->pcsr_ready = false;
     });
 }
 

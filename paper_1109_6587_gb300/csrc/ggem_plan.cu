@@ -309,6 +309,11 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
 
 }  // namespace
 
+void ggem::single_layer_dev(ggem_plan_t* P, const double* q, double* w) {
+    if (P->fp64) layer_impl<double>(P, 0, q, w);
+    else layer_impl<float>(P, 0, q, w);
+}
+
 void ggem::double_layer_dev(ggem_plan_t* P, const double* q, double* v) {
     if (P->fp64) layer_impl<double>(P, 1, q, v);
     else layer_impl<float>(P, 1, q, v);
@@ -592,7 +597,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_mlp, P->d_mlp_grad, P->d_mlp_m, P->d_mlp_v, P->d_mlp_wf,
                     P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
                     P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err,
-                    P->d_tc_fwd, P->d_tc_inv, P->d_spread_list};
+                    P->d_tc_fwd, P->d_tc_inv, P->d_spread_list, P->d_pstart,
+                    P->d_pnodes, P->d_rc, P->d_rscale};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);

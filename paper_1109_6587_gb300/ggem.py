@@ -48,7 +48,7 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats", "ggem_solve_guess",
            "ggem_mesh_particles", "ggem_mlp_features", "ggem_mlp_load", "ggem_mlp_save",
            "ggem_mlp_forward", "ggem_mlp_train", "ggem_mlp_guess", "ggem_bie_operator",
-           "ggem_check"]
+           "ggem_check", "ggem_rigid_solve"]
 
 MLP_MODEL_SIZE = 25 + 35075
 
@@ -83,6 +83,8 @@ def lib():
         L.ggem_mlp_guess.argtypes = [P, P, P, P]
         L.ggem_bie_operator.argtypes = [P, P, P, P]
         L.ggem_check.argtypes = [P]
+        L.ggem_rigid_solve.argtypes = [P, I, P, P, P, P, P, D, I, I, ctypes.POINTER(I),
+                                       ctypes.POINTER(D)]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -267,6 +269,38 @@ class Plan:
             q[...] = kq
         return q, its.value, rr.value, st
 
+    def rigid_solve(self, centres, u_inf=None, ext=None, f=None, uo=None, tol=1e-6,
+                    restart=30, maxit=300, check=True):
+        """Tractions and rigid-body velocities of the particles set by
+        mesh_particles (Sec. 6.1): centres [P, 3] reference points, u_inf
+        [N, 3] undisturbed velocity at the nodes (None: 0), ext [P, 6] external
+        force and torque (None: force- and torque-free).  f [N, 3] and uo
+        [P, 6] (U, Omega) are the initial guess (zero when None) and are
+        updated in place when given.  Returns (f, uo, iterations, true relative
+        residual, status); with check, an error status other than
+        GGEM_ERR_NOT_CONVERGED raises."""
+        n_p = int(np.asarray(centres.cpu() if hasattr(centres, "cpu") else centres).reshape(-1, 3).shape[0])
+        ref = u_inf if u_inf is not None else centres
+        if f is None:
+            f = _zeros_like_target(ref, (self.n_nodes, 3))
+        if uo is None:
+            uo = _zeros_like_target(ref, (n_p, 6))
+        pc, kc = _ptr(centres, np.float64)
+        pu, ku = _ptr(u_inf, np.float64)
+        pe, ke = _ptr(ext, np.float64)
+        pf, kf = _ptr(f, np.float64)
+        po, ko = _ptr(uo, np.float64)
+        its = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = lib().ggem_rigid_solve(self.h, n_p, pc, pu, pe, pf, po, tol, restart, maxit,
+                                    ctypes.byref(its), ctypes.byref(rr))
+        if check and st not in (0, 5, 6):
+            _check(st, self.h)
+        for out, keep in ((f, kf), (uo, ko)):
+            if keep is not out and not hasattr(out, "data_ptr"):
+                out[...] = keep
+        return f, uo, its.value, rr.value, st
+
     def check(self):
         """Raise if a device-side wait of the plan's kernels expired."""
         _check(lib().ggem_check(self.h), self.h)
@@ -350,7 +384,7 @@ class Plan:
 
     def solve_stats(self):
         """(GMRES cycles, FP64 operator applications, mixed operator applications)
-        of the last bie_solve."""
+        of the last bie_solve or rigid_solve."""
         c, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().ggem_solve_stats(self.h, ctypes.byref(c), ctypes.byref(a),
                                       ctypes.byref(b)), self.h)
@@ -372,6 +406,11 @@ def ggem_double_layer(plan, q, out=None):
 
 def bie_solve(plan, kappa, b, q=None, tol=1e-6, restart=30, maxit=300, use_mlp=False):
     return plan.bie_solve(kappa, b, q, tol, restart, maxit, use_mlp)
+
+
+def ggem_rigid_solve(plan, centres, u_inf=None, ext=None, f=None, uo=None, tol=1e-6,
+                     restart=30, maxit=300):
+    return plan.rigid_solve(centres, u_inf, ext, f, uo, tol, restart, maxit)
 
 
 def ggem_point_forces(plan, xs, g, xt=None, want_u=True, want_sigma=False):
