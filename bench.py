@@ -282,7 +282,7 @@ def roofline(res, args):
         # element-rule kernel on this workload, from one ncu capture of that
         # launch (its ncu summary is kept with the profiles); other
         # configurations have no capture
-        traffic = (114.4e6 + 4.5e6) if (args.precision == "mixed"
+        traffic = (114.9e6 + 4.4e6) if (args.precision == "mixed"
                                         and args.quadrature == "element") else None
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,

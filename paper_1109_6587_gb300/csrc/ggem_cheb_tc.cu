@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TCT)
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 s_fail = 1;
-                atomicAdd(err, 1);
+                atomicOr(err, 1);
             }
             break;
         }

@@ -281,6 +281,62 @@ __device__ __forceinline__ void pair_terms(const LocalConst<T>& k, T dx, T dy, T
     }
 }
 
+// Two candidate pairs at once, FP32 (element rule): the arithmetic of
+// pair_terms on paired lanes (add/mul/fma .f32x2), so one issued instruction
+// serves two pairs; rsqrt and exp2 stay scalar.  Every multiply-add is an
+// explicit FMA.
+struct PairAcc2 {
+    f2 ux = {0ull}, uy = {0ull}, uz = {0ull};
+};
+
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f2 dy, f2 dz,
+                                            f2 r2, f2 gx, f2 gy, f2 gz, f2 nx, f2 ny, f2 nz,
+                                            PairAcc2& a) {
+    float lo, hi;
+    f2_split(r2, lo, hi);
+    const f2 ir = f2_make(rsqrt_ftz(lo), rsqrt_ftz(hi));
+    const f2 r = r2 * ir;
+    f2_split(f2_splat(k.ke) * r2, lo, hi);
+    const f2 ex = f2_make(ex2_ftz(lo), ex2_ftz(hi));                 // exp(-alpha^2 r^2)
+    const f2 u = fma2(r, f2_splat(0.5f * k.al), f2_splat(-1.0f));  // alpha r / 2 - 1
+    const f2 ec = ex * erfcx_poly2(u);                               // erfc(alpha r)
+    const f2 xg = fma2(dz, gz, fma2(dy, gy, dx * gx));
+    if (MODE & OUT_U) {
+        // A = ec/r - c1 ex,  B = (ec/r^3 + c1 ex/r^2) xg
+        const f2 eir = ec * ir;
+        const f2 A = fma2(f2_splat(-k.c1), ex, eir);
+        const f2 B = (ir * ir) * fma2(f2_splat(k.c1), ex, eir) * xg;
+        a.ux = fma2(B, dx, fma2(A, gx, a.ux));
+        a.uy = fma2(B, dy, fma2(A, gy, a.uy));
+        a.uz = fma2(B, dz, fma2(A, gz, a.uz));
+    }
+    if (MODE & OUT_DBL) {
+        // D = -6 ec/r^5 - c2 ex/r^4 - c3 ex/r^2,  E = c4 ex
+        const f2 ir2 = ir * ir;
+        const f2 t = fma2(f2_splat(-6.0f), ec * ir, f2_splat(-k.c2) * ex);
+        const f2 D = fma2(ir2 * ir2, t, f2_splat(-k.c3) * ex * ir2);
+        const f2 E = f2_splat(k.c4) * ex;
+        const f2 xn = fma2(dz, nz, fma2(dy, ny, dx * nx));
+        const f2 gn = fma2(gz, nz, fma2(gy, ny, gx * nx));
+        const f2 Dxn = D * xg * xn;
+        a.ux = fma2(Dxn, dx, fma2(E, fma2(dx, gn, fma2(gx, xn, nx * xg)), a.ux));
+        a.uy = fma2(Dxn, dy, fma2(E, fma2(dy, gn, fma2(gy, xn, ny * xg)), a.uy));
+        a.uz = fma2(Dxn, dz, fma2(E, fma2(dz, gn, fma2(gz, xn, nz * xg)), a.uz));
+    }
+}
+
 // scaled output of one target in caller order
 template <typename T, int MODE>
 __device__ __forceinline__ void store_target(const LocalConst<T>& k, const PairAcc<T>& a, T* o) {
@@ -295,63 +351,42 @@ __device__ __forceinline__ void store_target(const LocalConst<T>& k, const PairA
     }
 }
 
-// u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
-// (unscaled in the loop; the caller-facing factors are applied at the end).
-//
-// One warp per target.  The warp lists the neighbour cells (offsets -R..R)
-// that come within r_cut of the target, then walks them one at a time with
-// consecutive lanes on consecutive sorted sources (coalesced float4 loads).
-// The hits are compacted into a per-warp queue and evaluated 32 at a time.
-// Partial sums are reduced with warp shuffles.
-constexpr int LW = 8;       // warps (targets) per block
-constexpr int kQueue = 64;  // hit queue per warp: < 32 left + <= 32 new always fit
-constexpr int kNb = 7 * 7 * 7;   // neighbour cell offsets for the largest reach (3)
-
-// ELEM: sources are element quadrature points and targets are mesh nodes
-// (caller index t); points of triangles having the target as a vertex are
-// skipped (their integral is done by the polar rule, Sec. 3.4.1).
-template <typename T, int KIND, int MODE, bool ELEM, int REACH>
-__global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
-    __shared__ int s_cst[LW][kNb];            // this target's cells: first source,
-    __shared__ int s_cnt[LW][kNb];            //   source count,
-    __shared__ unsigned short s_off[LW][kNb]; //   neighbour offset index
-    __shared__ v4_t<T> s_qd[LW][kQueue];     // queued hits: displacement, r^2
-    __shared__ int s_qs[LW][kQueue];         // queued hits: sorted source index
-    __shared__ double s_tab[sizeof(T) == 8 ? (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT : 1];
-    if (sizeof(T) == 8) {
-        for (int e = threadIdx.x; e < (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT; e += blockDim.x)
-            s_tab[e] = kErfcxTab64[e];
-        __syncthreads();
-    }
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * LW + wid;
-    if (t >= a.n_tgt) return;                     // warp-uniform
+// Target t: position in its cell's frame, cell coordinates and caller index.
+template <typename T, int KIND>
+__device__ __forceinline__ void load_target(const LocalArgs<T>& a, int t, T& ox, T& oy, T& oz,
+                                            int& cx, int& cy, int& cz, int& oidx) {
     const CellGrid& cg = a.cg;
-    int cx, cy, cz, oidx = t;
-    T ox, oy, oz;
-    {
-        v4_t<T> p;
-        int c;
-        if (KIND == TK_SORTED) {
-            p = a.src.pos[t];
-            c = a.src.cell[t];
-            oidx = a.src.perm[t];
-        } else {
-            p = a.tpos[t];
-            c = a.tcell[t];
-            if (a.tperm) oidx = a.tperm[t];
-        }
-        ox = p.x; oy = p.y; oz = p.z;
-        cx = c % cg.ncx;
-        cy = (c / cg.ncx) % cg.ncy;
-        cz = c / (cg.ncx * cg.ncy);
+    v4_t<T> p;
+    int c;
+    oidx = t;
+    if (KIND == TK_SORTED) {
+        p = a.src.pos[t];
+        c = a.src.cell[t];
+        oidx = a.src.perm[t];
+    } else {
+        p = a.tpos[t];
+        c = a.tcell[t];
+        if (a.tperm) oidx = a.tperm[t];
     }
-    // Neighbour cells at offsets -R..R (cells are at least r_cut/R wide, R =
-    // REACH = cg.reach); keep the non-empty ones whose nearest point lies within r_cut
-    // of the target (a slightly widened r_cut, so rounding can only keep more).
+    ox = p.x; oy = p.y; oz = p.z;
+    cx = c % cg.ncx;
+    cy = (c / cg.ncx) % cg.ncy;
+    cz = c / (cg.ncx * cg.ncy);
+}
+
+// The warp's list of neighbour cells at offsets -R..R (cells are at least
+// r_cut/R wide): the non-empty ones whose nearest point lies within r_cut of
+// the target (a slightly widened r_cut, so rounding can only keep more).
+// Writes first source, count and offset index of each into the warp's
+// shared-memory lists; returns their number (warp-uniform).
+template <typename T, int R>
+__device__ __forceinline__ int cull_cells(const LocalArgs<T>& a, int lane, T ox, T oy, T oz,
+                                          int cx, int cy, int cz, int* s_cst, int* s_cnt,
+                                          unsigned short* s_off) {
+    const CellGrid& cg = a.cg;
     const unsigned lt = (1u << lane) - 1u;
     const T reach2 = a.k.rc2 * (T)1.0001;
-    constexpr int R = REACH, side = 2 * R + 1, nb = side * side * side;
+    constexpr int side = 2 * R + 1, nb = side * side * side;
     int nc = 0;
     for (int r = 0; r < (nb + 31) / 32; ++r) {
         const int oi = r * 32 + lane;
@@ -381,14 +416,55 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             const int slot = nc + __popc(m & lt);
-            s_cst[wid][slot] = st;
-            s_cnt[wid][slot] = cnt;
-            s_off[wid][slot] = oi;
+            s_cst[slot] = st;
+            s_cnt[slot] = cnt;
+            s_off[slot] = (unsigned short)oi;
         }
         nc += __popc(m);
     }
     __syncwarp();
+    return nc;
+}
 
+// u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
+// (unscaled in the loop; the caller-facing factors are applied at the end).
+//
+// One warp per target.  The warp lists the neighbour cells (offsets -R..R)
+// that come within r_cut of the target, then walks them one at a time with
+// consecutive lanes on consecutive sorted sources (coalesced float4 loads).
+// The hits are compacted into a per-warp queue and evaluated 32 at a time.
+// Partial sums are reduced with warp shuffles.
+constexpr int LW = 8;       // warps (targets) per block
+constexpr int kQueue = 64;  // hit queue per warp: < 32 left + <= 32 new always fit
+constexpr int kNb = 7 * 7 * 7;   // neighbour cell offsets for the largest reach (3)
+
+// ELEM: sources are element quadrature points and targets are mesh nodes
+// (caller index t); points of triangles having the target as a vertex are
+// skipped (their integral is done by the polar rule, Sec. 3.4.1).  Used in
+// FP64; the FP32 element rule runs in k_local_elem32 below.
+template <typename T, int KIND, int MODE, bool ELEM, int REACH>
+__global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
+    __shared__ int s_cst[LW][kNb];            // this target's cells: first source,
+    __shared__ int s_cnt[LW][kNb];            //   source count,
+    __shared__ unsigned short s_off[LW][kNb]; //   neighbour offset index
+    __shared__ v4_t<T> s_qd[LW][kQueue];     // queued hits: displacement, r^2
+    __shared__ int s_qs[LW][kQueue];         // queued hits: sorted source index
+    __shared__ double s_tab[sizeof(T) == 8 ? (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT : 1];
+    if (sizeof(T) == 8) {
+        for (int e = threadIdx.x; e < (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT; e += blockDim.x)
+            s_tab[e] = kErfcxTab64[e];
+        __syncthreads();
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * LW + wid;
+    if (t >= a.n_tgt) return;                     // warp-uniform
+    int cx, cy, cz, oidx;
+    T ox, oy, oz;
+    load_target<T, KIND>(a, t, ox, oy, oz, cx, cy, cz, oidx);
+    constexpr int R = REACH, side = 2 * R + 1;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nc = cull_cells<T, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid], s_cnt[wid],
+                                    s_off[wid]);
     T nx = 0, ny = 0, nz = 0;
     if (MODE & OUT_DBL) {
         nx = (T)a.nrm[3 * oidx]; ny = (T)a.nrm[3 * oidx + 1]; nz = (T)a.nrm[3 * oidx + 2];
@@ -407,41 +483,6 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
         const T tz = oz - (T)(oi / (side * side) - R) * a.k.hz;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
-            if (ELEM && sizeof(T) == 4) {
-                // Element rule in FP32: about 70 % of the candidates are inside
-                // r_cut and cells hold ~1,500 points, so every lane evaluates its
-                // candidate and a miss contributes nothing (its strength is
-                // zeroed; every term carries a factor g, and the arithmetic stays
-                // finite for r < 2 r_cut).  Quadrature points never sit on a node
-                // (r > 0).  In FP64 the pair arithmetic is the scarce resource and
-                // the hit queue below is kept.
-                bool hit = false;
-                T dx = 0, dy = 0, dz = 0, r2 = 0;
-                int s = st;
-                if (i < cnt) {
-                    s = st + i;
-                    const v4_t<T> p = a.src.pos[s];
-                    dx = tx - p.x;
-                    dy = ty - p.y;
-                    dz = tz - p.z;
-                    r2 = dx * dx + dy * dy + dz * dz;
-                    hit = r2 < rc2;
-                    if (hit && r2 < a.near2) {
-                        const int4 v = a.qvs[s];
-                        hit = !(v.x == oidx || v.y == oidx || v.z == oidx);
-                    }
-                }
-                if (!__any_sync(0xffffffffu, hit)) continue;
-                if (i < cnt) {
-                    v4_t<T> g = a.src.g[s];
-                    if (!hit) {
-                        g.x = 0; g.y = 0; g.z = 0;
-                        r2 = rc2;               // any in-range value: the terms vanish
-                    }
-                    pair_terms<T, MODE>(a.k, dx, dy, dz, r2, g, nx, ny, nz, acc, s_tab);
-                }
-                continue;
-            }
             bool hit = false;
             T dx = 0, dy = 0, dz = 0, r2 = 0;
             int s = 0;
@@ -517,6 +558,92 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
     store_target<T, MODE>(a.k, acc, a.out + (size_t)oidx * a.out_stride);
 }
 
+// ------------------------------------------------- FP32 element rule
+// The element-rule local sum in FP32 reads ~1,500 quadrature points per cell
+// and evaluates about 70 % of them, so no hit queue: every lane takes two
+// candidates of each 64-point step through a cell and evaluates both with
+// paired FP32 arithmetic; a miss contributes nothing (its strength is zero,
+// and every term carries a factor g).  Strengths are loaded for hits only.
+constexpr int LWE = 8;        // warps (targets) per block
+constexpr int kChunk = 64;    // candidates per warp step
+
+template <int MODE, int REACH>
+__global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a) {
+    __shared__ int s_cst[LWE][kNb];
+    __shared__ int s_cnt[LWE][kNb];
+    __shared__ unsigned short s_off[LWE][kNb];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * LWE + wid;
+    if (t >= a.n_tgt) return;                     // warp-uniform
+    int cx, cy, cz, oidx;
+    float ox, oy, oz;
+    load_target<float, TK_POINTS>(a, t, ox, oy, oz, cx, cy, cz, oidx);
+    constexpr int R = REACH, side = 2 * R + 1;
+    const int nc = cull_cells<float, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid],
+                                        s_cnt[wid], s_off[wid]);
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (MODE & OUT_DBL) {
+        nx = (float)a.nrm[3 * oidx]; ny = (float)a.nrm[3 * oidx + 1]; nz = (float)a.nrm[3 * oidx + 2];
+    }
+    const float rc2 = a.k.rc2;
+    PairAcc2 acc;
+    for (int ci = 0; ci < nc; ++ci) {
+        const int st = s_cst[wid][ci], cnt = s_cnt[wid][ci], oi = s_off[wid][ci];
+        // target position in the frame of this source cell's corner
+        const float tx = ox - (float)(oi % side - R) * a.k.hx;
+        const float ty = oy - (float)((oi / side) % side - R) * a.k.hy;
+        const float tz = oz - (float)(oi / (side * side) - R) * a.k.hz;
+        for (int i0 = 0; i0 < cnt; i0 += kChunk) {
+            float d[2][4];
+            int sv[2];
+            bool h[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int i = i0 + 32 * j + lane;
+                h[j] = false;
+                sv[j] = st;
+                d[j][0] = d[j][1] = d[j][2] = 0.f;
+                d[j][3] = rc2;
+                if (i < cnt) {
+                    sv[j] = st + i;
+                    const float4 p = a.src.pos[sv[j]];
+                    d[j][0] = tx - p.x;
+                    d[j][1] = ty - p.y;
+                    d[j][2] = tz - p.z;
+                    const float q2 = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
+                    h[j] = q2 < rc2;
+                    if (h[j] && q2 < a.near2) {
+                        const int4 v = a.qvs[sv[j]];
+                        h[j] = !(v.x == oidx || v.y == oidx || v.z == oidx);
+                    }
+                    if (h[j]) d[j][3] = q2;      // misses keep an in-range r^2
+                }
+            }
+            if (!__any_sync(0xffffffffu, h[0] || h[1])) continue;
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+            if (h[0]) g0 = a.src.g[sv[0]];
+            if (h[1]) g1 = a.src.g[sv[1]];
+            pair_terms2<MODE>(a.k, f2_make(d[0][0], d[1][0]), f2_make(d[0][1], d[1][1]),
+                              f2_make(d[0][2], d[1][2]), f2_make(d[0][3], d[1][3]),
+                              f2_make(g0.x, g1.x), f2_make(g0.y, g1.y), f2_make(g0.z, g1.z),
+                              f2_splat(nx), f2_splat(ny), f2_splat(nz), acc);
+        }
+    }
+    float ux = f2_sum(acc.ux), uy = f2_sum(acc.uy), uz = f2_sum(acc.uz);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ux += __shfl_xor_sync(0xffffffffu, ux, o);
+        uy += __shfl_xor_sync(0xffffffffu, uy, o);
+        uz += __shfl_xor_sync(0xffffffffu, uz, o);
+    }
+    if (lane == 0) {
+        float* o = a.out + (size_t)oidx * a.out_stride;
+        o[0] = a.k.fU * ux;
+        o[1] = a.k.fU * uy;
+        o[2] = a.k.fU * uz;
+    }
+}
+
 template <typename T, int KIND, int REACH>
 static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     dim3 b(LW * 32), g((a.n_tgt + LW - 1) / LW);
@@ -549,6 +676,17 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
     // scan the same candidate cells (L1 reuse); output in caller order
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
                    tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
+    if constexpr (sizeof(T) == 4) {
+        dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
+        if (cg.reach == 3) {
+            if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a);
+            else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a);
+        } else {
+            if (layer == 0) k_local_elem32<OUT_U, 2><<<g, b, 0, st>>>(a);
+            else k_local_elem32<OUT_DBL, 2><<<g, b, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     dim3 b(LW * 32), g((tgt.n + LW - 1) / LW);
     if (cg.reach == 3) {
         if (layer == 0) k_local<T, TK_POINTS, OUT_U, true, 3><<<g, b, 0, st>>>(a);

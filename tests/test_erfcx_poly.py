@@ -61,3 +61,11 @@ def test_polynomial_error_fp64():
     for j in range(11, -1, -1):
         p = p * u + tab[j, i]
     assert np.abs(p / ref - 1).max() < 3e-15
+
+
+def test_paired_polynomial_has_the_same_coefficients():
+    # the paired-lane copy used by the FP32 element-rule kernel
+    txt = HDR.read_text()
+    first = re.search(r"f2 p = f2_splat\(([-+0-9.eE]+)f\);", txt).group(1)
+    rest = re.findall(r"p = fma2\(p, u, f2_splat\(([-+0-9.eE]+)f\)\);", txt)
+    assert [float(first)] + [float(v) for v in rest] == _coefficients()
