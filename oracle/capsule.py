@@ -201,20 +201,23 @@ def midpoint_step(susp, x_ref, lam, shear_modulus, kind, strength, dt, q0=None, 
     return susp.x + dt * u2, q2, i1 + i2
 
 
-def min_separation(x):
+def min_separation(x, box=None):
     """Smallest distance between two distinct nodes (any particles), by brute
-    force."""
+    force; with a box, the minimum image in x and z (the periodic system)."""
     x = np.asarray(x, dtype=np.float64)
     best = np.inf
     for i in range(len(x) - 1):
-        d = np.linalg.norm(x[i + 1:] - x[i], axis=1).min()
-        best = min(best, d)
+        d = x[i + 1:] - x[i]
+        if box is not None:
+            d[:, 0] -= box.Lx * np.round(d[:, 0] / box.Lx)
+            d[:, 2] -= box.Lz * np.round(d[:, 2] / box.Lz)
+        best = min(best, np.linalg.norm(d, axis=1).min())
     return float(best)
 
 
-def time_step(x, ca, radius, gamma_dot):
+def time_step(x, ca, radius, gamma_dot, box=None):
     """dt with gamma_dot dt = 0.5 Ca h_min / a (Sec. 5)."""
-    return 0.5 * ca * min_separation(x) / (radius * gamma_dot)
+    return 0.5 * ca * min_separation(x, box) / (radius * gamma_dot)
 
 
 # ------------------------------------------------------ volume and overlaps
