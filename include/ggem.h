@@ -243,6 +243,90 @@ ggem_status ggem_rigid_solve(ggem_plan_t *plan, int n_particles, const double *c
                              double tol, int restart, int maxit, int *iters,
                              double *true_relres);
 
+/* ------------------------------------------------------------------------
+ * Capsule dynamics (Sec. 4, 5, App. B): elastic capsules (neo-Hookean
+ * membranes around a fluid of viscosity lambda mu) carried by an undisturbed
+ * flow.  Node velocities come from Eqs. (bi_ua) and (qa); positions advance by
+ * the midpoint rule.  All of it runs on the plan's mesh, which a step moves.
+ * ------------------------------------------------------------------------ */
+enum { GGEM_FLOW_NONE = 0, GGEM_FLOW_SHEAR = 1, GGEM_FLOW_POISEUILLE = 2 };
+
+/* Reference (stress-free) shape of the membranes: x_ref [n_nodes][3] with the
+ * current mesh's triangles (e.g. the initial mesh).  Stores each triangle's
+ * reference metric; required by the traction and the step, kept until a
+ * ggem_mesh_set brings new triangles. */
+ggem_status ggem_membrane_reference(ggem_plan_t *plan, const double *x_ref);
+
+/* Traction jump at the nodes (Sec. 4, Eqs. (cntr2), (eq_WNH)): every flat
+ * triangle stores A0 W, W = (G/2)(lambda_1^2 + lambda_2^2 + 1/(lambda_1
+ * lambda_2)^2 - 3) of its uniform deformation from the reference; the force
+ * on a node is the gradient of the stored energy (principle of virtual work)
+ * and df_b = grad_b E / A_b, A_b the node's area (a third of its triangles'
+ * current areas).  df [n_nodes][3]; G = shear_modulus. */
+ggem_status ggem_membrane_traction(ggem_plan_t *plan, double shear_modulus, double *df);
+
+/* Undisturbed flow at the nodes (App. B): flow GGEM_FLOW_SHEAR, u = s (y -
+ * y_mid) e_x with y_mid the slit's mid-plane and s the shear rate;
+ * GGEM_FLOW_POISEUILLE, u = 4 s eta (1 - eta) e_x, eta = (y - y0)/W, s the
+ * centre-line velocity, pressure -8 mu s x / W^2; GGEM_FLOW_NONE, u = 0.
+ * u_inf [n_nodes][3] and f_inf = sigma_inf . n [n_nodes][3] (either may be
+ * NULL; f_inf needs triangles for the normals). */
+ggem_status ggem_undisturbed(ggem_plan_t *plan, int flow, double strength, double *u_inf,
+                             double *f_inf);
+
+typedef struct {
+    int flow;              /* GGEM_FLOW_* */
+    double strength;       /* shear rate or centre-line velocity */
+    double shear_modulus;  /* G of the membranes */
+    double dt;             /* time step (ggem_capsule_step) */
+    double tol;            /* Fredholm solve of each stage: as bie_solve */
+    int restart;
+    int maxit;
+    int use_mlp;
+} ggem_step_params;
+
+/* Node velocities of the capsules at the current mesh: b = -(df/(lambda + 1)
+ * + kappa f_inf)/(4 pi mu), kappa = (lambda - 1)/(lambda + 1) (Eq. (qa)),
+ * (I + kappa/(4 pi) D) q = b by bie_solve, u = u_inf + int q G dS
+ * (Eq. (bi_ua)).  lambda [n_nodes] viscosity ratio of each node's capsule;
+ * q [n_nodes][3] in: initial guess, out: the density; u [n_nodes][3].
+ * iters, true_relres as for bie_solve.  Needs ggem_membrane_reference. */
+ggem_status ggem_capsule_velocity(ggem_plan_t *plan, const ggem_step_params *sp,
+                                  const double *lambda, double *q, double *u, int *iters,
+                                  double *true_relres);
+
+/* One midpoint step of dx/dt = u (Sec. 5): x_half = x + dt/2 u(x), x_new =
+ * x + dt u(x_half), u as ggem_capsule_velocity; the second stage's solve
+ * starts from the first stage's density.  Moves the plan's mesh to x_new
+ * (cell lists, geometry, quadrature points rebuilt as by ggem_mesh_set; a
+ * node leaving the slit is an error).  q [n_nodes][3] in: guess, out: the
+ * second stage's density (the next step's guess); x_out [n_nodes][3] or NULL;
+ * iters: GMRES steps of both stages; true_relres: the larger of the two. */
+ggem_status ggem_capsule_step(ggem_plan_t *plan, const ggem_step_params *sp,
+                              const double *lambda, double *q, double *x_out, int *iters,
+                              double *true_relres);
+
+/* The plan's current node positions [n_nodes][3]. */
+ggem_status ggem_mesh_positions(const ggem_plan_t *plan, double *x);
+
+/* Smallest distance between two nodes (any particles; minimum image in x,
+ * z), the h_min of the time step rule gamma_dot dt = 0.5 Ca h_min / a
+ * (Sec. 5).  Pairs are searched in neighbouring cells of the plan's cell
+ * grid; with none there the result is the smallest cell width. */
+ggem_status ggem_min_separation(ggem_plan_t *plan, double *h_min);
+
+/* Enclosed volume of every particle of ggem_mesh_particles (divergence
+ * theorem over its outward-oriented triangles), volumes [n_particles]. */
+ggem_status ggem_particle_volumes(ggem_plan_t *plan, double *volumes);
+
+/* Volume correction (Sec. 5): every particle whose volume differs from v0
+ * [n_particles] by more than threshold * |v0| moves its nodes along their
+ * normals by (v0 - V)/S, S its area; repeated at most max_passes times until
+ * all are within the threshold (one pass leaves a second-order residual).
+ * Moves the plan's mesh; passes (out, may be NULL): passes made. */
+ggem_status ggem_volume_correct(ggem_plan_t *plan, const double *v0, double threshold,
+                                int max_passes, int *passes);
+
 /*
  * Allocation-free local velocity sum (no counterpart in the paper).
  *

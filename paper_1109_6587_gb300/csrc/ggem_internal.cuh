@@ -176,6 +176,23 @@ struct ggem_plan {
     double* d_rc = nullptr;            // [pcount_cap][3] reference points c_p
     double* d_rscale = nullptr;        // [pcount_cap][2] 1/(6 pi mu R_p), 1/(8 pi mu R_p^2)
     int rig_cap = 0;                   // particles d_pstart / d_rc / d_rscale hold
+    // capsule dynamics (allocated by their first use)
+    double* d_mref = nullptr;          // [cap_tris][4] reference metric G11, G12, G22, area
+    bool mref_ready = false;
+    double* d_cx0 = nullptr;           // [3 cap] positions at the start of a step
+    double* d_cdf = nullptr;           // [3 cap] traction jump
+    double* d_cuinf = nullptr;         // [3 cap] undisturbed velocity
+    double* d_cfinf = nullptr;         // [3 cap] undisturbed traction
+    double* d_cb = nullptr;            // [3 cap] right side of the Fredholm equation
+    double* d_ckap = nullptr;          // [cap] kappa per node
+    double* d_clam = nullptr;          // [cap] staged viscosity ratios
+    double* d_cw = nullptr;            // [3 cap] single layer of q / stage velocity
+    double* d_cq = nullptr;            // [3 cap] density when the caller's q is a host array
+    unsigned long long* d_cmin = nullptr;  // reduction word (bits of a positive double)
+    int* d_tstart = nullptr;           // [pcount_cap + 1] CSR of the triangles of each particle
+    int* d_tlist = nullptr;            // [cap_tris] triangle indices grouped by particle
+    double* d_cvol = nullptr;          // [pcount_cap] particle volumes / areas scratch
+    bool tcsr_ready = false;
     float* d_feat = nullptr;           // [cap][12] features
     float* d_mlp = nullptr;            // [35075] FP32 master parameters
     float* d_mlp_grad = nullptr;       // gradient accumulator

@@ -510,6 +510,7 @@ ggem_status ggem_mesh_particles(ggem_plan_t* P, int n_particles, const int* part
         P->n_particles = n_particles;
         P->particles_n = n;
         P->pcsr_ready = false;
+        P->tcsr_ready = false;
     });
 }
 

@@ -598,7 +598,9 @@ void plan_free(ggem_plan_t* P) {
                     P->d_mlp_wt, P->d_mlp_stats, P->d_mlp_out, P->d_smlp,
                     P->d_sres, P->d_mlp_dr, P->d_mlp_ssq, P->d_tc_err,
                     P->d_tc_fwd, P->d_tc_inv, P->d_spread_list, P->d_pstart,
-                    P->d_pnodes, P->d_rc, P->d_rscale};
+                    P->d_pnodes, P->d_rc, P->d_rscale, P->d_mref, P->d_cx0, P->d_cdf,
+                    P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
+                    P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -660,10 +662,16 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
         auto kind = [](const void* p) {
             return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         };
-        GG_CUDA(cudaMemcpyAsync(P->d_x, x, (size_t)n_nodes * 3 * sizeof(double), kind(x), st));
-        if (n_tris > 0)
+        // (the plan's own arrays may be passed back: nothing to copy then)
+        if (x != P->d_x)
+            GG_CUDA(cudaMemcpyAsync(P->d_x, x, (size_t)n_nodes * 3 * sizeof(double), kind(x),
+                                    st));
+        if (n_tris > 0 && tri != P->d_tri) {
             GG_CUDA(cudaMemcpyAsync(P->d_tri, tri, (size_t)n_tris * 3 * sizeof(int), kind(tri),
                                     st));
+            P->mref_ready = false;     // new connectivity: the membrane reference and the
+            P->tcsr_ready = false;     // per-particle triangle lists no longer apply
+        }
         int* bad = P->d_cell_count;   // scratch int
         GG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
         k_check_inside<<<(n_nodes + 255) / 256, 256, 0, st>>>(n_nodes, P->d_x, P->geo.y0,

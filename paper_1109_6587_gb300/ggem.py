@@ -48,7 +48,19 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_local_velocity_noalloc", "bie_solve", "ggem_solve_stats", "ggem_solve_guess",
            "ggem_mesh_particles", "ggem_mlp_features", "ggem_mlp_load", "ggem_mlp_save",
            "ggem_mlp_forward", "ggem_mlp_train", "ggem_mlp_guess", "ggem_bie_operator",
-           "ggem_check", "ggem_rigid_solve"]
+           "ggem_check", "ggem_rigid_solve", "ggem_membrane_reference",
+           "ggem_membrane_traction", "ggem_undisturbed", "ggem_capsule_velocity",
+           "ggem_capsule_step", "ggem_mesh_positions", "ggem_min_separation",
+           "ggem_particle_volumes", "ggem_volume_correct"]
+
+GGEM_FLOW = {"none": 0, "shear": 1, "poiseuille": 2}
+
+
+class ggem_step_params(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int), ("strength", ctypes.c_double),
+                ("shear_modulus", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("use_mlp", ctypes.c_int)]
 
 MLP_MODEL_SIZE = 25 + 35075
 
@@ -85,6 +97,16 @@ def lib():
         L.ggem_check.argtypes = [P]
         L.ggem_rigid_solve.argtypes = [P, I, P, P, P, P, P, D, I, I, ctypes.POINTER(I),
                                        ctypes.POINTER(D)]
+        SP = ctypes.POINTER(ggem_step_params)
+        L.ggem_membrane_reference.argtypes = [P, P]
+        L.ggem_membrane_traction.argtypes = [P, D, P]
+        L.ggem_undisturbed.argtypes = [P, I, D, P, P]
+        L.ggem_capsule_velocity.argtypes = [P, SP, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.ggem_capsule_step.argtypes = [P, SP, P, P, P, ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.ggem_mesh_positions.argtypes = [P, P]
+        L.ggem_min_separation.argtypes = [P, ctypes.POINTER(D)]
+        L.ggem_particle_volumes.argtypes = [P, P]
+        L.ggem_volume_correct.argtypes = [P, P, D, I, ctypes.POINTER(I)]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -155,6 +177,7 @@ class Plan:
                                ctypes.byref(h)), None)
         self.h = h
         self.n_nodes = 0
+        self.n_particles = 0
 
     @classmethod
     def for_box(cls, box, **kw):
@@ -301,6 +324,102 @@ class Plan:
                 out[...] = keep
         return f, uo, its.value, rr.value, st
 
+    # ------------------------------------------------------- capsule dynamics
+    def membrane_reference(self, x_ref):
+        """Stress-free shape of the membranes (same triangles as the mesh)."""
+        px, kx = _ptr(x_ref, np.float64)
+        _check(lib().ggem_membrane_reference(self.h, px), self.h)
+
+    def membrane_traction(self, shear_modulus, out=None):
+        """Traction jump Delta f [n, 3] of the neo-Hookean membranes (Sec. 4)."""
+        if out is None:
+            out = np.zeros((self.n_nodes, 3))
+        po, ko = _ptr(out, np.float64)
+        _check(lib().ggem_membrane_traction(self.h, float(shear_modulus), po), self.h)
+        if ko is not out and not hasattr(out, "data_ptr"):
+            out[...] = ko
+        return out
+
+    def undisturbed(self, flow, strength):
+        """(u_inf, f_inf) [n, 3] at the nodes for flow 'none', 'shear' or
+        'poiseuille' (App. B)."""
+        u = np.zeros((self.n_nodes, 3))
+        f = np.zeros((self.n_nodes, 3))
+        _check(lib().ggem_undisturbed(self.h, GGEM_FLOW[flow], float(strength),
+                                      u.ctypes.data_as(ctypes.c_void_p),
+                                      f.ctypes.data_as(ctypes.c_void_p)), self.h)
+        return u, f
+
+    @staticmethod
+    def _step_params(flow, strength, shear_modulus, dt, tol, restart, maxit, use_mlp):
+        return ggem_step_params(GGEM_FLOW[flow], float(strength), float(shear_modulus),
+                                float(dt), float(tol), int(restart), int(maxit), int(use_mlp))
+
+    def capsule_velocity(self, lam, flow="none", strength=0.0, shear_modulus=1.0, q=None,
+                         tol=1e-6, restart=30, maxit=300, use_mlp=0):
+        """Node velocities of Eqs. (bi_ua), (qa) at the current mesh.  q (guess,
+        zero when None) is updated in place when given.  Returns (u, q,
+        iterations, true relative residual)."""
+        n = self.n_nodes
+        if q is None:
+            q = np.zeros((n, 3))
+        sp = self._step_params(flow, strength, shear_modulus, 0.0, tol, restart, maxit, use_mlp)
+        pl, kl = _ptr(lam, np.float64)
+        pq, kq = _ptr(q, np.float64)
+        u = _zeros_like_target(q, (n, 3))
+        pu, ku = _ptr(u, np.float64)
+        its, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().ggem_capsule_velocity(self.h, ctypes.byref(sp), pl, pq, pu,
+                                           ctypes.byref(its), ctypes.byref(rr)), self.h)
+        for out, keep in ((q, kq), (u, ku)):
+            if keep is not out and not hasattr(out, "data_ptr"):
+                out[...] = keep
+        return u, q, its.value, rr.value
+
+    def capsule_step(self, lam, dt, flow="none", strength=0.0, shear_modulus=1.0, q=None,
+                     tol=1e-6, restart=30, maxit=300, use_mlp=0):
+        """One midpoint step (Sec. 5); the plan's mesh moves.  Returns (x_new
+        [n, 3] numpy, q, iterations, larger true relative residual)."""
+        n = self.n_nodes
+        if q is None:
+            q = np.zeros((n, 3))
+        sp = self._step_params(flow, strength, shear_modulus, dt, tol, restart, maxit, use_mlp)
+        pl, kl = _ptr(lam, np.float64)
+        pq, kq = _ptr(q, np.float64)
+        x = np.zeros((n, 3))
+        its, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(lib().ggem_capsule_step(self.h, ctypes.byref(sp), pl, pq,
+                                       x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(its),
+                                       ctypes.byref(rr)), self.h)
+        if kq is not q and not hasattr(q, "data_ptr"):
+            q[...] = kq
+        return x, q, its.value, rr.value
+
+    def mesh_positions(self):
+        x = np.zeros((self.n_nodes, 3))
+        _check(lib().ggem_mesh_positions(self.h, x.ctypes.data_as(ctypes.c_void_p)), self.h)
+        return x
+
+    def min_separation(self):
+        h = ctypes.c_double(0.0)
+        _check(lib().ggem_min_separation(self.h, ctypes.byref(h)), self.h)
+        return h.value
+
+    def particle_volumes(self):
+        v = np.zeros(self.n_particles)
+        _check(lib().ggem_particle_volumes(self.h, v.ctypes.data_as(ctypes.c_void_p)), self.h)
+        return v
+
+    def volume_correct(self, v0, threshold=1e-4, max_passes=10):
+        """Volume correction (Sec. 5); the plan's mesh moves.  Returns the
+        passes made."""
+        v = np.ascontiguousarray(v0, dtype=np.float64)
+        k = ctypes.c_int(0)
+        _check(lib().ggem_volume_correct(self.h, v.ctypes.data_as(ctypes.c_void_p),
+                                         float(threshold), int(max_passes), ctypes.byref(k)),
+               self.h)
+        return k.value
+
     def check(self):
         """Raise if a device-side wait of the plan's kernels expired."""
         _check(lib().ggem_check(self.h), self.h)
@@ -320,6 +439,7 @@ class Plan:
         n_p = int(part.max()) + 1 if n_particles is None else int(n_particles)
         _check(lib().ggem_mesh_particles(self.h, n_p, part.ctypes.data_as(ctypes.c_void_p)),
                self.h)
+        self.n_particles = n_p
 
     def mlp_features(self, kappa, r):
         """(features [n, 12] numpy, s = rms(r)) of the right-hand side r."""
