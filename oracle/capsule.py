@@ -38,8 +38,10 @@ Readings (the paper is silent or leaves the detail to its references):
     residual on a faceted mesh);
   * overlap correction: the gap of two particles is their smallest node to
     node distance (minimum image); pairs closer than the minimum gap move
-    apart rigidly along their line of centres by half the deficit each,
-    repeated until no pair violates it.  Node distances see near contacts,
+    apart rigidly along their line of centres (node centroids) by half the
+    deficit each, all pairs of a sweep at once from the positions at its
+    start (a particle in several pairs moves by the sum), sweeps repeated
+    until no pair violates it.  Node distances see near contacts,
     not deep overlaps (nodes of interpenetrating meshes can stay a node
     spacing apart); the correction exists to keep gaps from closing.
 """
@@ -255,33 +257,53 @@ def volume_correct(x, tri, particle, v0, threshold=1e-4, passes=10):
     return x, passes
 
 
-def overlap_correct(x, particle, n_particles, centres, box, h_min, max_sweeps=100):
-    """Move pairs of particles whose closest nodes are nearer than h_min apart
-    rigidly along their line of centres (minimum image in x, z), each by half
-    the deficit, until no pair violates the gap.  Returns (x, moves)."""
+def centroids(x, particle, n_particles):
+    """Mean node position of every particle (unwrapped meshes)."""
+    x = np.asarray(x, dtype=np.float64)
+    c = np.zeros((n_particles, 3))
+    cnt = np.zeros(n_particles)
+    np.add.at(c, np.asarray(particle), x)
+    np.add.at(cnt, np.asarray(particle), 1.0)
+    return c / cnt[:, None]
+
+
+def overlap_correct(x, particle, n_particles, box, h_min, max_sweeps=100):
+    """Minimum-gap correction (Sec. 7.1).  Each sweep finds every pair of
+    particles whose closest nodes (minimum image in x, z) are nearer than
+    h_min, from the positions at the start of the sweep, and moves both
+    rigidly along their line of centres (node centroids, minimum image) by
+    half the deficit each; a particle in several pairs moves by the sum.
+    Sweeps repeat until no pair violates the gap (gaps within 1e-9 h_min of
+    it count as met: a corrected pair lands on h_min up to rounding).
+    Returns (x, pair moves)."""
     x = np.array(x, dtype=np.float64)
     particle = np.asarray(particle)
-    c = np.array(centres, dtype=np.float64)
     moves = 0
+
+    def image(d):
+        d = d.copy()
+        d[..., 0] -= box.Lx * np.round(d[..., 0] / box.Lx)
+        d[..., 2] -= box.Lz * np.round(d[..., 2] / box.Lz)
+        return d
+
     for _ in range(max_sweeps):
-        changed = False
+        c = centroids(x, particle, n_particles)
+        disp = np.zeros((n_particles, 3))
+        found = 0
         for p in range(n_particles):
+            xp = x[particle == p]
             for q in range(p + 1, n_particles):
-                d = c[q] - c[p]
-                d[0] -= box.Lx * round(d[0] / box.Lx)
-                d[2] -= box.Lz * round(d[2] / box.Lz)
-                xp = x[particle == p]
-                xq = x[particle == q] - (c[q] - c[p] - d)   # q's image nearest p
-                gap = np.linalg.norm(xp[:, None, :] - xq[None, :, :], axis=2).min()
-                if gap < h_min:
+                xq = x[particle == q]
+                gap = np.linalg.norm(image(xp[:, None, :] - xq[None, :, :]), axis=2).min()
+                if gap < h_min * (1.0 - 1e-9):             # corrected gaps land on h_min
+                    d = image(c[q] - c[p])
                     e = d / np.linalg.norm(d)
                     s = 0.5 * (h_min - gap)
-                    x[particle == p] -= s * e
-                    x[particle == q] += s * e
-                    c[p] -= s * e
-                    c[q] += s * e
-                    moves += 1
-                    changed = True
-        if not changed:
+                    disp[p] -= s * e
+                    disp[q] += s * e
+                    found += 1
+        if not found:
             break
+        x += disp[particle]
+        moves += found
     return x, moves

@@ -32,7 +32,8 @@ Time stepping (Sec. 5):
 Volumes, volume correction and overlap correction: the volume of a mesh
 equals its convex hull's (scipy); the correction removes the volume error to
 second order; two capsules closer than the minimum gap end at least that far
-apart, displaced along their line of centres.
+apart, displaced along their line of centres; all violating pairs of a sweep
+move at once (a chain of three: the middle one stays).
 """
 import math
 
@@ -229,7 +230,7 @@ def test_overlap_correction():
     c1[0] -= box.Lx
     s = W.suspension(2, box, level=2, centres=np.array([c0, c1]))
     h = 0.05
-    x, moves = C.overlap_correct(s.x, s.particle, 2, s.centres, box, h)
+    x, moves = C.overlap_correct(s.x, s.particle, 2, box, h)
     assert moves >= 1
     d = s.centres[1] - s.centres[0]
     d[0] -= box.Lx * round(d[0] / box.Lx)
@@ -244,3 +245,23 @@ def test_overlap_correction():
         assert np.abs(disp - disp[0]).max() < 1e-12
         e = d / np.linalg.norm(d)
         assert np.linalg.norm(np.cross(disp[0], e)) < 1e-12 and sign * disp[0] @ e > 0
+
+
+def test_overlap_correction_sweeps_all_pairs_at_once():
+    # a chain of three spheres along an icosahedron vertex direction, each
+    # facing pair of vertices 0.03 apart: the middle one is pushed equally
+    # both ways in every sweep and stays, so each end closes half of its gap's
+    # deficit per sweep (0.03 -> 0.04 -> 0.045 ...) and ends 0.02 further out
+    box = W.Box(Lx=16.0, Lz=16.0, W=10.0, y0=-5.0, Nx=32, Ny=33, Nz=32)
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([phi, 0.0, 1.0]) / math.hypot(phi, 1.0)
+    c = np.array([8.0, 0.0, 8.0])
+    s = W.suspension(3, box, level=2, centres=np.array([c - 2.03 * v, c, c + 2.03 * v]))
+    x1, m1 = C.overlap_correct(s.x, s.particle, 3, box, 0.05, max_sweeps=1)
+    assert m1 == 2
+    assert np.allclose(x1[s.particle == 2][0] - s.x[s.particle == 2][0], 0.01 * v, atol=1e-15)
+    x, moves = C.overlap_correct(s.x, s.particle, 3, box, 0.05)
+    assert moves % 2 == 0 and moves > 4                     # two pairs per sweep
+    disp = [x[s.particle == p][0] - s.x[s.particle == p][0] for p in range(3)]
+    assert np.abs(disp[1]).max() < 1e-15
+    assert np.allclose(disp[0], -0.02 * v, atol=1e-10) and np.allclose(disp[2], 0.02 * v, atol=1e-10)
