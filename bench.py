@@ -415,6 +415,39 @@ def solve_metrics(args, susp, dev, train_steps=3, timed_steps=2):
     return out
 
 
+def dynamics_metrics(args, susp, dev, warm=1, timed=3):
+    """Capsule time steps of the workload (Sec. 5, 7.1): simple shear of rate
+    1, viscosity ratio 5, Ca = 0.3, membranes stress-free in the initial
+    spherical shape.  One step: the dt rule from the smallest node
+    separation, the midpoint step (per stage: traction jump, right side of
+    Eq. (qa), Fredholm solve to 1e-6 from the previous density, single
+    layer), the volume correction and the minimum-gap correction.  `warm`
+    untimed steps, then `timed` timed ones; mixed precision."""
+    import torch
+    from paper_1109_6587_gb300 import dynamics as D
+    from paper_1109_6587_gb300 import ggem
+
+    n = susp.x.shape[0]
+    P = ggem.Plan.for_box(susp.box, precision="mixed", quadrature=args.quadrature,
+                          max_points=n, max_tris=susp.tri.shape[0])
+    P.mesh_set(torch.as_tensor(susp.x, device=dev), torch.as_tensor(susp.tri, device=dev))
+    S = D.Suspension(P, susp.particle, len(susp.centres), lam=np.full(len(susp.centres), 5.0),
+                     ca=0.3, flow="shear", strength=1.0)
+    for _ in range(warm):
+        S.step()
+    recs = [S.step() for _ in range(timed)]
+    P.check()
+    out = {"flow": "simple shear, rate 1", "lambda": 5.0, "Ca": 0.3, "tol": 1e-6,
+           "steps_timed": timed, "s_per_step": float(np.mean([r["seconds"] for r in recs])),
+           "gmres_iters_per_step": float(np.mean([r["iters"] for r in recs])),
+           "dt": float(np.mean([r["dt"] for r in recs])),
+           "volume_passes": int(sum(r["volume_passes"] for r in recs)),
+           "overlap_moves": int(sum(r["overlap_moves"] for r in recs)),
+           "taylor_D_mean": float(S.deformation().mean()), "strain": S.t}
+    P.close()
+    return out
+
+
 def W_rigid(susp, t):
     from paper_1109_6587_gb300 import workloads as W
     return W.rigid_step(susp, seed=500, step=t) if t else susp
@@ -470,6 +503,7 @@ def main():
     if not args.no_solve:
         import torch
         line["solve"] = solve_metrics(args, res["susp"], torch.device("cuda"))
+        line["dynamics"] = dynamics_metrics(args, res["susp"], torch.device("cuda"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["susp"], args)
     if world > 1:

@@ -327,6 +327,17 @@ ggem_status ggem_particle_volumes(ggem_plan_t *plan, double *volumes);
 ggem_status ggem_volume_correct(ggem_plan_t *plan, const double *v0, double threshold,
                                 int max_passes, int *passes);
 
+/* Minimum-gap (overlap) correction (Sec. 7.1): every pair of particles whose
+ * closest nodes (minimum image in x, z) are nearer than h_min moves apart
+ * rigidly along its line of centres (node centroids, minimum image) by half
+ * the deficit each; all pairs of a sweep move at once from the positions at
+ * its start (a particle in several pairs moves by the sum), and sweeps repeat
+ * (at most max_sweeps) until no pair is nearer than h_min (1 - 1e-9).  Gaps
+ * are node to node: they see near contacts, not deep overlaps.  h_min must be
+ * at most a cell width of the plan (pairs are searched in neighbouring
+ * cells).  Moves the plan's mesh; moves (out, may be NULL): pair moves made. */
+ggem_status ggem_overlap_correct(ggem_plan_t *plan, double h_min, int max_sweeps, int *moves);
+
 /*
  * Allocation-free local velocity sum (no counterpart in the paper).
  *

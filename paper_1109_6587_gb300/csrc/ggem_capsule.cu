@@ -250,6 +250,98 @@ __global__ void k_normal_shift(int n, const int* __restrict__ part, const double
     for (int c = 0; c < 3; ++c) x[3 * b + c] += s * nrm[3 * b + c];
 }
 
+// mean node position of particle blockIdx.x (node lists of the particles)
+__global__ void __launch_bounds__(CB) k_centroids(const int* __restrict__ pstart,
+                                                  const int* __restrict__ pnodes,
+                                                  const double* __restrict__ x,
+                                                  double* __restrict__ c) {
+    __shared__ double red[3][CB / 32];
+    const int p = blockIdx.x;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int k = pstart[p] + threadIdx.x; k < pstart[p + 1]; k += CB) {
+        const int i = pnodes[k];
+        for (int d = 0; d < 3; ++d) a[d] += x[3 * i + d];
+    }
+    for (int d = 0; d < 3; ++d) {
+        double t = a[d];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[d][threadIdx.x >> 5] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double inv = 1.0 / (double)(pstart[p + 1] - pstart[p]);
+        for (int d = 0; d < 3; ++d) {
+            double t = 0.0;
+            for (int w = 0; w < CB / 32; ++w) t += red[d][w];
+            c[3 * p + d] = t * inv;
+        }
+    }
+}
+
+constexpr int kGapSlots = 4;   // other particles recorded per node
+
+// every node: the closest node of each (of up to kGapSlots) other particles
+// nearer than hthr in its own or a neighbouring cell; records (p, q, gap) for
+// q > p, p the node's own particle
+__global__ void k_gap_pairs(int n, GridGeom geo, CellGrid cg, const int* __restrict__ cell,
+                            const int* __restrict__ start, const int* __restrict__ perm,
+                            const int* __restrict__ part, const double* __restrict__ x,
+                            double hthr, int cap, int* __restrict__ rec,
+                            double* __restrict__ recd, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell[i];
+    const int cx = c % cg.ncx, cy = (c / cg.ncx) % cg.ncy, cz = c / (cg.ncx * cg.ncy);
+    const int me = perm[i], p = part[me];
+    const double px = x[3 * me], py = x[3 * me + 1], pz = x[3 * me + 2];
+    int sq[kGapSlots];
+    double sd[kGapSlots];
+    int ns = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int yy = cy + dy;
+                if (yy < 0 || yy >= cg.ncy) continue;
+                const int xx = (cx + dx + cg.ncx) % cg.ncx, zz = (cz + dz + cg.ncz) % cg.ncz;
+                const int cc = (zz * cg.ncy + yy) * cg.ncx + xx;
+                for (int j = start[cc]; j < start[cc + 1]; ++j) {
+                    const int o = perm[j], q = part[o];
+                    if (q <= p) continue;
+                    double ex = x[3 * o] - px, ey = x[3 * o + 1] - py, ez = x[3 * o + 2] - pz;
+                    ex -= geo.Lx * rint(ex / geo.Lx);
+                    ez -= geo.Lz * rint(ez / geo.Lz);
+                    const double d = sqrt(ex * ex + ey * ey + ez * ez);
+                    if (!(d < hthr)) continue;
+                    int k = 0;
+                    while (k < ns && sq[k] != q) ++k;
+                    if (k < ns) {
+                        sd[k] = fmin(sd[k], d);
+                    } else if (ns < kGapSlots) {
+                        sq[ns] = q;
+                        sd[ns] = d;
+                        ++ns;
+                    }
+                }
+            }
+    for (int k = 0; k < ns; ++k) {
+        const int r = atomicAdd(count, 1);
+        if (r < cap) {
+            rec[2 * r] = p;
+            rec[2 * r + 1] = sq[k];
+            recd[r] = sd[k];
+        }
+    }
+}
+
+// x_b += disp[particle_b]
+__global__ void k_translate(int n, const int* __restrict__ part, const double* __restrict__ disp,
+                            double* __restrict__ x) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int p = part[b];
+    for (int d = 0; d < 3; ++d) x[3 * b + d] += disp[3 * p + d];
+}
+
 unsigned nblk(size_t n) { return (unsigned)((n + CB - 1) / CB); }
 
 void ensure_capsule_ws(ggem_plan_t* P) {
@@ -571,6 +663,90 @@ ggem_status ggem_volume_correct(ggem_plan_t* P, const double* v0, double thresho
             GG_CHECK(s == GGEM_OK, s, std::string("corrected mesh: ") + ggem_last_error(P));
         }
         if (passes) *passes = k;
+    });
+}
+
+ggem_status ggem_overlap_correct(ggem_plan_t* P, double h_min, int max_sweeps, int* moves) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(P->mesh_ready, GGEM_ERR_INVALID_ARG, "no mesh set");
+        GG_CHECK(P->d_particle && P->particles_n == P->n_nodes, GGEM_ERR_INVALID_ARG,
+                 "particle ids not set for this mesh (ggem_mesh_particles)");
+        GG_CHECK(h_min > 0.0 && h_min <= std::min(P->cg.hx, std::min(P->cg.hy, P->cg.hz)),
+                 GGEM_ERR_INVALID_ARG, "h_min must be positive and at most a cell width");
+        GG_CHECK(max_sweeps >= 0, GGEM_ERR_INVALID_ARG, "max_sweeps must be >= 0");
+        particle_node_lists(P);
+        const int n = P->n_nodes, np = P->n_particles;
+        const int cap = kGapSlots * P->cap;
+        if (!P->d_orec) {
+            dalloc(P, &P->d_orec, (size_t)2 * cap);
+            dalloc(P, &P->d_orecd, (size_t)cap);
+            dalloc(P, &P->d_ocount, 1);
+        }
+        dfree(P->d_odisp);
+        P->d_odisp = nullptr;
+        dalloc(P, &P->d_odisp, (size_t)3 * np);
+        std::vector<double> c(3 * (size_t)np), disp(3 * (size_t)np);
+        std::vector<int> rec;
+        std::vector<double> recd;
+        const double hthr = h_min * (1.0 - 1e-9);   // corrected gaps land on h_min
+        int total = 0;
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+            GG_CUDA(cudaMemsetAsync(P->d_ocount, 0, sizeof(int), P->st));
+            k_gap_pairs<<<nblk(n), CB, 0, P->st>>>(n, P->geo, P->cg, P->d_mesh_cell,
+                                                   P->d_mesh_start, P->d_mesh_perm,
+                                                   P->d_particle, P->d_x, hthr, cap, P->d_orec,
+                                                   P->d_orecd, P->d_ocount);
+            k_centroids<<<np, CB, 0, P->st>>>(P->d_pstart, P->d_pnodes, P->d_x, P->d_odisp);
+            GG_CUDA(cudaGetLastError());
+            P->launches += 2;
+            int cnt = 0;
+            GG_CUDA(cudaMemcpyAsync(&cnt, P->d_ocount, sizeof(int), cudaMemcpyDeviceToHost,
+                                    P->st));
+            GG_CUDA(cudaMemcpyAsync(c.data(), P->d_odisp, c.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, P->st));
+            GG_CUDA(cudaStreamSynchronize(P->st));
+            GG_CHECK(cnt <= cap, GGEM_ERR_CAPACITY, "overlap records overflowed");
+            if (cnt == 0) break;
+            rec.resize(2 * (size_t)cnt);
+            recd.resize(cnt);
+            GG_CUDA(cudaMemcpyAsync(rec.data(), P->d_orec, rec.size() * sizeof(int),
+                                    cudaMemcpyDeviceToHost, P->st));
+            GG_CUDA(cudaMemcpyAsync(recd.data(), P->d_orecd, recd.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, P->st));
+            GG_CUDA(cudaStreamSynchronize(P->st));
+            // smallest gap of every violating pair, in pair order
+            std::vector<std::pair<std::pair<int, int>, double>> pairs(cnt);
+            for (int r = 0; r < cnt; ++r) pairs[r] = {{rec[2 * r], rec[2 * r + 1]}, recd[r]};
+            std::sort(pairs.begin(), pairs.end());
+            std::fill(disp.begin(), disp.end(), 0.0);
+            int found = 0;
+            for (size_t r = 0; r < pairs.size(); ++r) {
+                if (r > 0 && pairs[r].first == pairs[r - 1].first) continue;   // sorted: first is min
+                const int p = pairs[r].first.first, q = pairs[r].first.second;
+                const double gap = pairs[r].second;
+                double d[3];
+                for (int k = 0; k < 3; ++k) d[k] = c[3 * q + k] - c[3 * p + k];
+                d[0] -= P->geo.Lx * std::nearbyint(d[0] / P->geo.Lx);
+                d[2] -= P->geo.Lz * std::nearbyint(d[2] / P->geo.Lz);
+                const double len = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const double sh = 0.5 * (h_min - gap) / len;
+                for (int k = 0; k < 3; ++k) {
+                    disp[3 * p + k] -= sh * d[k];
+                    disp[3 * q + k] += sh * d[k];
+                }
+                ++found;
+            }
+            GG_CUDA(cudaMemcpyAsync(P->d_odisp, disp.data(), disp.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, P->st));
+            k_translate<<<nblk(n), CB, 0, P->st>>>(n, P->d_particle, P->d_odisp, P->d_x);
+            GG_CUDA(cudaGetLastError());
+            P->launches += 1;
+            const ggem_status s = ggem_mesh_set(P, n, P->d_x, P->n_tris, P->d_tri);
+            GG_CHECK(s == GGEM_OK, s, std::string("corrected mesh: ") + ggem_last_error(P));
+            total += found;
+        }
+        if (moves) *moves = total;
     });
 }
 

@@ -133,6 +133,11 @@ void stage(ggem_plan_t* P, int id, int nk, F&& f) {
 void single_layer_dev(ggem_plan_t* P, const double* q, double* w);
 void double_layer_dev(ggem_plan_t* P, const double* q, double* v);
 
+// node lists of the particles of ggem_mesh_particles (d_pstart / d_pnodes,
+// CSR, nodes ascending), built on first use after the ids change; also sizes
+// the per-particle arrays d_rc / d_rscale
+void particle_node_lists(ggem_plan_t* P);
+
 // out = base + A^-1 r estimated by the learned warm start (device arrays;
 // base may be NULL); defined with the network kernels
 void mlp_guess_dev(ggem_plan_t* P, const double* kappa, const double* r, const double* base,

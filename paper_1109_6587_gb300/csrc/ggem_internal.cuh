@@ -193,6 +193,10 @@ struct ggem_plan {
     int* d_tlist = nullptr;            // [cap_tris] triangle indices grouped by particle
     double* d_cvol = nullptr;          // [pcount_cap] particle volumes / areas scratch
     bool tcsr_ready = false;
+    int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
+    double* d_orecd = nullptr;         // [4 cap] overlap records: node gap
+    int* d_ocount = nullptr;           // record count
+    double* d_odisp = nullptr;         // [pcount_cap][3] rigid displacements / centroids
     float* d_feat = nullptr;           // [cap][12] features
     float* d_mlp = nullptr;            // [35075] FP32 master parameters
     float* d_mlp_grad = nullptr;       // gradient accumulator

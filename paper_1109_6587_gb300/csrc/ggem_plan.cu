@@ -600,7 +600,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_tc_fwd, P->d_tc_inv, P->d_spread_list, P->d_pstart,
                     P->d_pnodes, P->d_rc, P->d_rscale, P->d_mref, P->d_cx0, P->d_cdf,
                     P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
-                    P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol};
+                    P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
+                    P->d_ocount, P->d_odisp};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);

@@ -602,9 +602,11 @@ __global__ void __launch_bounds__(RB) k_rigid_setup(const int* __restrict__ psta
     }
 }
 
+}  // namespace
+
 // node lists of the particles (CSR, nodes ascending within a particle), from
 // the plan's particle ids; sizes the per-particle arrays
-void rigid_prepare(ggem_plan_t* P) {
+void ggem::particle_node_lists(ggem_plan_t* P) {
     const int np = P->n_particles, n = P->n_nodes;
     if (P->rig_cap < np) {
         for (void* q : {(void*)P->d_pstart, (void*)P->d_rc, (void*)P->d_rscale}) dfree(q);
@@ -632,6 +634,8 @@ void rigid_prepare(ggem_plan_t* P) {
     GG_CUDA(cudaStreamSynchronize(P->st));                       // host vectors go out of scope
     P->pcsr_ready = true;
 }
+
+namespace {
 
 // copy n doubles from a host or device array into device memory
 void copy_in(ggem_plan_t* P, double* dst, const double* src, size_t n) {
@@ -670,7 +674,7 @@ ggem_status ggem_rigid_solve(ggem_plan_t* P, int n_particles, const double* cent
         const size_t nf = (size_t)3 * n, nz = nf + (size_t)6 * np;
         ensure_solver_ws(P, restart, nz);
         ensure_twin(P);
-        rigid_prepare(P);
+        particle_node_lists(P);
         P->sol_cycles = P->sol_mv64 = P->sol_mvmix = 0;
         P->sol_guess_mlp = 0;
         P->sol_rel_plain = P->sol_rel_mlp = 0.0;

@@ -51,7 +51,7 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_check", "ggem_rigid_solve", "ggem_membrane_reference",
            "ggem_membrane_traction", "ggem_undisturbed", "ggem_capsule_velocity",
            "ggem_capsule_step", "ggem_mesh_positions", "ggem_min_separation",
-           "ggem_particle_volumes", "ggem_volume_correct"]
+           "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct"]
 
 GGEM_FLOW = {"none": 0, "shear": 1, "poiseuille": 2}
 
@@ -107,6 +107,7 @@ def lib():
         L.ggem_min_separation.argtypes = [P, ctypes.POINTER(D)]
         L.ggem_particle_volumes.argtypes = [P, P]
         L.ggem_volume_correct.argtypes = [P, P, D, I, ctypes.POINTER(I)]
+        L.ggem_overlap_correct.argtypes = [P, D, I, ctypes.POINTER(I)]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -418,6 +419,14 @@ class Plan:
         _check(lib().ggem_volume_correct(self.h, v.ctypes.data_as(ctypes.c_void_p),
                                          float(threshold), int(max_passes), ctypes.byref(k)),
                self.h)
+        return k.value
+
+    def overlap_correct(self, h_min, max_sweeps=100):
+        """Minimum-gap correction (Sec. 7.1); the plan's mesh moves.  Returns
+        the pair moves made."""
+        k = ctypes.c_int(0)
+        _check(lib().ggem_overlap_correct(self.h, float(h_min), int(max_sweeps),
+                                          ctypes.byref(k)), self.h)
         return k.value
 
     def check(self):

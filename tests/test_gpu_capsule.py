@@ -14,7 +14,9 @@ displacement plus a stretch, viscosity ratios 0.2 and 5, element quadrature.
     step made;
   * smallest node separation (minimum image) equal to brute force to
     rounding; volumes 1e-13; the volume correction lands within its threshold
-    and on the oracle's positions (1e-12).
+    and on the oracle's positions (1e-12);
+  * overlap correction: a pair across the periodic boundary and a chain of
+    three, the same pair moves as the oracle and its positions (1e-12).
 """
 import numpy as np
 import pytest
@@ -125,3 +127,37 @@ def test_separation_and_volumes(ggem, capsules):
     assert np.abs(xc - xo).max() < 1e-12
     vc = P.particle_volumes()
     assert np.abs(vc / v0 - 1).max() <= 1e-4
+
+
+def _facing(box, centres_along, level=2):
+    """Spheres placed by centres_along(v), v an icosahedron vertex direction
+    (facing vertices of neighbours lie on their line of centres)."""
+    import math
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    v = np.array([phi, 0.0, 1.0]) / math.hypot(phi, 1.0)
+    centres = np.array(centres_along(v))
+    return v, W.suspension(len(centres), box, level=level, centres=centres)
+
+
+@pytest.mark.parametrize("case", ["pair_across_boundary", "chain_of_three"])
+def test_overlap_correction(ggem, case):
+    box = _box()
+    if case == "pair_across_boundary":
+        def along(v):
+            c0 = np.array([15.5, 0.0, 8.0])
+            c1 = c0 + 2.03 * v
+            c1[0] -= box.Lx
+            return [c0, c1]
+    else:
+        def along(v):
+            c = np.array([8.0, 0.0, 8.0])
+            return [c - 2.03 * v, c, c + 2.03 * v]
+    _, s = _facing(box, along)
+    n_p = len(s.centres)
+    P = _plan(ggem, s, "fp64")
+    moves = P.overlap_correct(0.05)
+    x = P.mesh_positions()
+    xo, mo = C.overlap_correct(s.x, s.particle, n_p, box, 0.05)
+    assert moves == mo and moves >= 1
+    assert np.abs(x - xo).max() < 1e-12
+    assert P.overlap_correct(0.05) == 0                    # nothing left to correct
