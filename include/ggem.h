@@ -182,7 +182,7 @@ ggem_status ggem_double_layer(ggem_plan_t *plan, const double *q, double *v);
  * come from an FP64 twin plan on the same mesh (built by the first solve and
  * kept in step with later ggem_mesh_set calls; it doubles the plan's device
  * memory), and each correction is one GMRES cycle with the mixed operator,
- * solved to max(tol ||b|| / (2 ||r||), 1e-4) relative to its residual r.  The
+ * solved to max(tol ||b|| / (2 ||r||), 1e-5) relative to its residual r.  The
  * residual of the initial guess is formed with the mixed operator (the first
  * correction needs only ~1e-4) unless it is within 10 tol, when FP64 decides.
  * Arrays may be device or host memory.  The first solve allocates the

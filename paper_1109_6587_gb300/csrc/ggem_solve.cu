@@ -348,9 +348,12 @@ ggem_status refine(Solver& S, double nb, double tol, int restart, int maxit, dou
             break;
         }
         int m = std::min(restart, maxit - its);
-        // FP64: aim at the final tolerance.  Mixed: one correction gains at
-        // most ~4 digits (the mixed operator matches FP64 to ~1e-5 relative).
-        double eta = P->fp64 ? tol * nb / beta : std::max(0.5 * tol * nb / beta, 1e-4);
+        // FP64: aim at the final tolerance.  Mixed: after a correction solved
+        // to eta relative to r, the true residual is about (eta + eps) ||r||,
+        // eps ~ 1e-5 the mixed operator's relative accuracy; asking eta down to
+        // eps lets one correction from a warm start (||r|| ~ 1e-2 ||b||) reach
+        // 1e-6, so the solve needs a single FP64 residual after it.
+        double eta = P->fp64 ? tol * nb / beta : std::max(0.5 * tol * nb / beta, 1e-5);
         bool bd = false;
         int steps = S.cycle(P, m, beta, eta * beta, &bd);
         its += steps;
