@@ -44,7 +44,7 @@ typedef enum {
     GGEM_OK_BREAKDOWN = 6       /* GMRES happy breakdown: exact solution found */
 } ggem_status;
 
-enum { GGEM_FP64 = 0, GGEM_MIXED = 1 };          /* ggem_params.precision  */
+enum { GGEM_FP64 = 0, GGEM_MIXED = 1, GGEM_FP64_EMULATED = 2 };  /* ggem_params.precision */
 enum { GGEM_NODAL = 0, GGEM_ELEMENT = 1 };       /* ggem_params.quadrature */
 
 typedef struct ggem_plan ggem_plan_t;
@@ -56,7 +56,11 @@ typedef struct ggem_plan ggem_plan_t;
  *   rcut_factor  r_cut = rcut_factor/alpha; 0 selects 4 (Sec. 3.2.1).
  *   precision    GGEM_FP64: every step in FP64.  GGEM_MIXED: local sum,
  *                spreading, FFT, Chebyshev transforms and interpolation in
- *                FP32; per-mode tau solves in FP64.
+ *                FP32; per-mode tau solves in FP64.  GGEM_FP64_EMULATED: as
+ *                GGEM_FP64, except that the element-rule local sum runs in
+ *                double-float arithmetic (pairs of floats, ~48-bit
+ *                significand; GB300's FP32 rate is 64x its FP64 rate), at FP64
+ *                parity; the FP64 twin of a mixed plan uses it.
  *   quadrature   GGEM_ELEMENT: local part by the 4x4 Gauss product rule per
  *                triangle with the polar rule on triangles touching the
  *                target (Sec. 3.4.1, 3.5.2).  GGEM_NODAL: nodal point forces

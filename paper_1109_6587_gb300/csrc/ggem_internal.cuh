@@ -193,6 +193,9 @@ struct ggem_plan {
     int* d_tlist = nullptr;            // [cap_tris] triangle indices grouped by particle
     double* d_cvol = nullptr;          // [pcount_cap] particle volumes / areas scratch
     bool tcsr_ready = false;
+    bool ff = false;                   // element-rule local sum in double-float arithmetic
+    void* d_qp_ff = nullptr;           // [cap_qp][2] float4: sorted point offsets, hi / lo
+    void* d_qg_ff = nullptr;           // [cap_qp][2] float4: sorted point strengths, hi / lo
     int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
     double* d_orecd = nullptr;         // [4 cap] overlap records: node gap
     int* d_ocount = nullptr;           // record count
@@ -257,11 +260,15 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
 // nodes tgt (output in caller order), skipping points of triangles that
 // contain the target (only tested when closer than `near`); layer 0
 // velocity, 1 double layer
+// (FP64 with ff_pos / ff_g non-null: the double-float kernel on those copies)
 template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
-                           cudaStream_t st);
+                           cudaStream_t st, const void* ff_pos = nullptr,
+                           const void* ff_g = nullptr);
+// float-pair copy of n double4 (x, y, z, w) values: out[2 i] = hi, out[2 i + 1] = lo
+cudaError_t to_float_pairs(int n, const void* in, void* out, cudaStream_t st);
 cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st);
 
 // exclusive scan of count[0..n) into start[0..n] (start[n] = total)

@@ -10,6 +10,7 @@
 // visits a cell twice.
 #include "ggem_internal.cuh"
 #include "ggem_erfcx.cuh"
+#include "ggem_ff.cuh"
 
 namespace ggem {
 
@@ -644,6 +645,203 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a) {
     }
 }
 
+// ----------------------------------- element rule, FP64-accurate in float pairs
+// The FP64 element-rule local sum in double-float arithmetic (ggem_ff.cuh):
+// same cells, culling and hit queue as k_local<double, ..., ELEM>, with the
+// sources read from float-pair copies of the sorted offsets and strengths.
+// exp from a 2^(j/16) reduction, erfcx from the FP64 piecewise polynomials
+// (degrees 0..9 in pairs, 10..12 in float), 1/r by one Newton step.
+constexpr int kFFHead = 9;
+
+struct FFConst {
+    ff al, al2, rc2, near2, c1, c2, c3, c4, ln2_16, sixth;
+};
+
+struct FFAcc {
+    ff ux = {0.f, 0.f}, uy = {0.f, 0.f}, uz = {0.f, 0.f};
+};
+
+__device__ __forceinline__ ff ff_dot(ff ax, ff ay, ff az, ff bx, ff by, ff bz) {
+    return ff_add(ff_add(ff_mul(ax, bx), ff_mul(ay, by)), ff_mul(az, bz));
+}
+
+// erfcx(x), 0 <= x < 4, from the FP64 table in pairs (tab[j * 8 + i])
+__device__ __forceinline__ ff ff_erfcx(ff x, const ff* tab) {
+    const int i = min((int)(x.hi * 2.0f), GGEM_ERFCX64_NINT - 1);
+    const ff u = ff_add_f(ff_mul_f(x, 4.0f), -(float)(2 * i + 1));
+    const float uh = u.hi;
+    float t = tab[GGEM_ERFCX64_DEG * 8 + i].hi;
+    for (int j = GGEM_ERFCX64_DEG - 1; j > kFFHead; --j) t = fmaf(t, uh, tab[j * 8 + i].hi);
+    ff p = ff_of(t);
+    for (int j = kFFHead; j >= 0; --j) p = ff_add(ff_mul(p, u), tab[j * 8 + i]);
+    return p;
+}
+
+template <int MODE>
+__device__ __forceinline__ void pair_terms_ff(const FFConst& k, ff dx, ff dy, ff dz, ff r2, ff gx,
+                                              ff gy, ff gz, ff nx, ff ny, ff nz, const ff* tab,
+                                              const ff* t2, FFAcc& a) {
+    const ff ir = ff_rsqrt(r2);
+    const ff r = ff_mul(r2, ir);
+    const ff ex = ff_exp(ff_neg(ff_mul(k.al2, r2)), t2, k.ln2_16, k.sixth);
+    const ff ec = ff_mul(ex, ff_erfcx(ff_mul(k.al, r), tab));
+    const ff xg = ff_dot(dx, dy, dz, gx, gy, gz);
+    const ff ir2 = ff_mul(ir, ir);
+    if (MODE & OUT_U) {
+        // A = ec/r - c1 ex,  B = (ec/r^3 + c1 ex/r^2) xg
+        const ff eir = ff_mul(ec, ir);
+        const ff c1ex = ff_mul(k.c1, ex);
+        const ff A = ff_sub(eir, c1ex);
+        const ff B = ff_mul(ff_mul(ir2, ff_add(eir, c1ex)), xg);
+        a.ux = ff_add(a.ux, ff_add(ff_mul(A, gx), ff_mul(B, dx)));
+        a.uy = ff_add(a.uy, ff_add(ff_mul(A, gy), ff_mul(B, dy)));
+        a.uz = ff_add(a.uz, ff_add(ff_mul(A, gz), ff_mul(B, dz)));
+    }
+    if (MODE & OUT_DBL) {
+        // D = -6 ec/r^5 - c2 ex/r^4 - c3 ex/r^2,  E = c4 ex
+        const ff t = ff_sub(ff_mul_f(ff_mul(ec, ir), -6.0f), ff_mul(k.c2, ex));
+        const ff D = ff_sub(ff_mul(ff_mul(ir2, ir2), t), ff_mul(ff_mul(k.c3, ex), ir2));
+        const ff E = ff_mul(k.c4, ex);
+        const ff xn = ff_dot(dx, dy, dz, nx, ny, nz);
+        const ff gn = ff_dot(gx, gy, gz, nx, ny, nz);
+        const ff Dxn = ff_mul(ff_mul(D, xg), xn);
+        const ff nxg[3] = {ff_mul(nx, xg), ff_mul(ny, xg), ff_mul(nz, xg)};
+        const ff d[3] = {dx, dy, dz}, g[3] = {gx, gy, gz};
+        ff* acc[3] = {&a.ux, &a.uy, &a.uz};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const ff in = ff_add(ff_add(ff_mul(d[c], gn), ff_mul(g[c], xn)), nxg[c]);
+            *acc[c] = ff_add(*acc[c], ff_add(ff_mul(Dxn, d[c]), ff_mul(E, in)));
+        }
+    }
+}
+
+template <int MODE, int REACH>
+__global__ void __launch_bounds__(LW * 32) k_local_elem_ff(LocalArgs<double> a,
+                                                         const float4* __restrict__ qpos,
+                                                         const float4* __restrict__ qg) {
+    __shared__ int s_cst[LW][kNb];
+    __shared__ int s_cnt[LW][kNb];
+    __shared__ unsigned short s_off[LW][kNb];
+    __shared__ int2 s_q[LW][kQueue];              // queued hits: sorted point, cell slot
+    __shared__ ff s_tab[(GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT];
+    __shared__ ff s_t2[16];
+    for (int e = threadIdx.x; e < (GGEM_ERFCX64_DEG + 1) * GGEM_ERFCX64_NINT; e += blockDim.x)
+        s_tab[e] = ff_from_double(kErfcxTab64[e]);
+    if (threadIdx.x < 16) s_t2[threadIdx.x] = ff_from_double(exp2((double)threadIdx.x / 16.0));
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * LW + wid;
+    if (t >= a.n_tgt) return;                     // warp-uniform
+    int cx, cy, cz, oidx;
+    double ox, oy, oz;
+    load_target<double, TK_POINTS>(a, t, ox, oy, oz, cx, cy, cz, oidx);
+    constexpr int R = REACH, side = 2 * R + 1;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nc = cull_cells<double, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid], s_cnt[wid],
+                                         s_off[wid]);
+    FFConst k;
+    k.al = ff_from_double(a.k.al);
+    k.al2 = ff_from_double(a.k.al2);
+    k.rc2 = ff_from_double(a.k.rc2);
+    k.near2 = ff_from_double(a.near2);
+    k.c1 = ff_from_double(a.k.c1);
+    k.c2 = ff_from_double(a.k.c2);
+    k.c3 = ff_from_double(a.k.c3);
+    k.c4 = ff_from_double(a.k.c4);
+    k.ln2_16 = ff_from_double(0.043321698784996581);   // ln 2 / 16
+    k.sixth = ff_from_double(1.0 / 6.0);
+    const ff o[3] = {ff_from_double(ox), ff_from_double(oy), ff_from_double(oz)};
+    const ff hc[3] = {ff_from_double(a.k.hx), ff_from_double(a.k.hy), ff_from_double(a.k.hz)};
+    ff nx = ff_of(0.f), ny = ff_of(0.f), nz = ff_of(0.f);
+    if (MODE & OUT_DBL) {
+        nx = ff_from_double(a.nrm[3 * oidx]);
+        ny = ff_from_double(a.nrm[3 * oidx + 1]);
+        nz = ff_from_double(a.nrm[3 * oidx + 2]);
+    }
+    // target in the frame of the corner of cell slot ci
+    auto target = [&](int ci, ff& tx, ff& ty, ff& tz) {
+        const int oi = s_off[wid][ci];
+        tx = ff_sub(o[0], ff_mul_f(hc[0], (float)(oi % side - R)));
+        ty = ff_sub(o[1], ff_mul_f(hc[1], (float)((oi / side) % side - R)));
+        tz = ff_sub(o[2], ff_mul_f(hc[2], (float)(oi / (side * side) - R)));
+    };
+    auto eval = [&](int s, int ci, FFAcc& acc) {
+        ff tx, ty, tz;
+        target(ci, tx, ty, tz);
+        const float4 ph = qpos[2 * (size_t)s], pl = qpos[2 * (size_t)s + 1];
+        const ff dx = ff_sub(tx, {ph.x, pl.x}), dy = ff_sub(ty, {ph.y, pl.y}),
+                 dz = ff_sub(tz, {ph.z, pl.z});
+        const ff r2 = ff_dot(dx, dy, dz, dx, dy, dz);
+        const float4 gh = qg[2 * (size_t)s], gl = qg[2 * (size_t)s + 1];
+        pair_terms_ff<MODE>(k, dx, dy, dz, r2, {gh.x, gl.x}, {gh.y, gl.y}, {gh.z, gl.z}, nx, ny,
+                            nz, s_tab, s_t2, acc);
+    };
+    FFAcc acc;
+    int head = 0, qn = 0;                         // warp-uniform
+    for (int ci = 0; ci < nc; ++ci) {
+        const int st = s_cst[wid][ci], cnt = s_cnt[wid][ci];
+        ff tx, ty, tz;
+        target(ci, tx, ty, tz);
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            bool hit = false;
+            int s = 0;
+            if (i < cnt) {
+                s = st + i;
+                const float4 ph = qpos[2 * (size_t)s], pl = qpos[2 * (size_t)s + 1];
+                const ff dx = ff_sub(tx, {ph.x, pl.x}), dy = ff_sub(ty, {ph.y, pl.y}),
+                         dz = ff_sub(tz, {ph.z, pl.z});
+                const ff r2 = ff_dot(dx, dy, dz, dx, dy, dz);
+                hit = ff_lt(r2, k.rc2) && r2.hi > 0.f;
+                if (hit && ff_lt(r2, k.near2)) {
+                    const int4 v = a.qvs[s];
+                    hit = !(v.x == oidx || v.y == oidx || v.z == oidx);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) s_q[wid][(head + qn + __popc(m & lt)) & (kQueue - 1)] = make_int2(s, ci);
+            qn += __popc(m);
+            if (qn >= 32) {
+                __syncwarp();
+                const int2 e = s_q[wid][(head + lane) & (kQueue - 1)];
+                eval(e.x, e.y, acc);
+                head = (head + 32) & (kQueue - 1);
+                qn -= 32;
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) {
+        const int2 e = s_q[wid][(head + lane) & (kQueue - 1)];
+        eval(e.x, e.y, acc);
+    }
+    double ux = ff_to_double(acc.ux), uy = ff_to_double(acc.uy), uz = ff_to_double(acc.uz);
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        ux += __shfl_xor_sync(0xffffffffu, ux, o2);
+        uy += __shfl_xor_sync(0xffffffffu, uy, o2);
+        uz += __shfl_xor_sync(0xffffffffu, uz, o2);
+    }
+    if (lane == 0) {
+        double* out = a.out + (size_t)oidx * a.out_stride;
+        out[0] = a.k.fU * ux;
+        out[1] = a.k.fU * uy;
+        out[2] = a.k.fU * uz;
+    }
+}
+
+__global__ void k_to_float_pairs(int n, const double* __restrict__ in, float4* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* v = in + 4 * (size_t)i;
+    const ff x = ff_from_double(v[0]), y = ff_from_double(v[1]), z = ff_from_double(v[2]),
+             w = ff_from_double(v[3]);
+    out[2 * (size_t)i] = make_float4(x.hi, y.hi, z.hi, w.hi);
+    out[2 * (size_t)i + 1] = make_float4(x.lo, y.lo, z.lo, w.lo);
+}
+
 template <typename T, int KIND, int REACH>
 static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     dim3 b(LW * 32), g((a.n_tgt + LW - 1) / LW);
@@ -666,11 +864,17 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     else launch_kind<T, KIND, 2>(a, mode, st);
 }
 
+cudaError_t to_float_pairs(int n, const void* in, void* out, cudaStream_t st) {
+    if (n > 0)
+        k_to_float_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, (const double*)in, (float4*)out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
-                           cudaStream_t st) {
+                           cudaStream_t st, const void* ff_pos, const void* ff_g) {
     if (tgt.n <= 0) return cudaSuccess;
     // targets: the mesh nodes in cell order, so the warps of a block mostly
     // scan the same candidate cells (L1 reuse); output in caller order
@@ -688,6 +892,20 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
         return cudaGetLastError();
     }
     dim3 b(LW * 32), g((tgt.n + LW - 1) / LW);
+    if constexpr (sizeof(T) == 8) {
+        if (ff_pos && ff_g) {
+            const float4* fp = (const float4*)ff_pos;
+            const float4* fg = (const float4*)ff_g;
+            if (cg.reach == 3) {
+                if (layer == 0) k_local_elem_ff<OUT_U, 3><<<g, b, 0, st>>>(a, fp, fg);
+                else k_local_elem_ff<OUT_DBL, 3><<<g, b, 0, st>>>(a, fp, fg);
+            } else {
+                if (layer == 0) k_local_elem_ff<OUT_U, 2><<<g, b, 0, st>>>(a, fp, fg);
+                else k_local_elem_ff<OUT_DBL, 2><<<g, b, 0, st>>>(a, fp, fg);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (cg.reach == 3) {
         if (layer == 0) k_local<T, TK_POINTS, OUT_U, true, 3><<<g, b, 0, st>>>(a);
         else k_local<T, TK_POINTS, OUT_DBL, true, 3><<<g, b, 0, st>>>(a);
@@ -726,7 +944,7 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
     template cudaError_t local_sum_elem<T>(const GridGeom&, const CellGrid&,                  \
                                            const SortedSources<T>&, const int4*, double,        \
                                            const SortedSources<T>&, const double*, int, T*, int, \
-                                           cudaStream_t);
+                                           cudaStream_t, const void*, const void*);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

@@ -248,6 +248,7 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         if (elem)
             GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qp_perm, P->d_qv, (const v4_t<T>*)P->d_qw, q,
                                     8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg, st));
+        if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
@@ -282,7 +283,7 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         qs.n = P->n_qp;
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
-                                      P->d_nrm, layer, loc, 3, ls));
+                                      P->d_nrm, layer, loc, 3, ls, P->d_qp_ff, P->d_qg_ff));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
@@ -354,8 +355,9 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     GG_CHECK(prm.Ny >= 9 && prm.Ny <= 257, GGEM_ERR_INVALID_ARG, "Ny must lie in [9, 257]");
     GG_CHECK(prm.Lx > 0 && prm.Lz > 0 && prm.W > 0 && prm.mu > 0, GGEM_ERR_INVALID_ARG,
              "Lx, Lz, W and mu must be positive");
-    GG_CHECK(prm.precision == GGEM_FP64 || prm.precision == GGEM_MIXED, GGEM_ERR_INVALID_ARG,
-             "precision must be GGEM_FP64 or GGEM_MIXED");
+    GG_CHECK(prm.precision == GGEM_FP64 || prm.precision == GGEM_MIXED ||
+                 prm.precision == GGEM_FP64_EMULATED,
+             GGEM_ERR_INVALID_ARG, "precision must be GGEM_FP64, GGEM_MIXED or GGEM_FP64_EMULATED");
     GG_CHECK(prm.quadrature == GGEM_NODAL || prm.quadrature == GGEM_ELEMENT,
              GGEM_ERR_INVALID_ARG, "quadrature must be GGEM_NODAL or GGEM_ELEMENT");
     GG_CHECK(prm.max_points > 0 && prm.max_tris >= 0, GGEM_ERR_INVALID_ARG,
@@ -371,7 +373,8 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     g.rcut = rf / g.alpha;
     GG_CHECK(g.alpha * prm.Lx > 2 * rf && g.alpha * prm.Lz > 2 * rf, GGEM_ERR_INVALID_ARG,
              "alpha*L must exceed 2*rcut_factor (r_cut below half the period)");
-    P->fp64 = prm.precision == GGEM_FP64;
+    P->fp64 = prm.precision != GGEM_MIXED;
+    P->ff = prm.precision == GGEM_FP64_EMULATED && prm.quadrature == GGEM_ELEMENT;
     P->nmodes = prm.Nz * g.nkx;
     CellGrid& cg = P->cg;
     // cells at least r_cut/R wide; the local sums search +-R cells and keep
@@ -416,7 +419,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
         std::vector<double> yd((size_t)Ny * Ny);
         for (int j = 0; j < Ny; ++j)
             for (int k = 0; k < Ny; ++k) yd[(size_t)j * Ny + k] = yj[j] - yj[k];
-        if (prm.precision == GGEM_FP64) {
+        if (P->fp64) {
             dalloc(P, (double**)&P->d_ydiff, yd.size());
             GG_CUDA(cudaMemcpy(P->d_ydiff, yd.data(), yd.size() * sizeof(double),
                                cudaMemcpyHostToDevice));
@@ -563,6 +566,10 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
         dalloc(P, &P->d_qp_start, (size_t)P->ncell + 1);
         GG_CUDA(cudaMalloc(&P->d_qp_pos, cq * v4 + 32));
         GG_CUDA(cudaMalloc(&P->d_qg, cq * v4 + 32));
+        if (P->ff) {                       // float-pair copies: [point][hi, lo] float4
+            GG_CUDA(cudaMalloc(&P->d_qp_ff, cq * 2 * sizeof(float4) + 32));
+            GG_CUDA(cudaMalloc(&P->d_qg_ff, cq * 2 * sizeof(float4) + 32));
+        }
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
     GG_CUDA(cudaEventCreate(&P->ev1));
@@ -601,7 +608,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_pnodes, P->d_rc, P->d_rscale, P->d_mref, P->d_cx0, P->d_cdf,
                     P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
-                    P->d_ocount, P->d_odisp};
+                    P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -735,6 +742,7 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 GG_CUDA(build_cells<double>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                             P->d_qp_start, P->d_cursor, P->d_qp_cell,
                                             P->d_qp_perm, (double4_32a*)P->d_qp_pos, st));
+                if (P->ff) GG_CUDA(to_float_pairs(nq, P->d_qp_pos, P->d_qp_ff, st));
             } else {
                 GG_CUDA(build_cells<float>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                            P->d_qp_start, P->d_cursor, P->d_qp_cell,

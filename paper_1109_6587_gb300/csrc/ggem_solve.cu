@@ -294,7 +294,7 @@ void ensure_solver_ws(ggem_plan_t* P, int m, size_t len) {
 void ensure_twin(ggem_plan_t* P) {
     if (P->fp64 || P->twin) return;
     ggem_params tp = P->prm;
-    tp.precision = GGEM_FP64;
+    tp.precision = GGEM_FP64_EMULATED;    // FP64 accuracy, float-pair local sum
     ggem_plan_t* T = nullptr;
     ggem_status s = ggem_plan(&tp, P->st, &T);
     GG_CHECK(s == GGEM_OK, s, std::string("FP64 twin plan: ") + ggem_last_error(nullptr));

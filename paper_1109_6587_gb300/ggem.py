@@ -21,7 +21,7 @@ GGEM_OK = 0
 STATUS = {0: "GGEM_OK", 1: "GGEM_ERR_INVALID_ARG", 2: "GGEM_ERR_CAPACITY",
           3: "GGEM_ERR_CUDA", 4: "GGEM_ERR_NUMERICAL", 5: "GGEM_ERR_NOT_CONVERGED",
           6: "GGEM_OK_BREAKDOWN"}
-GGEM_FP64, GGEM_MIXED = 0, 1
+GGEM_FP64, GGEM_MIXED, GGEM_FP64_EMULATED = 0, 1, 2
 GGEM_NODAL, GGEM_ELEMENT = 0, 1
 
 
@@ -162,7 +162,8 @@ class Plan:
     def __init__(self, Lx, Lz, W, y0, Nx, Ny, Nz, alpha=0.0, rcut_factor=0.0, mu=1.0,
                  precision="fp64", quadrature="nodal", max_points=1 << 16, max_tris=0,
                  stream=None):
-        prec = {"fp64": GGEM_FP64, "mixed": GGEM_MIXED}[precision]
+        prec = {"fp64": GGEM_FP64, "mixed": GGEM_MIXED,
+                "fp64_emulated": GGEM_FP64_EMULATED}[precision]
         quad = {"nodal": GGEM_NODAL, "element": GGEM_ELEMENT}[quadrature]
         self.params = ggem_params(Lx, Lz, W, y0, Nx, Ny, Nz, alpha, rcut_factor, mu, prec,
                                   quad, max_points, max_tris)
