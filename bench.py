@@ -282,8 +282,7 @@ def roofline(res, args):
         # element-rule kernel on this workload, from one ncu capture of that
         # launch (its ncu summary is kept with the profiles); other
         # configurations have no capture
-        traffic = (114.9e6 + 4.4e6) if (args.precision == "mixed"
-                                        and args.quadrature == "element") else None
+        traffic = None    # pending a capture of the current kernel
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"

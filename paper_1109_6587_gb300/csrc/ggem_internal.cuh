@@ -196,6 +196,9 @@ struct ggem_plan {
     bool ff = false;                   // element-rule local sum in double-float arithmetic
     void* d_qp_ff = nullptr;           // [cap_qp][2] float4: sorted point offsets, hi / lo
     void* d_qg_ff = nullptr;           // [cap_qp][2] float4: sorted point strengths, hi / lo
+    float* d_qp_soa = nullptr;         // [3][soa_ld] FP32 plans: sorted point offsets x, y, z
+    float* d_qg_soa = nullptr;         // [3][soa_ld] FP32 plans: sorted point strengths
+    size_t soa_ld = 0;                 // plane stride: cap_qp + one padded step, even
     int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
     double* d_orecd = nullptr;         // [4 cap] overlap records: node gap
     int* d_ocount = nullptr;           // record count
@@ -260,13 +263,17 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
 // nodes tgt (output in caller order), skipping points of triangles that
 // contain the target (only tested when closer than `near`); layer 0
 // velocity, 1 double layer
-// (FP64 with ff_pos / ff_g non-null: the double-float kernel on those copies)
+// aux_pos / aux_g: FP32, the structure-of-arrays planes of the sorted points
+// (x, y, z, stride aux_ld; required); FP64, float-pair copies selecting the
+// double-float kernel (nullptr: native FP64)
 template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
-                           cudaStream_t st, const void* ff_pos = nullptr,
-                           const void* ff_g = nullptr);
+                           cudaStream_t st, const void* aux_pos = nullptr,
+                           const void* aux_g = nullptr, size_t aux_ld = 0);
+// structure-of-arrays planes (x, y, z; stride ld) of n float4 values
+cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st);
 // float-pair copy of n double4 (x, y, z, w) values: out[2 i] = hi, out[2 i + 1] = lo
 cudaError_t to_float_pairs(int n, const void* in, void* out, cudaStream_t st);
 cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st);

@@ -562,14 +562,21 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 // ------------------------------------------------- FP32 element rule
 // The element-rule local sum in FP32 reads ~1,500 quadrature points per cell
 // and evaluates about 70 % of them, so no hit queue: every lane takes two
-// candidates of each 64-point step through a cell and evaluates both with
-// paired FP32 arithmetic; a miss contributes nothing (its strength is zero,
-// and every term carries a factor g).  Strengths are loaded for hits only.
+// adjacent candidates of each 64-point step through a cell and evaluates both
+// with paired FP32 arithmetic; a miss contributes nothing (its strength is
+// zero, and every term carries a factor g).  The points are read from
+// structure-of-arrays copies (x, y, z and gx, gy, gz planes of stride ld), so
+// one 8-byte load brings a coordinate of both candidates already paired.
+// Steps start at even sorted indices (8-byte alignment); slots outside the cell
+// are masked like misses (the planes are padded by one step, zero-filled).
 constexpr int LWE = 8;        // warps (targets) per block
 constexpr int kChunk = 64;    // candidates per warp step
 
 template <int MODE, int REACH>
-__global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a) {
+__global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
+                                                          const float* __restrict__ ps,
+                                                          const float* __restrict__ gs,
+                                                          size_t ld) {
     __shared__ int s_cst[LWE][kNb];
     __shared__ int s_cnt[LWE][kNb];
     __shared__ unsigned short s_off[LWE][kNb];
@@ -586,48 +593,48 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a) {
     if (MODE & OUT_DBL) {
         nx = (float)a.nrm[3 * oidx]; ny = (float)a.nrm[3 * oidx + 1]; nz = (float)a.nrm[3 * oidx + 2];
     }
+    const f2 nx2 = f2_splat(nx), ny2 = f2_splat(ny), nz2 = f2_splat(nz);
     const float rc2 = a.k.rc2;
+    const f2 rc22 = f2_splat(rc2);
+    const float2* px = (const float2*)ps;
+    const float2* py = (const float2*)(ps + ld);
+    const float2* pz = (const float2*)(ps + 2 * ld);
+    const float2* gx = (const float2*)gs;
+    const float2* gy = (const float2*)(gs + ld);
+    const float2* gz = (const float2*)(gs + 2 * ld);
     PairAcc2 acc;
     for (int ci = 0; ci < nc; ++ci) {
-        const int st = s_cst[wid][ci], cnt = s_cnt[wid][ci], oi = s_off[wid][ci];
+        const int st = s_cst[wid][ci], end = st + s_cnt[wid][ci], oi = s_off[wid][ci];
         // target position in the frame of this source cell's corner
-        const float tx = ox - (float)(oi % side - R) * a.k.hx;
-        const float ty = oy - (float)((oi / side) % side - R) * a.k.hy;
-        const float tz = oz - (float)(oi / (side * side) - R) * a.k.hz;
-        for (int i0 = 0; i0 < cnt; i0 += kChunk) {
-            float d[2][4];
-            int sv[2];
-            bool h[2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int i = i0 + 32 * j + lane;
-                h[j] = false;
-                sv[j] = st;
-                d[j][0] = d[j][1] = d[j][2] = 0.f;
-                d[j][3] = rc2;
-                if (i < cnt) {
-                    sv[j] = st + i;
-                    const float4 p = a.src.pos[sv[j]];
-                    d[j][0] = tx - p.x;
-                    d[j][1] = ty - p.y;
-                    d[j][2] = tz - p.z;
-                    const float q2 = d[j][0] * d[j][0] + d[j][1] * d[j][1] + d[j][2] * d[j][2];
-                    h[j] = q2 < rc2;
-                    if (h[j] && q2 < a.near2) {
-                        const int4 v = a.qvs[sv[j]];
-                        h[j] = !(v.x == oidx || v.y == oidx || v.z == oidx);
-                    }
-                    if (h[j]) d[j][3] = q2;      // misses keep an in-range r^2
-                }
+        const f2 tx = f2_splat(ox - (float)(oi % side - R) * a.k.hx);
+        const f2 ty = f2_splat(oy - (float)((oi / side) % side - R) * a.k.hy);
+        const f2 tz = f2_splat(oz - (float)(oi / (side * side) - R) * a.k.hz);
+        for (int i0 = st & ~1; i0 < end; i0 += kChunk) {
+            const int i = i0 + 2 * lane;          // even: candidates i and i + 1
+            const int h = i >> 1;
+            const float2 qx = px[h], qy = py[h], qz = pz[h];
+            const f2 dx = tx - f2_make(qx.x, qx.y), dy = ty - f2_make(qy.x, qy.y),
+                     dz = tz - f2_make(qz.x, qz.y);
+            f2 r2 = fma2(dz, dz, fma2(dy, dy, dx * dx));
+            float r0, r1;
+            f2_split(r2, r0, r1);
+            bool h0 = i >= st && i < end && r0 < rc2;
+            bool h1 = i + 1 >= st && i + 1 < end && r1 < rc2;
+            if (h0 && r0 < a.near2) {
+                const int4 v = a.qvs[i];
+                h0 = !(v.x == oidx || v.y == oidx || v.z == oidx);
             }
-            if (!__any_sync(0xffffffffu, h[0] || h[1])) continue;
-            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-            if (h[0]) g0 = a.src.g[sv[0]];
-            if (h[1]) g1 = a.src.g[sv[1]];
-            pair_terms2<MODE>(a.k, f2_make(d[0][0], d[1][0]), f2_make(d[0][1], d[1][1]),
-                              f2_make(d[0][2], d[1][2]), f2_make(d[0][3], d[1][3]),
-                              f2_make(g0.x, g1.x), f2_make(g0.y, g1.y), f2_make(g0.z, g1.z),
-                              f2_splat(nx), f2_splat(ny), f2_splat(nz), acc);
+            if (h1 && r1 < a.near2) {
+                const int4 v = a.qvs[i + 1];
+                h1 = !(v.x == oidx || v.y == oidx || v.z == oidx);
+            }
+            if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+            const f2 m = f2_make(h0 ? 1.f : 0.f, h1 ? 1.f : 0.f);
+            r2 = fma2(m, r2 - rc22, rc22);        // misses: an in-range r^2
+            const float2 wx = gx[h], wy = gy[h], wz = gz[h];
+            pair_terms2<MODE>(a.k, dx, dy, dz, r2, m * f2_make(wx.x, wx.y),
+                              m * f2_make(wy.x, wy.y), m * f2_make(wz.x, wz.y), nx2, ny2, nz2,
+                              acc);
         }
     }
     float ux = f2_sum(acc.ux), uy = f2_sum(acc.uy), uz = f2_sum(acc.uz);
@@ -643,6 +650,16 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a) {
         o[1] = a.k.fU * uy;
         o[2] = a.k.fU * uz;
     }
+}
+
+// structure-of-arrays copy of n float4 (x, y, z, w): planes x, y, z of stride ld
+__global__ void k_to_soa(int n, const float4* __restrict__ in, float* __restrict__ out, size_t ld) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = in[i];
+    out[i] = v.x;
+    out[ld + i] = v.y;
+    out[2 * ld + i] = v.z;
 }
 
 // ----------------------------------- element rule, FP64-accurate in float pairs
@@ -864,6 +881,11 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     else launch_kind<T, KIND, 2>(a, mode, st);
 }
 
+cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st) {
+    if (n > 0) k_to_soa<<<(n + 255) / 256, 256, 0, st>>>(n, (const float4*)in, out, ld);
+    return cudaGetLastError();
+}
+
 cudaError_t to_float_pairs(int n, const void* in, void* out, cudaStream_t st) {
     if (n > 0)
         k_to_float_pairs<<<(n + 255) / 256, 256, 0, st>>>(n, (const double*)in, (float4*)out);
@@ -874,28 +896,32 @@ template <typename T>
 cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const SortedSources<T>& src,
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
-                           cudaStream_t st, const void* ff_pos, const void* ff_g) {
+                           cudaStream_t st, const void* aux_pos, const void* aux_g,
+                           size_t aux_ld) {
     if (tgt.n <= 0) return cudaSuccess;
     // targets: the mesh nodes in cell order, so the warps of a block mostly
     // scan the same candidate cells (L1 reuse); output in caller order
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
                    tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
     if constexpr (sizeof(T) == 4) {
+        if (!aux_pos || !aux_g || aux_ld == 0) return cudaErrorInvalidValue;
+        const float* ps = (const float*)aux_pos;
+        const float* gs = (const float*)aux_g;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
         if (cg.reach == 3) {
-            if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a);
-            else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a);
+            if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
+            else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
         } else {
-            if (layer == 0) k_local_elem32<OUT_U, 2><<<g, b, 0, st>>>(a);
-            else k_local_elem32<OUT_DBL, 2><<<g, b, 0, st>>>(a);
+            if (layer == 0) k_local_elem32<OUT_U, 2><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
+            else k_local_elem32<OUT_DBL, 2><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
         }
         return cudaGetLastError();
     }
     dim3 b(LW * 32), g((tgt.n + LW - 1) / LW);
     if constexpr (sizeof(T) == 8) {
-        if (ff_pos && ff_g) {
-            const float4* fp = (const float4*)ff_pos;
-            const float4* fg = (const float4*)ff_g;
+        if (aux_pos && aux_g) {
+            const float4* fp = (const float4*)aux_pos;
+            const float4* fg = (const float4*)aux_g;
             if (cg.reach == 3) {
                 if (layer == 0) k_local_elem_ff<OUT_U, 3><<<g, b, 0, st>>>(a, fp, fg);
                 else k_local_elem_ff<OUT_DBL, 3><<<g, b, 0, st>>>(a, fp, fg);
@@ -944,7 +970,7 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
     template cudaError_t local_sum_elem<T>(const GridGeom&, const CellGrid&,                  \
                                            const SortedSources<T>&, const int4*, double,        \
                                            const SortedSources<T>&, const double*, int, T*, int, \
-                                           cudaStream_t, const void*, const void*);
+                                           cudaStream_t, const void*, const void*, size_t);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

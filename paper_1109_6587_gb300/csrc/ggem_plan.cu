@@ -249,6 +249,7 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
             GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qp_perm, P->d_qv, (const v4_t<T>*)P->d_qw, q,
                                     8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
+        if (elem && !P->fp64) GG_CUDA(to_soa(P->n_qp, P->d_qg, P->d_qg_soa, P->soa_ld, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
@@ -283,7 +284,9 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         qs.n = P->n_qp;
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
-                                      P->d_nrm, layer, loc, 3, ls, P->d_qp_ff, P->d_qg_ff));
+                                      P->d_nrm, layer, loc, 3, ls,
+                                      P->fp64 ? P->d_qp_ff : (void*)P->d_qp_soa,
+                                      P->fp64 ? P->d_qg_ff : (void*)P->d_qg_soa, P->soa_ld));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
@@ -570,6 +573,13 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             GG_CUDA(cudaMalloc(&P->d_qp_ff, cq * 2 * sizeof(float4) + 32));
             GG_CUDA(cudaMalloc(&P->d_qg_ff, cq * 2 * sizeof(float4) + 32));
         }
+        if (!P->fp64) {                    // planes padded by one 64-point step, zeroed
+            P->soa_ld = (cq + 64 + 63) / 64 * 64;
+            dalloc(P, &P->d_qp_soa, 3 * P->soa_ld);
+            dalloc(P, &P->d_qg_soa, 3 * P->soa_ld);
+            GG_CUDA(cudaMemset(P->d_qp_soa, 0, 3 * P->soa_ld * sizeof(float)));
+            GG_CUDA(cudaMemset(P->d_qg_soa, 0, 3 * P->soa_ld * sizeof(float)));
+        }
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
     GG_CUDA(cudaEventCreate(&P->ev1));
@@ -608,7 +618,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_pnodes, P->d_rc, P->d_rscale, P->d_mref, P->d_cx0, P->d_cdf,
                     P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
-                    P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff};
+                    P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
+                    P->d_qg_soa};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -747,6 +758,7 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 GG_CUDA(build_cells<float>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                            P->d_qp_start, P->d_cursor, P->d_qp_cell,
                                            P->d_qp_perm, (float4*)P->d_qp_pos, st));
+                GG_CUDA(to_soa(nq, P->d_qp_pos, P->d_qp_soa, P->soa_ld, st));
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
             P->n_qp = nq;
