@@ -208,12 +208,26 @@ enum { AU = 0, AV = 1, AW = 2, AP = 3, AT = 4 };
 // Thread (mode, part r, parity p).  FP64 is used where App. C's boundary-value
 // solve needs it -- the tau recurrences and the influence matrix; right-hand
 // sides, derivatives and combinations run in T.
+// SMEM: the mode scratch (SA, SX) lives in the block's shared memory, one warp
+// per block and its 8 modes fastest ([row][8]), so the sequential recurrences
+// wait on shared-memory latency instead of L2; otherwise it is the global
+// scratch ([row][nmodes]).
 template <typename T>
-__global__ void __launch_bounds__(128) k_ks(KSArgs<T> a) {
+__host__ __device__ constexpr size_t ks_coef_doubles(int Ny) {
+    return ((size_t)3 * Ny * sizeof(T) + 7) / 8;
+}
+template <typename T>
+__host__ __device__ constexpr size_t ks_smem_bytes(int Ny) {
+    return (ks_coef_doubles<T>(Ny) + (((size_t)5 * 2 * Ny * 8 * sizeof(T) + 7) / 8) +
+            (size_t)3 * 2 * Ny * 8) * sizeof(double);
+}
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
     const GridGeom& geo = a.geo;
     const int nkx = geo.nkx, nm = geo.Nz * nkx;
     const int Ny = geo.Ny, N = Ny - 1;
-    extern __shared__ double smc[];            // coef table [3][Ny] as T
+    extern __shared__ double smc[];            // coef table [3][Ny] as T (+ mode scratch)
     T* ct = reinterpret_cast<T*>(smc);
     for (int e = threadIdx.x; e < 3 * Ny; e += blockDim.x) ct[e] = (T)a.coef[e];
     __syncthreads();
@@ -226,11 +240,25 @@ __global__ void __launch_bounds__(128) k_ks(KSArgs<T> a) {
     const int m = (blockIdx.x * blockDim.x + threadIdx.x) / 32 * 8 + mm;
     if (m >= nm) return;                        // warp-uniform (nm is a multiple of 8)
     const size_t sm = nm;
+    T* saBase;
+    double* sxBase;
+    size_t sst;                                 // stride between scratch rows
+    if (SMEM) {
+        T* sa = reinterpret_cast<T*>(smc + ks_coef_doubles<T>(Ny));
+        double* sx = smc + ks_coef_doubles<T>(Ny) + ((size_t)5 * 2 * Ny * 8 * sizeof(T) + 7) / 8;
+        saBase = sa + mm;
+        sxBase = sx + mm;
+        sst = 8;
+    } else {
+        saBase = a.SA + m;
+        sxBase = a.SX + m;
+        sst = sm;
+    }
     auto SA = [&](int A, int R, int n) -> T& {
-        return a.SA[((size_t)(A * 2 + R) * Ny + n) * sm + m];
+        return saBase[((size_t)(A * 2 + R) * Ny + n) * sst];
     };
     auto SX = [&](int A, int R, int n) -> double& {
-        return a.SX[((size_t)(A * 2 + R) * Ny + n) * sm + m];
+        return sxBase[((size_t)(A * 2 + R) * Ny + n) * sst];
     };
     auto TH = [&](int A, int n) -> double { return a.thom[((size_t)A * Ny + n) * sm + m]; };
     const int nout = ((a.out_sel & 1) ? 3 : 0) + ((a.out_sel & 2) ? 6 : 0);
@@ -489,9 +517,31 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
     T* SA = (T*)scratch;
     double* SX = (double*)((char*)scratch + ((naux * sizeof(T) + 255) & ~(size_t)255));
     KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, SA, SX, out_sel, ocoef};
-    long threads = ((long)(nm + 7) / 8) * 32;
+    long warps = (long)(nm + 7) / 8;
+    // mode scratch in shared memory when a warp's share fits the opt-in limit
+    static int optin = -1;                      // per process: one device per plan
+    if (optin < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+            optin = 0;
+    }
+    const size_t bytes = ks_smem_bytes<T>(geo.Ny);
+    if (bytes <= (size_t)optin) {
+        static size_t granted = 0;              // per instantiation: the limit set so far
+        if (bytes > granted) {
+            cudaError_t e = cudaFuncSetAttribute(k_ks<T, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bytes);
+            if (e != cudaSuccess) return e;
+            granted = bytes;
+        }
+        k_ks<T, true><<<(unsigned)warps, 32, bytes, st>>>(a);
+        return cudaGetLastError();
+    }
     size_t smem = (size_t)3 * geo.Ny * sizeof(double);
-    k_ks<T><<<(unsigned)((threads + 127) / 128), 128, smem, st>>>(a);
+    k_ks<T, false><<<(unsigned)((warps * 32 + 127) / 128), 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 

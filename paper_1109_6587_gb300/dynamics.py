@@ -17,17 +17,27 @@ import time
 
 import numpy as np
 
+from .ggem import GGEMError
+
 
 class Suspension:
     """Capsules on a plan: the plan holds the mesh (moved by every step), the
     membrane reference is the mesh given at construction, lambda per particle."""
 
     def __init__(self, plan, particle, n_particles, lam, ca=0.3, radius=1.0, flow="shear",
-                 strength=1.0, mu=1.0, h_gap=0.05, vol_threshold=1e-4):
+                 strength=1.0, mu=1.0, h_gap=0.05, vol_threshold=1e-4, tri=None, x_ref=None,
+                 v0=None):
+        """tri (optional): the mesh's triangles, kept for checkpoints; x_ref and
+        v0 (optional): membrane reference and initial volumes when resuming
+        (default: the plan's current mesh and its volumes)."""
         self.P = plan
         self.particle = np.asarray(particle)
         self.n_particles = int(n_particles)
-        self.lam_nodes = np.ascontiguousarray(np.asarray(lam, dtype=np.float64)[self.particle])
+        self.lam = np.asarray(lam, dtype=np.float64)
+        self.lam_nodes = np.ascontiguousarray(self.lam[self.particle])
+        self.tri = None if tri is None else np.asarray(tri, dtype=np.int32)
+        self.mu = mu
+        self.h_gap_factor = h_gap
         self.ca, self.radius, self.flow, self.strength = ca, radius, flow, strength
         # Ca = mu gamma_dot a / G with gamma_dot the shear rate (shear flow) or
         # the wall shear rate 4 U0 / H (pressure-driven flow)
@@ -36,10 +46,51 @@ class Suspension:
         self.h_gap = h_gap * radius
         self.vol_threshold = vol_threshold
         plan.mesh_particles(self.particle, self.n_particles)
-        plan.membrane_reference(plan.mesh_positions())
-        self.v0 = plan.particle_volumes()
+        self.x_ref = plan.mesh_positions() if x_ref is None else np.asarray(x_ref, np.float64)
+        plan.membrane_reference(np.ascontiguousarray(self.x_ref))
+        self.v0 = plan.particle_volumes() if v0 is None else np.asarray(v0, np.float64)
         self.q = np.zeros((plan.n_nodes, 3))
         self.t = 0.0
+        self.steps = 0
+
+    # ------------------------------------------------------------ checkpoints
+    def save(self, path):
+        """Checkpoint (numpy .npz): node positions, triangles, membrane
+        reference, the density that seeds the next solve, initial volumes,
+        time, step count, viscosity ratios, particle ids and the run's
+        parameters; plus the learned model when the plan holds one (its Adam
+        moments are not kept: a resumed run trains afresh)."""
+        if self.tri is None:
+            raise ValueError("checkpoints need the triangles (pass tri= at construction)")
+        extra = {}
+        try:
+            extra["mlp"] = self.P.mlp_save()
+        except GGEMError:                 # the plan holds no model
+            pass
+        np.savez(path, x=self.P.mesh_positions(), tri=self.tri, x_ref=self.x_ref,
+                 q=np.asarray(self.q.cpu() if hasattr(self.q, "cpu") else self.q),
+                 v0=self.v0, t=self.t, steps=self.steps, lam=self.lam, particle=self.particle,
+                 params=np.array([self.ca, self.radius, self.strength, self.mu,
+                                  self.h_gap_factor, self.vol_threshold]),
+                 flow=np.array(self.flow), **extra)
+
+    @classmethod
+    def resume(cls, plan, path):
+        """A suspension continuing a checkpoint on `plan` (a plan for the same
+        box with room for the mesh): the next step reproduces the one the
+        saved run would have taken."""
+        z = np.load(path)
+        ca, radius, strength, mu, h_gap, vol_threshold = (float(v) for v in z["params"])
+        plan.mesh_set(np.ascontiguousarray(z["x"]), np.ascontiguousarray(z["tri"]))
+        if "mlp" in z:
+            plan.mlp_load(z["mlp"])
+        S = cls(plan, z["particle"], len(z["lam"]), z["lam"], ca=ca, radius=radius,
+                flow=str(z["flow"]), strength=strength, mu=mu, h_gap=h_gap,
+                vol_threshold=vol_threshold, tri=z["tri"], x_ref=z["x_ref"], v0=z["v0"])
+        S.q = np.array(z["q"])
+        S.t = float(z["t"])
+        S.steps = int(z["steps"])
+        return S
 
     def dt(self):
         return 0.5 * self.ca * self.P.min_separation() / (self.radius * self.gamma)
@@ -55,6 +106,7 @@ class Suspension:
         passes = self.P.volume_correct(self.v0, self.vol_threshold, 10)
         moves = self.P.overlap_correct(self.h_gap)
         self.t += dt
+        self.steps += 1
         return {"dt": dt, "iters": its, "relres": rr, "volume_passes": passes,
                 "overlap_moves": moves, "seconds": time.perf_counter() - t0}
 
