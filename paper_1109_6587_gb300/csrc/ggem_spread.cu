@@ -3,17 +3,19 @@
 //   f(node) = - sum_s g_s rho_g(node - x_s*),   |node - x_s*| < r_cut,
 //   rho_g(r) = alpha^3 pi^{-3/2} exp(-alpha^2 r^2) (5/2 - alpha^2 r^2).
 //
-// Output-stationary: a block owns a tile of TS x TS grid columns (x, z) over a
-// slab of NS y-planes, accumulates in shared memory every source whose r_cut
-// ball reaches those nodes, and writes them once with plain stores (no global
-// atomics, no clearing pass).  One warp per candidate source: lane l tests
-// column i0 + l and row k0 + l once (ballot), then the warp walks only the
-// (column, row) pairs inside the source's disc, for the slab's planes.  The
+// Source-parallel: a warp takes one sorted source (FP64, k_spread_scatter) or
+// two neighbouring ones (FP32, k_spread_pair: the union of their stencils,
+// both weights per node, one reduction with their sum), lists the columns,
+// rows and planes of its stencil, and adds the weights into an interleaved
+// [Ny][Nz][Nx][4] accumulation grid with float4 / double vector reductions in
+// L2; k_deinterleave then writes the planar [Ny][3][Nz][Nx] forcing.  The
 // Gaussian factor is separable, exp(-a^2 r^2) = exp(-a^2 dx^2)
 // exp(-a^2 dy^2) exp(-a^2 dz^2), so each source costs one exponential per
-// column, row and plane.  Displacements come from per-source descriptors
-// (integer grid offsets plus small remainders, built once per source set), so
-// the kernel runs in T only: no FP64 instruction, accurate in large boxes.
+// column, row and plane (the fast Gaussian gridding idea), the remaining
+// work per node being a few multiplies.  Displacements come from per-source
+// descriptors (integer grid offsets plus small remainders, built once per
+// source set), so the kernel runs in T only: no FP64 instruction, accurate in
+// large boxes.
 #include "ggem_internal.cuh"
 
 namespace ggem {
