@@ -276,8 +276,7 @@ cudaError_t cheb_apply_tc(int Ny, const void* prep, const float* in, float* out,
     if (smem > 227 * 1024 || MB > 2) return cudaErrorNotSupported;
     uint32_t tcols = 32;
     while (tcols < (uint32_t)(MB * NT)) tcols <<= 1;
-    cudaError_t e = cudaFuncSetAttribute(k_cheb_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = grant_max_smem((const void*)k_cheb_tc);
     if (e != cudaSuccess) return e;
     const long ntiles = (cols + NT - 1) / NT;
     // two CTAs per SM when their shared memory fits (one stages while the other

@@ -158,12 +158,10 @@ static cudaError_t fft_x(const GridGeom& geo, T* data, int nplanes, const void* 
     const c2_t<T>* tpost = tw + M / 2;
     unsigned nb = (unsigned)((nrows + R - 1) / R);
     if (inv) {
-        cudaFuncSetAttribute(k_fft_x_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        grant_max_smem((const void*)k_fft_x_c2r<T>);
         k_fft_x_c2r<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nrows, M, logM, tw, tpost, R);
     } else {
-        cudaFuncSetAttribute(k_fft_x_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        grant_max_smem((const void*)k_fft_x_r2c<T>);
         k_fft_x_r2c<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nrows, M, logM, tw, tpost, R);
     }
     return cudaGetLastError();
@@ -176,7 +174,7 @@ static cudaError_t fft_z(const GridGeom& geo, T* data, int nplanes, const void* 
     int TB = min(nkx, 8);
     size_t smem = (size_t)TB * Nz * sizeof(c2_t<T>);
     unsigned nb = (unsigned)((long)nplanes * ((nkx + TB - 1) / TB));
-    cudaFuncSetAttribute(k_fft_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    grant_max_smem((const void*)k_fft_z<T>);
     k_fft_z<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nkx, Nz, logNz, (const c2_t<T>*)tw_z, TB,
                                       inv);
     return cudaGetLastError();
@@ -241,7 +239,7 @@ cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaS
         if (e != cudaErrorNotSupported) return e;
     }
     size_t smem = (size_t)Ny * Ny * sizeof(T);
-    cudaFuncSetAttribute(k_cheb<T, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    grant_max_smem((const void*)k_cheb<T, 24>);
     k_cheb<T, 24><<<(unsigned)((cols + 255) / 256), 256, smem, st>>>(Ny, M, in, out, cols);
     return cudaGetLastError();
 }

@@ -6,9 +6,32 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "ggem.h"
 
 namespace ggem {
+
+// Lets `kernel` use up to the device's opt-in shared memory per block.  Set
+// once per kernel under a lock, so launches from several host threads (plans
+// of different sizes) never lower each other's limit; occupancy still follows
+// each launch's own dynamic size.  Returns the status of that one call.
+inline cudaError_t grant_max_smem(const void* kernel) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, cudaError_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(kernel);
+    if (it != done.end()) return it->second;
+    int dev = 0, v = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    done[kernel] = e;
+    return e;
+}
 
 // ------------------------------------------------------------ small types
 template <typename T> struct V4;

@@ -519,24 +519,14 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
     KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, SA, SX, out_sel, ocoef};
     long warps = (long)(nm + 7) / 8;
     // mode scratch in shared memory when a warp's share fits the opt-in limit
-    static int optin = -1;                      // per process: one device per plan
-    if (optin < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
-            cudaSuccess)
-            optin = 0;
-    }
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        grant_max_smem((const void*)k_ks<T, true>) != cudaSuccess)
+        optin = 0;
     const size_t bytes = ks_smem_bytes<T>(geo.Ny);
     if (bytes <= (size_t)optin) {
-        static size_t granted = 0;              // per instantiation: the limit set so far
-        if (bytes > granted) {
-            cudaError_t e = cudaFuncSetAttribute(k_ks<T, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
-            if (e != cudaSuccess) return e;
-            granted = bytes;
-        }
         k_ks<T, true><<<(unsigned)warps, 32, bytes, st>>>(a);
         return cudaGetLastError();
     }

@@ -203,6 +203,60 @@ def capsules_1000(seed=0):
     return suspension(1000, box_1000_capsules(), level=3, radius=1.0, seed=seed)
 
 
+# Evans-Fung biconcave profile of a red blood cell in units of its radius R0:
+# half-thickness h(rho) = (R0/2) sqrt(1 - rho^2) (C0 + C1 rho^2 + C2 rho^4),
+# rho the distance from the axis over R0 (Evans and Fung 1972).
+EVANS_FUNG = (0.2072, 2.0026, -1.1228)
+
+
+def rbc_mesh(level=3, radius=1.0):
+    """Biconcave capsule: the icosphere's vertices mapped onto the Evans-Fung
+    profile about the y axis (x, z scaled by the radius, y replaced by the
+    signed half-thickness at that distance from the axis).  The map keeps the
+    triangles' orientation (outward normals)."""
+    v, t = icosphere(level)
+    rho2 = np.clip(v[:, 0] ** 2 + v[:, 2] ** 2, 0.0, 1.0)
+    c0, c1, c2 = EVANS_FUNG
+    h = 0.5 * radius * np.sqrt(1.0 - rho2) * (c0 + c1 * rho2 + c2 * rho2 * rho2)
+    x = np.stack([radius * v[:, 0], np.sign(v[:, 1]) * h, radius * v[:, 2]], 1)
+    return x, t
+
+
+def random_rotations(n, rng):
+    """n uniformly random rotation matrices (QR of Gaussian matrices, sign
+    fixed so that the factor is a proper rotation)."""
+    out = np.empty((n, 3, 3))
+    for k in range(n):
+        q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+        q = q * np.sign(np.diag(r))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        out[k] = q
+    return out
+
+
+def box_rbc_4000():
+    """150 x [-15, 15] x 150 slit, 512 x 129 x 512 grid."""
+    return Box(Lx=150.0, Lz=150.0, W=30.0, y0=-15.0, Nx=512, Ny=129, Nz=512)
+
+
+def rbc_4000(seed=0, level=3, radius=1.0):
+    """4000 biconcave capsules x 642 nodes (2,568,000 points), each randomly
+    oriented, centres placed as for spheres of the cell's radius (which
+    bounds it) with the minimum gap 0.05a."""
+    box = box_rbc_4000()
+    rng = np.random.default_rng(seed)
+    centres = place_centres(4000, box, radius, rng)
+    rot = random_rotations(len(centres), rng)
+    v, t = rbc_mesh(level, radius)
+    nb = v.shape[0]
+    x = (centres[:, None, :] + np.einsum("pij,nj->pni", rot, v)).reshape(-1, 3)
+    tri = (t[None, :, :] + nb * np.arange(len(centres))[:, None, None]).reshape(-1, 3)
+    part = np.repeat(np.arange(len(centres), dtype=np.int32), nb)
+    return Suspension(box, np.ascontiguousarray(x), tri.astype(np.int32), part, centres,
+                      radius)
+
+
 # ---- Fredholm-solve inputs and emulated time steps ------------------------
 
 def bie_rhs(susp: Suspension, lam=5.0, gamma=1.0, seed=0, step=0, mu=1.0):
