@@ -13,6 +13,10 @@ solve at true relative residual 1e-6, per emulated time step, for the plain
 FP64 solve, the mixed solve and the mixed solve with the learned warm start
 -- is measured on the same workload and reported under "solve".
 
+Other workloads (--workload capsules1000 or rbc4000: 642,000 and 2,568,000
+points) measure the same step at the larger configurations; the pair counts of
+their roofline are taken on a sample of 20,000 targets.
+
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
 GPU (the evaluation is one problem per GPU; no collective), value = sum of
@@ -45,19 +49,35 @@ def _args():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_emulated"])
     ap.add_argument("--quadrature", default="element", choices=["nodal", "element"])
+    ap.add_argument("--workload", default="capsules100",
+                    choices=["capsules100", "capsules1000", "rbc4000"],
+                    help="capsules100 (default, the benchmark configuration), capsules1000 "
+                         "(642,000 points) or rbc4000 (2,568,000 points); the CPU baseline "
+                         "runs on the default only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     return ap.parse_args()
 
 
-def _workload():
+WORKLOADS = {
+    "capsules100": ("capsules_100",
+                    "100 spherical capsules x 642 nodes (64,200 points), slit 40 x [-5,5] x 40"),
+    "capsules1000": ("capsules_1000",
+                     "1000 spherical capsules x 642 nodes (642,000 points), slit 80 x [-10,10] x 80"),
+    "rbc4000": ("rbc_4000",
+                "4000 biconcave capsules x 642 nodes (2,568,000 points), slit 150 x [-15,15] x 150"),
+}
+
+
+def _workload(args=None):
     from paper_1109_6587_gb300 import workloads as W
-    return W.capsules_100(seed=0)
+    name = "capsules100" if args is None else args.workload
+    return getattr(W, WORKLOADS[name][0])(seed=0)
 
 
 def _config(susp, args):
     b = susp.box
-    return {"workload": "100 spherical capsules x 642 nodes (64,200 points), slit 40 x [-5,5] x 40",
+    return {"workload": WORKLOADS[args.workload][1],
             "n_points": int(susp.x.shape[0]), "grid": [b.Nx, b.Ny, b.Nz],
             "precision": args.precision, "quadrature": args.quadrature,
             "step": "single-layer + double-layer matvec",
@@ -125,16 +145,33 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+SAMPLE_ABOVE = 100_000      # larger workloads count pairs on a sample of targets
+SAMPLE_TARGETS = 20_000
+
+
+def _target_sample(n):
+    """All targets, or a seeded sample of SAMPLE_TARGETS of them for large
+    workloads; returns (indices, scale to all targets)."""
+    if n <= SAMPLE_ABOVE:
+        return np.arange(n), 1.0
+    idx = np.sort(np.random.default_rng(7).choice(n, SAMPLE_TARGETS, replace=False))
+    return idx, n / SAMPLE_TARGETS
+
+
 def _pair_count(susp, rcut):
-    """Number of (target, source) pairs with 0 < r < r_cut (minimum image in x, z)."""
+    """Number of (target, source) pairs with 0 < r < r_cut (minimum image in x,
+    z); counted on a sample of targets for large workloads."""
     from scipy.spatial import cKDTree
     b = susp.box
     x = susp.x.copy()
     x[:, 0] %= b.Lx
     x[:, 2] %= b.Lz
     x[:, 1] -= b.y0
-    tree = cKDTree(x, boxsize=[b.Lx, 4 * b.W + 4 * rcut, b.Lz])
-    return 2 * len(tree.query_pairs(rcut, output_type="ndarray"))
+    box = [b.Lx, 4 * b.W + 4 * rcut, b.Lz]
+    idx, scale = _target_sample(len(x))
+    tree = cKDTree(x, boxsize=box)
+    # every sampled target counts itself once at r = 0
+    return int(scale * (cKDTree(x[idx], boxsize=box).count_neighbors(tree, rcut) - len(idx)))
 
 
 def _quad_points(susp):
@@ -163,10 +200,13 @@ def _elem_pair_count(susp, rcut):
         a[:, 1] -= b.y0
         return a
     box = [b.Lx, 4 * b.W + 4 * rcut, b.Lz]
+    idx, scale = _target_sample(len(susp.x))
     tq = cKDTree(wrap(qx), boxsize=box)
-    tn = cKDTree(wrap(susp.x), boxsize=box)
+    tn = cKDTree(wrap(susp.x[idx]), boxsize=box)
     total = int(tn.count_neighbors(tq, rcut))
-    return total - 16 * 3 * len(susp.tri)
+    # the 16 points of each triangle containing a (sampled) node are the polar rule's
+    own = np.bincount(susp.tri.ravel(), minlength=len(susp.x))[idx].sum()
+    return int(scale * (total - 16 * own))
 
 
 def aggregate(t_ms, steps, n_points, world, device):
@@ -190,7 +230,7 @@ def run_mine(args, rank, world):
 
     torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
     dev = torch.device("cuda")
-    susp = _workload()
+    susp = _workload(args)
     n = susp.x.shape[0]
     P = ggem.Plan.for_box(susp.box, precision=args.precision, quadrature=args.quadrature,
                           max_points=n, max_tris=susp.tri.shape[0])
@@ -472,7 +512,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        susp = _workload()
+        susp = _workload(args)
         times = []
         for _ in range(args.warmup):
             pass       # the oracle has no warm-up state
@@ -512,7 +552,7 @@ def main():
         import torch
         line["solve"] = solve_metrics(args, res["susp"], torch.device("cuda"))
         line["dynamics"] = dynamics_metrics(args, res["susp"], torch.device("cuda"))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "capsules100":
         line["cpu_baseline"] = cpu_baseline(res["susp"], args)
     if world > 1:
         import torch.distributed as dist
