@@ -13,9 +13,10 @@
 
 namespace ggem {
 
-// Lets `kernel` use up to the device's opt-in shared memory per block.  Set
-// once per kernel under a lock, so launches from several host threads (plans
-// of different sizes) never lower each other's limit; occupancy still follows
+// Lets `kernel` use as much dynamic shared memory as the device allows a block
+// (the opt-in limit less the kernel's static shared memory).  Set once per
+// kernel under a lock, so launches from several host threads (plans of
+// different sizes) never lower each other's limit; occupancy still follows
 // each launch's own dynamic size.  Returns the status of that one call.
 inline cudaError_t grant_max_smem(const void* kernel) {
     static std::mutex mu;
@@ -24,11 +25,14 @@ inline cudaError_t grant_max_smem(const void* kernel) {
     auto it = done.find(kernel);
     if (it != done.end()) return it->second;
     int dev = 0, v = 0;
+    cudaFuncAttributes fa;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 v - (int)fa.sharedSizeBytes);
     done[kernel] = e;
     return e;
 }

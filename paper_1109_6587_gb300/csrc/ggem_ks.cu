@@ -519,6 +519,7 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
     KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, SA, SX, out_sel, ocoef};
     long warps = (long)(nm + 7) / 8;
     // mode scratch in shared memory when a warp's share fits the opt-in limit
+    // (the kernel has no static shared memory)
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
