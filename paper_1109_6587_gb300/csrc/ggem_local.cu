@@ -324,17 +324,19 @@ __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f
         a.uz = fma2(B, dz, fma2(A, gz, a.uz));
     }
     if (MODE & OUT_DBL) {
-        // D = -6 ec/r^5 - c2 ex/r^4 - c3 ex/r^2,  E = c4 ex
+        // D = -6 ec/r^5 - c2 ex/r^4 - c3 ex/r^2 = ir2 (ir2 (-6 ec ir - c2 ex) - c3 ex),
+        // E = c4 ex; the update D xg xn d + E (d gn + g xn + n xg) regrouped as
+        // d (D xg xn + E gn) + g (E xn) + n (E xg)
         const f2 ir2 = ir * ir;
         const f2 t = fma2(f2_splat(-6.0f), ec * ir, f2_splat(-k.c2) * ex);
-        const f2 D = fma2(ir2 * ir2, t, f2_splat(-k.c3) * ex * ir2);
+        const f2 D = ir2 * fma2(ir2, t, f2_splat(-k.c3) * ex);
         const f2 E = f2_splat(k.c4) * ex;
         const f2 xn = fma2(dz, nz, fma2(dy, ny, dx * nx));
         const f2 gn = fma2(gz, nz, fma2(gy, ny, gx * nx));
-        const f2 Dxn = D * xg * xn;
-        a.ux = fma2(Dxn, dx, fma2(E, fma2(dx, gn, fma2(gx, xn, nx * xg)), a.ux));
-        a.uy = fma2(Dxn, dy, fma2(E, fma2(dy, gn, fma2(gy, xn, ny * xg)), a.uy));
-        a.uz = fma2(Dxn, dz, fma2(E, fma2(dz, gn, fma2(gz, xn, nz * xg)), a.uz));
+        const f2 cd = fma2(D * xg, xn, E * gn), cg = E * xn, cn = E * xg;
+        a.ux = fma2(dx, cd, fma2(gx, cg, fma2(nx, cn, a.ux)));
+        a.uy = fma2(dy, cd, fma2(gy, cg, fma2(ny, cn, a.uy)));
+        a.uz = fma2(dz, cd, fma2(gz, cg, fma2(nz, cn, a.uz)));
     }
 }
 
@@ -595,7 +597,6 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
     }
     const f2 nx2 = f2_splat(nx), ny2 = f2_splat(ny), nz2 = f2_splat(nz);
     const float rc2 = a.k.rc2;
-    const f2 rc22 = f2_splat(rc2);
     const float2* px = (const float2*)ps;
     const float2* py = (const float2*)(ps + ld);
     const float2* pz = (const float2*)(ps + 2 * ld);
@@ -629,12 +630,12 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
                 h1 = !(v.x == oidx || v.y == oidx || v.z == oidx);
             }
             if (!__any_sync(0xffffffffu, h0 || h1)) continue;
-            const f2 m = f2_make(h0 ? 1.f : 0.f, h1 ? 1.f : 0.f);
-            r2 = fma2(m, r2 - rc22, rc22);        // misses: an in-range r^2
+            // misses: zero strength and an in-range r^2 (selects, off the FMA pipe)
+            r2 = f2_make(h0 ? r0 : rc2, h1 ? r1 : rc2);
             const float2 wx = gx[h], wy = gy[h], wz = gz[h];
-            pair_terms2<MODE>(a.k, dx, dy, dz, r2, m * f2_make(wx.x, wx.y),
-                              m * f2_make(wy.x, wy.y), m * f2_make(wz.x, wz.y), nx2, ny2, nz2,
-                              acc);
+            pair_terms2<MODE>(a.k, dx, dy, dz, r2, f2_make(h0 ? wx.x : 0.f, h1 ? wx.y : 0.f),
+                              f2_make(h0 ? wy.x : 0.f, h1 ? wy.y : 0.f),
+                              f2_make(h0 ? wz.x : 0.f, h1 ? wz.y : 0.f), nx2, ny2, nz2, acc);
         }
     }
     float ux = f2_sum(acc.ux), uy = f2_sum(acc.uy), uz = f2_sum(acc.uz);
