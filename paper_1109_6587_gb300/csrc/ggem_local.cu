@@ -222,7 +222,7 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
 
 // Pair arithmetic of Eq. (local), shared by the local-sum kernels.
 // exp(-alpha^2 r^2) and erfc(alpha r) = exp(-x^2) erfcx(x) with the
-// polynomials of ggem_erfcx.cuh (FP32: degree 16; FP64: 8 pieces of degree 12,
+// polynomials of ggem_erfcx.cuh (FP32: degree 14; FP64: 8 pieces of degree 12,
 // coefficients in shared memory), so the pair needs one exponential and no
 // erfc call; the FP32 exponential is 2^(ke r^2).
 template <typename T> struct PairAcc {

@@ -1,9 +1,11 @@
 """The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the polynomials of
-ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff): degree 16 (FP32),
+ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff): degree 14 (FP32),
 8 pieces of degree 12 (FP64).  FP32:
 Its coefficients, read from the generated header, must approximate scipy's
-erfcx to 1e-8 relative in FP64 and to 4e-7 (a few FP32 ulps, like CUDA's
-erfcf) when evaluated in FP32 by the same Horner scheme."""
+erfcx to 2e-7 relative in FP64 (the approximation error is kept near the
+rounding error of the polynomial's own FP32 evaluation, ~2e-7, so neither
+dominates) and to 4e-7 (a few FP32 ulps, like CUDA's erfcf) when evaluated in
+FP32 by the same Horner scheme."""
 import pathlib
 import re
 
@@ -30,14 +32,14 @@ def _table64():
 
 def test_polynomial_error():
     c = _coefficients()
-    assert len(c) == 17
+    assert len(c) == 15
     x = np.linspace(0.0, 4.0, 100001)
     ref = special.erfcx(x)
     u = x / 2 - 1
     p = np.full_like(u, c[0])
     for a in c[1:]:
         p = p * u + a
-    assert np.abs(p / ref - 1).max() < 1e-8
+    assert np.abs(p / ref - 1).max() < 2e-7
     x32 = x.astype(np.float32)
     u32 = (x32 * np.float32(0.5) - np.float32(1)).astype(np.float32)
     p32 = np.full_like(u32, np.float32(c[0]))
