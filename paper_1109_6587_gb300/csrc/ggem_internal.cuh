@@ -252,7 +252,7 @@ struct ggem_plan {
     void* d_tc_fwd = nullptr;          // split-bf16 Chebyshev matrices (mixed plans)
     void* d_tc_inv = nullptr;
     int nsm = 0;                       // multiprocessors of the plan's device
-    cudaStream_t st2 = nullptr;        // second stream: local part beside the global part
+    cudaStream_t st2 = nullptr;        // second stream (greatest priority): the longer of local / global part
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double prof_ms[16] = {0};
     long prof_calls[16] = {0};

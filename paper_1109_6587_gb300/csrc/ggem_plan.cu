@@ -104,9 +104,9 @@ int nout_of(int sel) { return ((sel & 1) ? 3 : 0) + ((sel & 2) ? 6 : 0); }
 // Global part: wall data, spread, transforms, tau solves, inverse transforms.
 // The physical result is left in gridB as [Ny][nout][Nz][Nx].
 template <typename T>
-void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_sel) {
+void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_sel,
+                cudaStream_t st) {
     const GridGeom& geo = P->geo;
-    cudaStream_t st = P->st;
     T* A = (T*)P->d_gridA;
     T* B = (T*)P->d_gridB;
     T* Wl = (T*)P->d_wall;
@@ -170,7 +170,7 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
                              (const v4_t<T>*)P->d_tgt_pos, nullptr, mode, loc, stride, st));
     });
     int sel = (u ? 1 : 0) | (s ? 2 : 0);
-    run_global<T>(P, src, false, sel);
+    run_global<T>(P, src, false, sel, P->st);
     const double* xtt = tgt_is_src ? xs : xt;
     int nt = tgt_is_src ? n_src : n_tgt;
     int nout = nout_of(sel);
@@ -254,15 +254,21 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
     T* loc = (T*)P->d_local;
-    // The local part and the global part are independent until the combine:
-    // the local kernels run on the plan's second stream, forked after the
-    // strengths are gathered and joined before the interpolation (both on one
-    // stream when tracing, so that stage times stay separable).
+    // The local part and the global part are independent until the combine.
+    // The longer of the two -- the local sum under the element rule (~5x the
+    // global part), the global part's chain of short kernels with nodal
+    // sources -- runs on the plan's second stream, created with the device's
+    // greatest priority, so its blocks are scheduled first and the other part
+    // fills the SMs it leaves; forked after the strengths are gathered,
+    // joined before the interpolation (both on one stream when tracing, so
+    // that stage times stay separable).
     const bool overlap = !P->prof && P->st2;
-    cudaStream_t ls = overlap ? P->st2 : st;
+    cudaStream_t ls = overlap && elem ? P->st2 : st;
+    cudaStream_t gs = overlap && !elem ? P->st2 : st;
+    cudaStream_t side = overlap ? P->st2 : st;
     if (overlap) {
         GG_CUDA(cudaEventRecord(P->ev_fork, st));
-        GG_CUDA(cudaStreamWaitEvent(ls, P->ev_fork, 0));
+        GG_CUDA(cudaStreamWaitEvent(side, P->ev_fork, 0));
     }
     if (!elem) {
         stage(P, ST_LOCAL, 1, [&] {
@@ -293,9 +299,11 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
                                     P->d_adj_start, P->d_adj, q, P->rule, loc, 3, ls));
         });
     }
-    if (overlap) GG_CUDA(cudaEventRecord(P->ev_join, ls));
-    run_global<T>(P, src, true, layer == 0 ? 1 : 2);
-    if (overlap) GG_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
+    run_global<T>(P, src, true, layer == 0 ? 1 : 2, gs);
+    if (overlap) {
+        GG_CUDA(cudaEventRecord(P->ev_join, side));
+        GG_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
+    }
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
             // nodal form: remove the free-space global self term (4 alpha/sqrt(pi)) A_b q_b;
@@ -583,7 +591,11 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
     GG_CUDA(cudaEventCreate(&P->ev1));
-    GG_CUDA(cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;
+        GG_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        GG_CUDA(cudaStreamCreateWithPriority(&P->st2, cudaStreamNonBlocking, greatest));
+    }
     GG_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     GG_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     GG_CUDA(cudaDeviceSynchronize());
