@@ -322,8 +322,9 @@ def roofline(res, args):
         # element-rule kernel on this workload, from one ncu capture of that
         # launch (its ncu summary is kept with the profiles); other
         # configurations have no capture
-        traffic = (94.5e6 + 4.4e6) if (args.precision == "mixed"
-                                       and args.quadrature == "element") else None
+        traffic = (94.9e6 + 4.2e6) if (args.precision == "mixed"
+                                       and args.quadrature == "element"
+                                       and args.workload == "capsules100") else None
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
