@@ -14,6 +14,7 @@ Paper: Kumar & Graham, arXiv 1109.6587.  Steps, in the paper's order:
      Chebyshev tau (two top rows = wall conditions)    (bc_vel), (inf_mat), (cheb_sol)
   6. stress sigma^g = -p + mu (grad u + grad u^T) ..... Sec. 3.5.1
   7. 4th-order (5-point) Lagrange interpolation ....... Sec. 3.2.2
+     or the expansion summed at each point ............. Sec. 3.2.3, Eq. (u_expn)
   8. u = u^l + u^g ..................................... Eq. (tot_l_g)
 Boundary integral operators (Sec. 3.4, 3.5), the Fredholm solve (Sec. 5,
 restarted GMRES with modified Gram-Schmidt) and the rigid-particle solve
@@ -41,6 +42,11 @@ Readings (the paper is silent, ambiguous or garbled here):
     sigma/mu (Eq. (st_dbl)).
   * Element form: the global part and the wall data use the trapezoidal nodal
     strengths A_b q_b (Eq. (rhog_sum)); the local part uses the element rule.
+  * Spectral off-grid evaluation (Sec. 3.2.3 names the non-uniform FFT as the
+    way to exponential accuracy off the mesh without writing it out): the
+    value at a point is the trigonometric (x, z; Nyquist modes zero) times
+    Chebyshev (y, degree Ny - 1) expansion of the grid field summed there --
+    the quantity a non-uniform FFT approximates to its tolerance.
 """
 from __future__ import annotations
 
@@ -451,6 +457,35 @@ def interp(box, field, xt):
     return np.einsum("cnabd,nabd->nc", vals, w)
 
 
+def spectral_coefficients(box, field):
+    """Fourier (x, z) x Chebyshev (y) coefficients of grid fields [C, Ny, Nz, Nx]:
+    a[c, n, m, l] with field = sum a T_n(ybar) exp(i (k_l x + k_m z)) at the
+    grid nodes (Eq. (u_expn)); the Nyquist modes are zero, as in the solve."""
+    coef = np.fft.fft2(field, axes=(2, 3)) / (box.Nx * box.Nz)
+    _, _, nyq = mode_wavenumbers(box)
+    coef[:, :, nyq] = 0.0
+    return np.einsum("nj,cjzx->cnzx", cheb_forward(box.Ny), coef)
+
+
+def spectral_eval(box, field, xt):
+    """Evaluate grid fields [C, Ny, Nz, Nx] at points xt [n, 3] by summing their
+    expansion (Eq. (u_expn)) at each point: the exactly convergent off-mesh
+    evaluation of Sec. 3.2.3 (what a non-uniform FFT computes to its
+    tolerance).  T_n(ybar) = cos(n arccos ybar).  -> [n, C]."""
+    xt = _f64(xt)
+    a = spectral_coefficients(box, field)
+    KX, KZ, _ = mode_wavenumbers(box)
+    kx, kz = KX[0], KZ[:, 0]
+    n = np.arange(box.Ny)
+    out = np.empty((xt.shape[0], field.shape[0]))
+    for t, (x, y, z) in enumerate(xt):
+        yb = np.clip(2.0 * (y - box.y0) / box.W - 1.0, -1.0, 1.0)
+        Tn = np.cos(n * np.arccos(yb))
+        ex, ez = np.exp(1j * kx * x), np.exp(1j * kz * z)
+        out[t] = np.real(np.einsum("cnml,n,m,l->c", a, Tn, ez, ex, optimize=True))
+    return out
+
+
 # ------------------------------------------------------------- point forces
 
 _SYM6 = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
@@ -483,8 +518,18 @@ def global_fields(box, xs, g, mu=1.0, alpha=None, rcut=None, want_stress=False):
     return global_solve(box, f, gb, gt, mu, want_stress)
 
 
+def evaluate(box, field, xt, offgrid="lagrange"):
+    """Grid fields at off-grid points: 5-point Lagrange interpolation (Sec. 3.2.2)
+    or, with offgrid="spectral", the expansion summed at each point (Sec. 3.2.3)."""
+    if offgrid == "spectral":
+        return spectral_eval(box, field, xt)
+    if offgrid != "lagrange":
+        raise ValueError("offgrid must be 'lagrange' or 'spectral'")
+    return interp(box, field, xt)
+
+
 def point_forces(box, xs, g, xt=None, mu=1.0, alpha=None, rcut=None,
-                 want_u=True, want_sig=False):
+                 want_u=True, want_sig=False, offgrid="lagrange"):
     """GGEM velocity [n,3] and stress [n,3,3] at targets due to point forces.
 
     xt=None means the targets are the sources themselves (self pair left out,
@@ -497,11 +542,11 @@ def point_forces(box, xs, g, xt=None, mu=1.0, alpha=None, rcut=None,
     ug, pg, sg = global_fields(box, xs, g, mu, alpha, rcut, want_sig)
     u = s = None
     if want_u:
-        u = ul + interp(box, ug, xt)
+        u = ul + evaluate(box, ug, xt, offgrid)
         if self_t:
             u -= (4.0 * alpha / math.sqrt(math.pi)) * _f64(g) / (8.0 * math.pi * mu)
     if want_sig:
-        s = sl + sym6_to_full(interp(box, sg, xt))
+        s = sl + sym6_to_full(evaluate(box, sg, xt, offgrid))
     return u, s
 
 
@@ -526,7 +571,7 @@ def geometry(x, tri):
 
 
 def single_layer(susp, q, quadrature="element", mu=1.0, alpha=None, rcut=None,
-                 targets=None):
+                 targets=None, offgrid="lagrange"):
     """w_j(z) = int q_i G_ji dS at the nodes (Sec. 3.4).  [N, 3] (or targets)."""
     box = susp.box
     alpha = default_alpha(box) if alpha is None else alpha
@@ -535,15 +580,21 @@ def single_layer(susp, q, quadrature="element", mu=1.0, alpha=None, rcut=None,
     g = 8.0 * math.pi * mu * Ab[:, None] * _f64(q)
     tsel = np.arange(susp.x.shape[0]) if targets is None else np.asarray(targets)
     if quadrature == "nodal":
-        u, _ = point_forces(box, susp.x, g, None, mu, alpha, rcut)
-        return u[tsel]
+        if targets is None or offgrid == "lagrange":
+            u, _ = point_forces(box, susp.x, g, None, mu, alpha, rcut, offgrid=offgrid)
+            return u[tsel]
+        xt = susp.x[tsel]
+        ul, _ = local_point(box, alpha, rcut, mu, susp.x, g, xt)   # r = 0 pairs excluded
+        ug, _, _ = global_fields(box, susp.x, g, mu, alpha, rcut)
+        return (ul + evaluate(box, ug, xt, offgrid)
+                - (4.0 * alpha / math.sqrt(math.pi)) * g[tsel] / (8.0 * math.pi * mu))
     wl = local_elem(box, alpha, rcut, 0, susp.x, susp.tri, q, targets=tsel)
     ug, _, _ = global_fields(box, susp.x, g, mu, alpha, rcut)
-    return wl + interp(box, ug, susp.x[tsel])
+    return wl + evaluate(box, ug, susp.x[tsel], offgrid)
 
 
 def double_layer(susp, q, quadrature="element", mu=1.0, alpha=None, rcut=None,
-                 targets=None):
+                 targets=None, offgrid="lagrange"):
     """v_j(z) = n_k(z) int q_i T_jik dS at the nodes (Sec. 3.5).  [N, 3]."""
     box = susp.box
     alpha = default_alpha(box) if alpha is None else alpha
@@ -553,7 +604,7 @@ def double_layer(susp, q, quadrature="element", mu=1.0, alpha=None, rcut=None,
     tsel = np.arange(susp.x.shape[0]) if targets is None else np.asarray(targets)
     xt = susp.x[tsel]
     _, _, sg = global_fields(box, susp.x, g, mu, alpha, rcut, want_stress=True)
-    vg = np.einsum("nk,njk->nj", nb[tsel], sym6_to_full(interp(box, sg, xt))) / mu
+    vg = np.einsum("nk,njk->nj", nb[tsel], sym6_to_full(evaluate(box, sg, xt, offgrid))) / mu
     if quadrature == "nodal":
         _, sl = local_point(box, alpha, rcut, mu, susp.x, g, xt, want_u=False,
                             want_sig=True)
