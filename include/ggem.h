@@ -20,8 +20,9 @@
  *    asynchronous on the plan's stream.
  *  - The caller owns every input and output array; the plan owns all
  *    workspaces.  No entry point below allocates device memory except
- *    ggem_plan, ggem_mesh_set (which sizes its mesh tables once) and the
- *    first bie_solve on a plan (Krylov workspace; FP64 twin of a mixed plan).
+ *    ggem_plan, ggem_mesh_set (which sizes its mesh tables once),
+ *    ggem_set_offgrid (the oversampled grid) and the first bie_solve on a
+ *    plan (Krylov workspace; FP64 twin of a mixed plan).
  *  - Every entry point returns a ggem_status; no C++ exception crosses the
  *    ABI.  On error ggem_last_error(plan) gives a message.
  */
@@ -98,6 +99,32 @@ const char *ggem_last_error(const ggem_plan_t *plan);
 
 /* Effective alpha and r_cut of the plan (host values). */
 ggem_status ggem_plan_info(const ggem_plan_t *plan, double *alpha, double *rcut);
+
+enum { GGEM_OFFGRID_LAGRANGE = 0, GGEM_OFFGRID_SPECTRAL = 1 };   /* ggem_set_offgrid */
+
+/*
+ * How the global solution is evaluated at points off the grid (every entry
+ * point that returns velocities, stresses or layer values at nodes or
+ * targets).
+ *   GGEM_OFFGRID_LAGRANGE (the default): 5-point Lagrange interpolation in
+ *     each direction, error ~ h^5 (Sec. 3.2.2).
+ *   GGEM_OFFGRID_SPECTRAL: the Fourier (x, z) x Chebyshev (y) expansion of the
+ *     global solution itself, evaluated to a tolerance rather than
+ *     interpolated, so that the error off the mesh decays as fast as on it
+ *     (the non-uniform FFT route that Sec. 3.2.3 points to).  In x and z the
+ *     modes are deconvolved by a Gaussian window, transformed on a grid
+ *     oversampled 2x, and gathered with the window over 2 half_width points
+ *     per direction (Greengard & Lee's type-2 non-uniform FFT); in y the
+ *     Chebyshev polynomial is evaluated by the barycentric formula on all Ny
+ *     nodes.  half_width: 0 selects 12 for FP64-accurate plans (window error
+ *     ~1e-13) and 6 for GGEM_MIXED (~2e-7); otherwise 2..16.  Cost per target
+ *     ~Ny (2 half_width)^2 per output component, against 125 for Lagrange.
+ * Allocates the oversampled grid (Ny x 9 x 2Nz x 2Nx values of the plan's
+ * precision) on the first switch to GGEM_OFFGRID_SPECTRAL; a mixed plan's
+ * FP64 twin follows the setting (with its own default width).
+ * Returns GGEM_ERR_INVALID_ARG for an unknown mode or width.
+ */
+ggem_status ggem_set_offgrid(ggem_plan_t *plan, int mode, int half_width);
 
 /*
  * Set the surface mesh (Sec. 3.3): n_nodes nodes x [n][3] and n_tris

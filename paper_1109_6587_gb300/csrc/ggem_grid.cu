@@ -6,6 +6,8 @@
 // Grid layout: physical [Ny][comp][Nz][Nx] (real T); after the x transform
 // each row of Nx reals holds Nx/2 complex modes k_x = 0..Nx/2-1 in place (the
 // Nyquist mode is dropped, i.e. set to zero); spectral [Ny][comp][Nz][Nx/2].
+#include <algorithm>
+
 #include "ggem_internal.cuh"
 
 namespace ggem {
@@ -172,6 +174,8 @@ static cudaError_t fft_z(const GridGeom& geo, T* data, int nplanes, const void* 
                          cudaStream_t st) {
     int Nz = geo.Nz, logNz = ilog2(Nz), nkx = geo.Nx / 2;
     int TB = min(nkx, 8);
+    // (the oversampled grids of the spectral evaluation reach Nz = 2048)
+    while (TB > 1 && (size_t)TB * Nz * sizeof(c2_t<T>) > (size_t)160 * 1024) TB >>= 1;
     size_t smem = (size_t)TB * Nz * sizeof(c2_t<T>);
     unsigned nb = (unsigned)((long)nplanes * ((nkx + TB - 1) / TB));
     grant_max_smem((const void*)k_fft_z<T>);
@@ -274,6 +278,9 @@ template <typename T> struct InterpArgs {
     int out_stride;
 };
 
+template <typename T>
+__device__ __forceinline__ void interp_store(const InterpArgs<T>& a, int t, const T* acc);
+
 // mode 0: velocity (3 comps): out = local + interp - self
 // mode 1: stress (6 comps):   out = local + interp
 // mode 2: double layer:       out_j = local_j + n_k sigma_jk / mu
@@ -334,6 +341,131 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
             }
         }
     }
+    interp_store<T>(a, t, acc);
+}
+
+// Spectral evaluation of the global field at the targets (GGEM_OFFGRID_SPECTRAL),
+// a warp per target.  The oversampled grid holds the field deconvolved by the
+// Gaussian window g(t) = exp(-c t^2) (t in fine spacings), so the window
+// gathered over the 2w nearest fine nodes in x and in z gives the Fourier sum
+// at the target to the window's tolerance (the type-2 non-uniform FFT of
+// Greengard & Lee); in y the values at the Chebyshev-Lobatto nodes are summed
+// with the barycentric weights lambda_j / (y - y_j), lambda_j = (-1)^j halved
+// at both ends, normalised by their sum -- the polynomial through all Ny
+// nodes, i.e. the Chebyshev series (a node hit exactly takes that node).
+// Lanes split into G groups of 32/G: a lane owns one x offset, a group every
+// G-th z row, so a row's 2w values are one contiguous load per group.
+template <typename T>
+__global__ void __launch_bounds__(128) k_interp_spectral(InterpArgs<T> a, SpecGrid sg) {
+    extern __shared__ double spsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int t = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (t >= a.n) return;                       // warp-uniform
+    const GridGeom& geo = a.geo;
+    const int Ny = geo.Ny, N = Ny - 1, w = sg.w, w2 = 2 * sg.w;
+    double* by = spsm + (size_t)wib * (Ny + 32);
+    double* wzs = by + Ny;
+    const double xt = a.x[3 * (size_t)t], yt = a.x[3 * (size_t)t + 1],
+                 zt = a.x[3 * (size_t)t + 2];
+    double part = 0.0;
+    int hit = -1;
+    for (int j = lane; j < Ny; j += 32) {
+        const double d = yt - a.yj[j];
+        double lam = (j & 1) ? -1.0 : 1.0;
+        if (j == 0 || j == N) lam *= 0.5;
+        double v = 0.0;
+        if (d == 0.0) hit = j;
+        else v = lam / d;
+        by[j] = v;
+        part += v;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        part += __shfl_xor_sync(0xffffffffu, part, o);
+        hit = max(hit, __shfl_xor_sync(0xffffffffu, hit, o));
+    }
+    const double inv = hit >= 0 ? 0.0 : 1.0 / part;
+    for (int j = lane; j < Ny; j += 32) by[j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : by[j] * inv;
+    const double ux = (xt - geo.Lx * floor(xt / geo.Lx)) * (sg.Mx / geo.Lx);
+    const double uz = (zt - geo.Lz * floor(zt / geo.Lz)) * (sg.Mz / geo.Lz);
+    const int px0 = (int)floor(ux), pz0 = (int)floor(uz);
+    const double fx = ux - px0, fz = uz - pz0;
+    if (lane < w2) {
+        const double tz = fz - (double)(lane - w + 1);
+        wzs[lane] = exp(-sg.c * tz * tz);
+    }
+    const int lpg = w2 <= 8 ? 8 : (w2 <= 16 ? 16 : 32);
+    const int G = 32 / lpg, g = lane / lpg, xl = lane - g * lpg;
+    const bool xv = xl < w2;
+    const double tx = fx - (double)(xl - w + 1);
+    const T wx = xv ? (T)exp(-sg.c * tx * tx) : (T)0;
+    int px = (px0 + xl - w + 1) % sg.Mx;
+    px += px < 0 ? sg.Mx : 0;
+    __syncwarp();
+    const int nc = (a.mode == 0) ? 3 : 6;
+    const size_t plane = (size_t)sg.Mz * sg.Mx;
+    const T* F = (const T*)sg.fine;
+    T acc[6] = {0, 0, 0, 0, 0, 0};
+    if (xv) {
+        for (int j = 0; j < Ny; ++j) {
+            const double bj = by[j];
+            if (bj == 0.0) continue;            // warp-uniform (shared weights)
+            const T* Fj = F + ((size_t)j * a.ncomp_total + a.comp0) * plane + px;
+            for (int jz = g; jz < w2; jz += G) {
+                int pz = (pz0 + jz - w + 1) % sg.Mz;
+                pz += pz < 0 ? sg.Mz : 0;
+                const T wv = (T)(bj * wzs[jz]);
+                const T* Fr = Fj + (size_t)pz * sg.Mx;
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    if (c < nc) acc[c] += wv * Fr[c * plane];
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        T v = acc[c] * wx;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[c] = v;
+    }
+    if (lane == 0) interp_store<T>(a, t, acc);
+}
+
+// Deconvolve and zero-pad the spectral planes onto the oversampled grid: fine
+// mode (kz', kx') takes the coarse mode with the same signed wavenumbers times
+// dx[kx] dz[kz]; modes the coarse grid lacks (and its Nyquist modes) are zero.
+template <typename T>
+__global__ void k_spec_pad(const c2_t<T>* __restrict__ spec, long nplanes, int Nx, int Nz,
+                           int Mx, int Mz, const T* __restrict__ dx, const T* __restrict__ dz,
+                           c2_t<T>* __restrict__ fine) {
+    const long total = nplanes * (long)Mz * (Mx / 2);
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        const int mkx = Mx / 2, nkx = Nx / 2;
+        const long pl = e / ((long)Mz * mkx);
+        const int r = (int)(e - pl * Mz * (long)mkx);
+        const int kzf = r / mkx, kxf = r - kzf * mkx;
+        c2_t<T> v;
+        v.x = (T)0;
+        v.y = (T)0;
+        if (kxf < nkx) {
+            int kz = -1;
+            if (kzf < Nz / 2) kz = kzf;
+            else if (kzf > Mz - Nz / 2) kz = kzf - (Mz - Nz);
+            if (kz >= 0) {
+                const c2_t<T> c = spec[(pl * Nz + kz) * nkx + kxf];
+                const T f = dx[kxf] * dz[kz];
+                v.x = c.x * f;
+                v.y = c.y * f;
+            }
+        }
+        fine[e] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void interp_store(const InterpArgs<T>& a, int t, const T* acc) {
     double* o = a.out + (size_t)t * a.out_stride;
     const T* lo = a.local ? a.local + (size_t)t * a.local_stride : nullptr;
     if (a.mode == 0) {
@@ -351,7 +483,7 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
         double v0 = n0 * s[0] + n1 * s[1] + n2 * s[2];
         double v1 = n0 * s[1] + n1 * s[3] + n2 * s[4];
         double v2 = n0 * s[2] + n1 * s[4] + n2 * s[5];
-        double im = 1.0 / geo.mu;
+        double im = 1.0 / a.geo.mu;
         o[0] = v0 * im + (lo ? (double)lo[0] : 0.0);
         o[1] = v1 * im + (lo ? (double)lo[1] : 0.0);
         o[2] = v2 * im + (lo ? (double)lo[2] : 0.0);
@@ -363,11 +495,28 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
                            int comp0, int n_tgt, const double* x_tgt, const T* local,
                            int local_stride, const double* nrm, const double* qself,
                            const double* wself, double self_coef, int mode, double* out,
-                           int out_stride, cudaStream_t st) {
+                           int out_stride, cudaStream_t st, const SpecGrid* spec) {
     if (n_tgt <= 0) return cudaSuccess;
     InterpArgs<T> a{geo, yj, grid, ncomp_total, comp0, mode, n_tgt, x_tgt, local,
                     local_stride, nrm, qself, wself, self_coef, out, out_stride};
-    k_interp<T><<<(n_tgt + 127) / 128, 128, 0, st>>>(a);
+    if (spec) {
+        // a warp per target, 4 per block; per warp Ny barycentric weights and
+        // 32 z-window values in shared memory
+        const size_t smem = (size_t)4 * (geo.Ny + 32) * sizeof(double);
+        k_interp_spectral<T><<<(n_tgt + 3) / 4, 128, smem, st>>>(a, *spec);
+    } else {
+        k_interp<T><<<(n_tgt + 127) / 128, 128, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t spectral_pad(const GridGeom& geo, const T* spec, int nplanes, int Mx, int Mz,
+                         const T* dx, const T* dz, T* fine, cudaStream_t st) {
+    const long total = (long)nplanes * Mz * (Mx / 2);
+    const unsigned nb = (unsigned)std::min<long>((total + 255) / 256, 152L * 16);
+    k_spec_pad<T><<<nb, 256, 0, st>>>((const c2_t<T>*)spec, nplanes, geo.Nx, geo.Nz, Mx, Mz,
+                                      dx, dz, (c2_t<T>*)fine);
     return cudaGetLastError();
 }
 
@@ -381,7 +530,9 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
     template cudaError_t interp_combine<T>(const GridGeom&, const double*, const T*, int, int, \
                                            int, const double*, const T*, int, const double*,   \
                                            const double*, const double*, double, int, double*, \
-                                           int, cudaStream_t);
+                                           int, cudaStream_t, const SpecGrid*);                   \
+    template cudaError_t spectral_pad<T>(const GridGeom&, const T*, int, int, int, const T*,   \
+                                         const T*, T*, cudaStream_t);
 GGEM_INST_GRID(float)
 GGEM_INST_GRID(double)
 

@@ -189,6 +189,14 @@ struct ggem_plan {
     double* d_sh = nullptr;            // Arnoldi coefficients / correction weights
     double* h_sh = nullptr;            // pinned host copy of d_sh
     ggem_plan* twin = nullptr;         // FP64 plan on the same mesh (mixed plans)
+    // spectral off-grid evaluation (ggem_set_offgrid)
+    int offgrid = 0;                   // GGEM_OFFGRID_*
+    int spec_w = 0;                    // Gaussian window half-width (fine points per side)
+    void* d_spec = nullptr;            // [Ny][9][2Nz][2Nx] T oversampled grid
+    void* d_spec_twx = nullptr;        // FFT twiddles of lengths 2Nx and 2Nz, laid out as
+    void* d_spec_twz = nullptr;        //   d_tw_x / d_tw_z
+    void* d_spec_dx = nullptr;         // [Nx/2] T deconvolution factors, k_x >= 0
+    void* d_spec_dz = nullptr;         // [Nz] T deconvolution factors, FFT order in z
     int sol_iters = 0, sol_cycles = 0, sol_mv64 = 0, sol_mvmix = 0;
     double sol_relres = 0.0;
     // learned warm start (allocated by its first use)
@@ -366,11 +374,31 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
 // mode 0: velocity, out = local + interp - self_coef * wself * qself
 // mode 1: stress (6), out = local + interp
 // mode 2: double layer, out_j = local_j + n_k sigma_jk / mu
+// Oversampled grid of the spectral off-grid evaluation: physical values
+// [Ny][ncomp_total][Mz][Mx] of the field deconvolved by the Gaussian window
+// exp(-c t^2) (t in fine-grid spacings), gathered over w points per side.
+struct SpecGrid {
+    const void* fine;
+    int Mx, Mz, w;
+    double c;
+};
+
+// Combine of local and global parts at the targets: the global grid field
+// evaluated by 5-point Lagrange interpolation, or (spec != nullptr) from the
+// oversampled grid by the Gaussian window in x, z and the barycentric
+// Chebyshev formula in y.
 template <typename T>
 cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid, int ncomp_total,
                            int comp0, int n_tgt, const double* x_tgt, const T* local,
                            int local_stride, const double* nrm, const double* qself,
                            const double* wself, double self_coef, int mode, double* out,
-                           int out_stride, cudaStream_t st);
+                           int out_stride, cudaStream_t st, const SpecGrid* spec = nullptr);
+
+// Spectral planes [nplanes][Nz][Nx/2] (complex T, after the Chebyshev
+// inverse) -> deconvolved, zero-padded planes [nplanes][Mz][Mx/2] of the
+// oversampled grid (complex T), ready for fft_inverse on the Mx x Mz grid.
+template <typename T>
+cudaError_t spectral_pad(const GridGeom& geo, const T* spec, int nplanes, int Mx, int Mz,
+                         const T* dx, const T* dz, T* fine, cudaStream_t st);
 
 }  // namespace ggem

@@ -28,6 +28,44 @@ thread_local std::string g_create_error = "no plan";
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// FFT tables of an Nx x Nz grid (complex, interleaved): twx = the Nx/4
+// twiddles of the length-Nx/2 complex FFT, then the Nx/2 post-twiddles
+// exp(-2 pi i k/Nx) of the real transform; twz = the Nz/2 twiddles in z.
+void fft_tables(int Nx, int Nz, std::vector<double>& twx, std::vector<double>& twz) {
+    const int M = Nx / 2;
+    twx.assign(2 * (M / 2 + M), 0.0);
+    twz.assign(2 * (Nz / 2), 0.0);
+    for (int k = 0; k < M / 2; ++k) {
+        twx[2 * k] = std::cos(2 * kPi * k / M);
+        twx[2 * k + 1] = -std::sin(2 * kPi * k / M);
+    }
+    for (int k = 0; k < M; ++k) {
+        twx[2 * (M / 2 + k)] = std::cos(2 * kPi * k / Nx);
+        twx[2 * (M / 2 + k) + 1] = -std::sin(2 * kPi * k / Nx);
+    }
+    for (int k = 0; k < Nz / 2; ++k) {
+        twz[2 * k] = std::cos(2 * kPi * k / Nz);
+        twz[2 * k + 1] = -std::sin(2 * kPi * k / Nz);
+    }
+}
+
+// Window of the spectral off-grid evaluation with oversampling 2 and w
+// points per side (Greengard & Lee): variance tau = pi w / (N^2 R (R - 1/2))
+// in units where the period is 2 pi, so exp(-(s - s_p)^2 / 4 tau) =
+// exp(-c t^2) with t in fine spacings and c = pi (R - 1/2) / (R w).
+constexpr double kSpecR = 2.0;
+double spec_c(int w) { return kPi * (kSpecR - 0.5) / (kSpecR * w); }
+
+SpecGrid spec_grid(const ggem_plan_t* P) {
+    SpecGrid g;
+    g.fine = P->d_spec;
+    g.Mx = 2 * P->prm.Nx;
+    g.Mz = 2 * P->prm.Nz;
+    g.w = P->spec_w;
+    g.c = spec_c(P->spec_w);
+    return g;
+}
+
 // ------------------------------------------------------------- geometry
 __global__ void k_tri_geom(int m, const double* __restrict__ x, const int* __restrict__ tri,
                            double* __restrict__ ta, double* __restrict__ tn,
@@ -137,6 +175,20 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
         GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
                               (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm, P->d_tc_inv));
     });
+    if (P->offgrid == GGEM_OFFGRID_SPECTRAL) {
+        // deconvolve onto the oversampled grid and transform there
+        stage(P, ST_FFT_INV, 3, [&] {
+            GridGeom fg = geo;
+            fg.Nx = 2 * geo.Nx;
+            fg.Nz = 2 * geo.Nz;
+            fg.nkx = geo.Nx;
+            GG_CUDA(spectral_pad<T>(geo, B, geo.Ny * nout, fg.Nx, fg.Nz, (const T*)P->d_spec_dx,
+                                    (const T*)P->d_spec_dz, (T*)P->d_spec, st));
+            GG_CUDA(fft_inverse<T>(fg, (T*)P->d_spec, geo.Ny * nout, P->d_spec_twx,
+                                   P->d_spec_twz, st));
+        });
+        return;
+    }
     stage(P, ST_FFT_INV, 2, [&] {
         GG_CUDA(fft_inverse<T>(geo, B, geo.Ny * nout, P->d_tw_x, P->d_tw_z, st));
     });
@@ -174,17 +226,19 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
     const double* xtt = tgt_is_src ? xs : xt;
     int nt = tgt_is_src ? n_src : n_tgt;
     int nout = nout_of(sel);
+    const SpecGrid sg = spec_grid(P);
+    const SpecGrid* spec = P->offgrid == GGEM_OFFGRID_SPECTRAL ? &sg : nullptr;
     stage(P, ST_INTERP, (u ? 1 : 0) + (s ? 1 : 0), [&] {
         if (u) {
             double sc = 4.0 * geo.alpha / std::sqrt(kPi) / (8.0 * kPi * geo.mu);
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, nout, 0, nt, xtt, loc,
                                       stride, nullptr, tgt_is_src ? g : nullptr, nullptr, sc, 0,
-                                      u, 3, st));
+                                      u, 3, st, spec));
         }
         if (s)
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, nout, u ? 3 : 0, nt,
                                       xtt, loc + (u ? 3 : 0), stride, nullptr, nullptr, nullptr,
-                                      0.0, 1, s, 6, st));
+                                      0.0, 1, s, 6, st, spec));
     });
 }
 
@@ -304,6 +358,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         GG_CUDA(cudaEventRecord(P->ev_join, side));
         GG_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
     }
+    const SpecGrid sg = spec_grid(P);
+    const SpecGrid* spec = P->offgrid == GGEM_OFFGRID_SPECTRAL ? &sg : nullptr;
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
             // nodal form: remove the free-space global self term (4 alpha/sqrt(pi)) A_b q_b;
@@ -311,10 +367,10 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
             double sc = elem ? 0.0 : 4.0 * geo.alpha / std::sqrt(kPi);
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 3, 0, n, P->d_x, loc,
                                       3, nullptr, elem ? nullptr : q, P->d_area, sc, 0, out, 3,
-                                      st));
+                                      st, spec));
         } else {
             GG_CUDA(interp_combine<T>(geo, P->d_yj, (const T*)P->d_gridB, 6, 0, n, P->d_x, loc,
-                                      3, P->d_nrm, nullptr, nullptr, 0.0, 2, out, 3, st));
+                                      3, P->d_nrm, nullptr, nullptr, 0.0, 2, out, 3, st, spec));
         }
     });
 }
@@ -356,6 +412,47 @@ void upload_tables(ggem_plan_t* P, const std::vector<double>& cf, const std::vec
     }
     GG_CUDA(cudaMemcpy(P->d_tw_x, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_tw_z, d.data(), d.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+// Oversampled grid, its FFT tables and the deconvolution factors of the
+// spectral off-grid evaluation with window half-width w.  The factor of mode
+// l is 1 / (M ghat(l)) with ghat(l) = sqrt(tau/pi) exp(-l^2 tau) the Fourier
+// coefficient of the periodised window; 1/M is the trapezoidal weight of the
+// gather on M fine nodes.  Nyquist modes get 0.
+template <typename T>
+void spec_setup(ggem_plan_t* P, int w) {
+    const int Nx = P->prm.Nx, Nz = P->prm.Nz, Ny = P->prm.Ny;
+    const int Mx = 2 * Nx, Mz = 2 * Nz;
+    if (!P->d_spec) {
+        // up to 9 components: velocity and stress of ggem_point_forces
+        dalloc(P, (T**)&P->d_spec, (size_t)Ny * 9 * Mz * Mx);
+        std::vector<double> twx, twz;
+        fft_tables(Mx, Mz, twx, twz);
+        std::vector<T> a(twx.begin(), twx.end()), b(twz.begin(), twz.end());
+        dalloc(P, (T**)&P->d_spec_twx, a.size());
+        dalloc(P, (T**)&P->d_spec_twz, b.size());
+        GG_CUDA(cudaMemcpy(P->d_spec_twx, a.data(), a.size() * sizeof(T),
+                           cudaMemcpyHostToDevice));
+        GG_CUDA(cudaMemcpy(P->d_spec_twz, b.data(), b.size() * sizeof(T),
+                           cudaMemcpyHostToDevice));
+        dalloc(P, (T**)&P->d_spec_dx, (size_t)Nx / 2);
+        dalloc(P, (T**)&P->d_spec_dz, (size_t)Nz);
+    }
+    if (w == P->spec_w) return;
+    const double den = kSpecR * (kSpecR - 0.5);
+    const double taux = kPi * w / ((double)Nx * Nx * den), tauz = kPi * w / ((double)Nz * Nz * den);
+    std::vector<T> dx(Nx / 2), dz(Nz);
+    for (int l = 0; l < Nx / 2; ++l)
+        dx[l] = (T)(std::sqrt(kPi / taux) * std::exp((double)l * l * taux) / Mx);
+    for (int k = 0; k < Nz; ++k) {
+        const int m = k < Nz / 2 ? k : k - Nz;
+        dz[k] = k == Nz / 2 ? (T)0
+                            : (T)(std::sqrt(kPi / tauz) * std::exp((double)m * m * tauz) / Mz);
+    }
+    GG_CUDA(cudaStreamSynchronize(P->st));     // no launch may still read the old factors
+    GG_CUDA(cudaMemcpy(P->d_spec_dx, dx.data(), dx.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_spec_dz, dz.data(), dz.size() * sizeof(T), cudaMemcpyHostToDevice));
+    P->spec_w = w;
 }
 
 void plan_build(ggem_plan_t* P, const ggem_params& prm) {
@@ -410,20 +507,8 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             cf[(size_t)n * Ny + j] = 2.0 / (N * cn * cj) * c * inxz;
             ci[(size_t)j * Ny + n] = c;
         }
-    int M = prm.Nx / 2;
-    std::vector<double> twx(2 * (M / 2 + M)), twz(2 * (prm.Nz / 2));
-    for (int k = 0; k < M / 2; ++k) {
-        twx[2 * k] = std::cos(2 * kPi * k / M);
-        twx[2 * k + 1] = -std::sin(2 * kPi * k / M);
-    }
-    for (int k = 0; k < M; ++k) {
-        twx[2 * (M / 2 + k)] = std::cos(2 * kPi * k / prm.Nx);
-        twx[2 * (M / 2 + k) + 1] = -std::sin(2 * kPi * k / prm.Nx);
-    }
-    for (int k = 0; k < prm.Nz / 2; ++k) {
-        twz[2 * k] = std::cos(2 * kPi * k / prm.Nz);
-        twz[2 * k + 1] = -std::sin(2 * kPi * k / prm.Nz);
-    }
+    std::vector<double> twx, twz;
+    fft_tables(prm.Nx, prm.Nz, twx, twz);
     dalloc(P, &P->d_yj, Ny);
     GG_CUDA(cudaMemcpy(P->d_yj, yj.data(), Ny * sizeof(double), cudaMemcpyHostToDevice));
     {
@@ -631,7 +716,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
-                    P->d_qg_soa};
+                    P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
+                    P->d_spec_dz};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
@@ -671,6 +757,26 @@ ggem_status ggem_plan_destroy(ggem_plan_t* P) {
 const char* ggem_last_error(const ggem_plan_t* P) {
     if (!P) return g_create_error.c_str();
     return P->err.c_str();
+}
+
+ggem_status ggem_set_offgrid(ggem_plan_t* P, int mode, int half_width) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(mode == GGEM_OFFGRID_LAGRANGE || mode == GGEM_OFFGRID_SPECTRAL,
+                 GGEM_ERR_INVALID_ARG, "mode must be GGEM_OFFGRID_LAGRANGE or _SPECTRAL");
+        GG_CHECK(half_width == 0 || (half_width >= 2 && half_width <= 16), GGEM_ERR_INVALID_ARG,
+                 "half_width must be 0 (default) or in [2, 16]");
+        if (mode == GGEM_OFFGRID_SPECTRAL) {
+            const int w = half_width ? half_width : (P->fp64 ? 12 : 6);
+            if (P->fp64) spec_setup<double>(P, w);
+            else spec_setup<float>(P, w);
+        }
+        P->offgrid = mode;
+        if (P->twin) {
+            ggem_status ts = ggem_set_offgrid(P->twin, mode, 0);
+            GG_CHECK(ts == GGEM_OK, ts, std::string("FP64 twin: ") + ggem_last_error(P->twin));
+        }
+    });
 }
 
 ggem_status ggem_plan_info(const ggem_plan_t* P, double* alpha, double* rcut) {

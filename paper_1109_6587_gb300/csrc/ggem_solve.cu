@@ -301,6 +301,10 @@ void ensure_twin(ggem_plan_t* P) {
     P->twin = T;
     s = ggem_mesh_set(T, P->n_nodes, P->d_x, P->n_tris, P->d_tri);
     GG_CHECK(s == GGEM_OK, s, std::string("FP64 twin mesh: ") + ggem_last_error(T));
+    if (P->offgrid != GGEM_OFFGRID_LAGRANGE) {    // the twin evaluates the same operator
+        s = ggem_set_offgrid(T, P->offgrid, 0);
+        GG_CHECK(s == GGEM_OK, s, std::string("FP64 twin off-grid: ") + ggem_last_error(T));
+    }
 }
 
 // Solver on plan P for unknown vectors of length n3 (workspace ready).

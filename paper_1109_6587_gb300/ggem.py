@@ -51,7 +51,10 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_check", "ggem_rigid_solve", "ggem_membrane_reference",
            "ggem_membrane_traction", "ggem_undisturbed", "ggem_capsule_velocity",
            "ggem_capsule_step", "ggem_mesh_positions", "ggem_min_separation",
-           "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct"]
+           "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct",
+           "ggem_set_offgrid"]
+
+GGEM_OFFGRID = {"lagrange": 0, "spectral": 1}
 
 GGEM_FLOW = {"none": 0, "shear": 1, "poiseuille": 2}
 
@@ -108,6 +111,7 @@ def lib():
         L.ggem_particle_volumes.argtypes = [P, P]
         L.ggem_volume_correct.argtypes = [P, P, D, I, ctypes.POINTER(I)]
         L.ggem_overlap_correct.argtypes = [P, D, I, ctypes.POINTER(I)]
+        L.ggem_set_offgrid.argtypes = [P, I, I]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -161,7 +165,7 @@ class Plan:
 
     def __init__(self, Lx, Lz, W, y0, Nx, Ny, Nz, alpha=0.0, rcut_factor=0.0, mu=1.0,
                  precision="fp64", quadrature="nodal", max_points=1 << 16, max_tris=0,
-                 stream=None):
+                 stream=None, offgrid="lagrange", offgrid_width=0):
         prec = {"fp64": GGEM_FP64, "mixed": GGEM_MIXED,
                 "fp64_emulated": GGEM_FP64_EMULATED}[precision]
         quad = {"nodal": GGEM_NODAL, "element": GGEM_ELEMENT}[quadrature]
@@ -180,6 +184,14 @@ class Plan:
         self.h = h
         self.n_nodes = 0
         self.n_particles = 0
+        if offgrid != "lagrange" or offgrid_width:
+            self.set_offgrid(offgrid, offgrid_width)
+
+    def set_offgrid(self, mode, half_width=0):
+        """Off-grid evaluation of the global part: 'lagrange' (5-point, Sec.
+        3.2.2) or 'spectral' (the expansion itself by a Gaussian-window
+        non-uniform FFT, Sec. 3.2.3); half_width 0 = 12 (FP64) / 6 (mixed)."""
+        _check(lib().ggem_set_offgrid(self.h, GGEM_OFFGRID[mode], int(half_width)), self.h)
 
     @classmethod
     def for_box(cls, box, **kw):

@@ -161,3 +161,33 @@ def test_overlap_correction(ggem, case):
     assert moves == mo and moves >= 1
     assert np.abs(x - xo).max() < 1e-12
     assert P.overlap_correct(0.05) == 0                    # nothing left to correct
+
+
+def test_capsule_argument_errors(ggem, capsules):
+    s, x_ref, lam = capsules
+    P = ggem.Plan.for_box(s.box, precision="fp64", quadrature="element", max_points=len(s.x),
+                          max_tris=len(s.tri))
+    P.mesh_set(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.tri, device="cuda"))
+    with pytest.raises(ggem.GGEMError):             # no membrane reference yet
+        P.membrane_traction(1.0)
+    with pytest.raises(ggem.GGEMError):
+        P.capsule_velocity(lam, "shear", 1.0)
+    with pytest.raises(ggem.GGEMError):             # particle ids not set
+        P.particle_volumes()
+    with pytest.raises(ggem.GGEMError):
+        P.overlap_correct(0.05)
+    P.membrane_reference(x_ref)
+    P.mesh_particles(s.particle, 2)
+    with pytest.raises(ggem.GGEMError):             # dt must be positive
+        P.capsule_step(lam, 0.0, "shear", 1.0)
+    with pytest.raises(ggem.GGEMError):             # the gap must fit a cell
+        P.overlap_correct(100.0)
+    with pytest.raises(KeyError):                   # unknown flow name (binding)
+        P.undisturbed("couette", 1.0)
+    bad = ggem.lib().ggem_undisturbed(P.h, 7, 1.0, None, None)
+    assert bad == 1                                 # GGEM_ERR_INVALID_ARG for an unknown flow
+    # a new triangle set drops the membrane reference
+    P.mesh_set(torch.as_tensor(s.x, device="cuda"), torch.as_tensor(s.tri.copy(), device="cuda"))
+    with pytest.raises(ggem.GGEMError):
+        P.membrane_traction(1.0)
+    P.check()
