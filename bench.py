@@ -56,6 +56,9 @@ def _args():
                          "runs on the default only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--offgrid", default="lagrange", choices=["lagrange", "spectral"],
+                    help="off-grid evaluation of the global part (5-point Lagrange or the "
+                         "spectral non-uniform FFT evaluation)")
     return ap.parse_args()
 
 
@@ -80,6 +83,7 @@ def _config(susp, args):
     return {"workload": WORKLOADS[args.workload][1],
             "n_points": int(susp.x.shape[0]), "grid": [b.Nx, b.Ny, b.Nz],
             "precision": args.precision, "quadrature": args.quadrature,
+            "offgrid": args.offgrid,
             "step": "single-layer + double-layer matvec",
             "l2": "flushed (256 MiB write) before every timed step",
             "parallelism": f"replicas x{args.gpus}"}
@@ -233,7 +237,7 @@ def run_mine(args, rank, world):
     susp = _workload(args)
     n = susp.x.shape[0]
     P = ggem.Plan.for_box(susp.box, precision=args.precision, quadrature=args.quadrature,
-                          max_points=n, max_tris=susp.tri.shape[0])
+                          max_points=n, max_tris=susp.tri.shape[0], offgrid=args.offgrid)
     P.mesh_set(torch.as_tensor(susp.x, device=dev), torch.as_tensor(susp.tri, device=dev))
     rng = np.random.default_rng(1234 + rank)
     qs = [torch.as_tensor(rng.standard_normal((n, 3)), device=dev) for _ in range(4)]
@@ -496,6 +500,55 @@ def dynamics_metrics(args, susp, dev, warm=1, timed=3):
     return out
 
 
+def offgrid_metrics(args, susp, dev, warm=3, timed=10):
+    """The same step with the other off-grid evaluation (spectral when the
+    main line uses Lagrange interpolation, and vice versa): step time and the
+    stage times it changes."""
+    import torch
+    from paper_1109_6587_gb300 import ggem
+    other = "spectral" if args.offgrid == "lagrange" else "lagrange"
+    n = susp.x.shape[0]
+    P = ggem.Plan.for_box(susp.box, precision=args.precision, quadrature=args.quadrature,
+                          max_points=n, max_tris=susp.tri.shape[0], offgrid=other)
+    P.mesh_set(torch.as_tensor(susp.x, device=dev), torch.as_tensor(susp.tri, device=dev))
+    rng = np.random.default_rng(77)
+    q = torch.as_tensor(rng.standard_normal((n, 3)), device=dev)
+    w = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    v = torch.empty_like(w)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        P.single_layer(q, w)
+        P.double_layer(q, v)
+    torch.cuda.synchronize()
+    t_ms = 0.0
+    for _ in range(timed):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.single_layer(q, w)
+        P.double_layer(q, v)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_ms += a.elapsed_time(b)
+    P.trace(True)
+    for _ in range(timed):
+        flush.zero_()
+        P.single_layer(q, w)
+        P.double_layer(q, v)
+    torch.cuda.synchronize()
+    st = P.trace_read()
+    P.trace(False)
+    ms = t_ms / timed
+    out = {"offgrid": other, "ms_per_step": ms, "value": n / (ms * 1e-3) / 1e6,
+           "unit": "Mpts/s"}
+    for k in ("fft_inverse", "interpolate"):
+        if k in st:
+            out[k + "_ms"] = st[k][0] / st[k][1]
+    P.close()
+    return out
+
+
 def W_rigid(susp, t):
     from paper_1109_6587_gb300 import workloads as W
     return W.rigid_step(susp, seed=500, step=t) if t else susp
@@ -553,6 +606,7 @@ def main():
         import torch
         line["solve"] = solve_metrics(args, res["susp"], torch.device("cuda"))
         line["dynamics"] = dynamics_metrics(args, res["susp"], torch.device("cuda"))
+        line["offgrid_other"] = offgrid_metrics(args, res["susp"], torch.device("cuda"))
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "capsules100":
         line["cpu_baseline"] = cpu_baseline(res["susp"], args)
     if world > 1:

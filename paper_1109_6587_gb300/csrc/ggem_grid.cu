@@ -281,6 +281,10 @@ template <typename T> struct InterpArgs {
 template <typename T>
 __device__ __forceinline__ void interp_store(const InterpArgs<T>& a, int t, const T* acc);
 
+template <typename T> __device__ __forceinline__ T wexp(T x);
+template <> __device__ __forceinline__ float wexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double wexp<double>(double x) { return exp(x); }
+
 // mode 0: velocity (3 comps): out = local + interp - self
 // mode 1: stress (6 comps):   out = local + interp
 // mode 2: double layer:       out_j = local_j + n_k sigma_jk / mu
@@ -354,72 +358,104 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
 // at both ends, normalised by their sum -- the polynomial through all Ny
 // nodes, i.e. the Chebyshev series (a node hit exactly takes that node).
 // Lanes split into G groups of 32/G: a lane owns one x offset, a group every
-// G-th z row, so a row's 2w values are one contiguous load per group.
+// G-th z row; for each row the y sum runs innermost (one load and one FMA per
+// node and component), then the row's window weight scales it.  The weights
+// (y in T, z in T, row offsets) sit in the warp's shared memory.  Warps take
+// the targets in sg.order (cell order for mesh nodes) so that the stencils of
+// a block overlap in L1.
 template <typename T>
-__global__ void __launch_bounds__(128) k_interp_spectral(InterpArgs<T> a, SpecGrid sg) {
+__global__ void __launch_bounds__(128, 8) k_interp_spectral(InterpArgs<T> a, SpecGrid sg) {
     extern __shared__ double spsm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int t = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (t >= a.n) return;                       // warp-uniform
+    const int k = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (k >= a.n) return;                       // warp-uniform
+    const int t = sg.order ? sg.order[k] : k;
     const GridGeom& geo = a.geo;
     const int Ny = geo.Ny, N = Ny - 1, w = sg.w, w2 = 2 * sg.w;
-    double* by = spsm + (size_t)wib * (Ny + 32);
-    double* wzs = by + Ny;
+    // per warp: Ny + 32 T weights, 32 row offsets (laid out in doubles)
+    double* wbase = spsm + (size_t)wib * (Ny + 64);
+    T* by = reinterpret_cast<T*>(wbase);
+    T* wzs = by + Ny;
+    long* roff = reinterpret_cast<long*>(wbase + Ny + 32);
     const double xt = a.x[3 * (size_t)t], yt = a.x[3 * (size_t)t + 1],
                  zt = a.x[3 * (size_t)t + 2];
-    double part = 0.0;
+    // Weights in the plan's precision T (GB300 issues FP64 at 1/64 of the FP32
+    // rate; only the coordinate reductions below stay in FP64).
+    T bj[9];                                    // Ny <= 257: at most 9 per lane
+    T part = (T)0;
     int hit = -1;
-    for (int j = lane; j < Ny; j += 32) {
-        const double d = yt - a.yj[j];
-        double lam = (j & 1) ? -1.0 : 1.0;
-        if (j == 0 || j == N) lam *= 0.5;
-        double v = 0.0;
-        if (d == 0.0) hit = j;
-        else v = lam / d;
-        by[j] = v;
-        part += v;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int j = lane + 32 * r;
+        bj[r] = (T)0;
+        if (j < Ny) {
+            const T d = (T)(yt - a.yj[j]);
+            T lam = (j & 1) ? (T)-1 : (T)1;
+            if (j == 0 || j == N) lam *= (T)0.5;
+            if (d == (T)0) hit = j;
+            else bj[r] = lam / d;
+            part += bj[r];
+        }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         part += __shfl_xor_sync(0xffffffffu, part, o);
         hit = max(hit, __shfl_xor_sync(0xffffffffu, hit, o));
     }
-    const double inv = hit >= 0 ? 0.0 : 1.0 / part;
-    for (int j = lane; j < Ny; j += 32) by[j] = hit >= 0 ? (j == hit ? 1.0 : 0.0) : by[j] * inv;
-    const double ux = (xt - geo.Lx * floor(xt / geo.Lx)) * (sg.Mx / geo.Lx);
-    const double uz = (zt - geo.Lz * floor(zt / geo.Lz)) * (sg.Mz / geo.Lz);
-    const int px0 = (int)floor(ux), pz0 = (int)floor(uz);
-    const double fx = ux - px0, fz = uz - pz0;
+    const T inv = (T)1 / part;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int j = lane + 32 * r;
+        if (j < Ny) by[j] = bj[r] * inv;
+    }
+    // fine-grid coordinates: integer part wrapped into the period, fraction in T
+    const double ux = xt * sg.sx, uz = zt * sg.sz;
+    const double flx = floor(ux), flz = floor(uz);
+    const T fx = (T)(ux - flx), fz = (T)(uz - flz);
+    const int px0 = (int)((long long)flx % sg.Mx), pz0 = (int)((long long)flz % sg.Mz);
+    const T cw = (T)sg.c;
     if (lane < w2) {
-        const double tz = fz - (double)(lane - w + 1);
-        wzs[lane] = exp(-sg.c * tz * tz);
+        const T tz = fz - (T)(lane - w + 1);
+        wzs[lane] = wexp<T>(-cw * tz * tz);
+        int pz = (pz0 + lane - w + 1) % sg.Mz;
+        pz += pz < 0 ? sg.Mz : 0;
+        roff[lane] = (long)pz * sg.Mx;
     }
     const int lpg = w2 <= 8 ? 8 : (w2 <= 16 ? 16 : 32);
     const int G = 32 / lpg, g = lane / lpg, xl = lane - g * lpg;
     const bool xv = xl < w2;
-    const double tx = fx - (double)(xl - w + 1);
-    const T wx = xv ? (T)exp(-sg.c * tx * tx) : (T)0;
+    const T tx = fx - (T)(xl - w + 1);
+    const T wx = xv ? wexp<T>(-cw * tx * tx) : (T)0;
     int px = (px0 + xl - w + 1) % sg.Mx;
     px += px < 0 ? sg.Mx : 0;
     __syncwarp();
     const int nc = (a.mode == 0) ? 3 : 6;
     const size_t plane = (size_t)sg.Mz * sg.Mx;
-    const T* F = (const T*)sg.fine;
+    const size_t jstride = (size_t)a.ncomp_total * plane;
+    const T* F = (const T*)sg.fine + (size_t)a.comp0 * plane + px;
     T acc[6] = {0, 0, 0, 0, 0, 0};
     if (xv) {
-        for (int j = 0; j < Ny; ++j) {
-            const double bj = by[j];
-            if (bj == 0.0) continue;            // warp-uniform (shared weights)
-            const T* Fj = F + ((size_t)j * a.ncomp_total + a.comp0) * plane + px;
-            for (int jz = g; jz < w2; jz += G) {
-                int pz = (pz0 + jz - w + 1) % sg.Mz;
-                pz += pz < 0 ? sg.Mz : 0;
-                const T wv = (T)(bj * wzs[jz]);
-                const T* Fr = Fj + (size_t)pz * sg.Mx;
+        for (int jz = g; jz < w2; jz += G) {
+            const T* Fr = F + roff[jz];
+            T sum[6] = {0, 0, 0, 0, 0, 0};
+            if (hit >= 0) {                     // on a Chebyshev node (warp-uniform)
+                const T* Fj = Fr + (size_t)hit * jstride;
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
-                    if (c < nc) acc[c] += wv * Fr[c * plane];
+                    if (c < nc) sum[c] = Fj[c * plane];
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < Ny; ++j) {
+                    const T b = by[j];
+                    const T* Fj = Fr + (size_t)j * jstride;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        if (c < nc) sum[c] += b * Fj[c * plane];
+                }
             }
+            const T wz = wzs[jz];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc[c] += wz * sum[c];
         }
     }
 #pragma unroll
@@ -500,9 +536,9 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
     InterpArgs<T> a{geo, yj, grid, ncomp_total, comp0, mode, n_tgt, x_tgt, local,
                     local_stride, nrm, qself, wself, self_coef, out, out_stride};
     if (spec) {
-        // a warp per target, 4 per block; per warp Ny barycentric weights and
-        // 32 z-window values in shared memory
-        const size_t smem = (size_t)4 * (geo.Ny + 32) * sizeof(double);
+        // a warp per target, 4 per block; per warp Ny barycentric weights,
+        // 32 z-window values and 32 row offsets in shared memory
+        const size_t smem = (size_t)4 * (geo.Ny + 64) * sizeof(double);
         k_interp_spectral<T><<<(n_tgt + 3) / 4, 128, smem, st>>>(a, *spec);
     } else {
         k_interp<T><<<(n_tgt + 127) / 128, 128, 0, st>>>(a);

@@ -381,6 +381,8 @@ struct SpecGrid {
     const void* fine;
     int Mx, Mz, w;
     double c;
+    double sx, sz;      // Mx / Lx, Mz / Lz: fine spacings per unit length
+    const int* order;   // target processing order (nullptr: 0..n-1)
 };
 
 // Combine of local and global parts at the targets: the global grid field

@@ -63,6 +63,9 @@ SpecGrid spec_grid(const ggem_plan_t* P) {
     g.Mz = 2 * P->prm.Nz;
     g.w = P->spec_w;
     g.c = spec_c(P->spec_w);
+    g.sx = g.Mx / P->prm.Lx;
+    g.sz = g.Mz / P->prm.Lz;
+    g.order = nullptr;
     return g;
 }
 
@@ -226,7 +229,8 @@ void point_forces_impl(ggem_plan_t* P, int n_src, const double* xs, const double
     const double* xtt = tgt_is_src ? xs : xt;
     int nt = tgt_is_src ? n_src : n_tgt;
     int nout = nout_of(sel);
-    const SpecGrid sg = spec_grid(P);
+    SpecGrid sg = spec_grid(P);
+    sg.order = tgt_is_src ? P->d_perm : nullptr;    // sources in cell order
     const SpecGrid* spec = P->offgrid == GGEM_OFFGRID_SPECTRAL ? &sg : nullptr;
     stage(P, ST_INTERP, (u ? 1 : 0) + (s ? 1 : 0), [&] {
         if (u) {
@@ -358,7 +362,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         GG_CUDA(cudaEventRecord(P->ev_join, side));
         GG_CUDA(cudaStreamWaitEvent(st, P->ev_join, 0));
     }
-    const SpecGrid sg = spec_grid(P);
+    SpecGrid sg = spec_grid(P);
+    sg.order = P->d_mesh_perm;                      // mesh nodes in cell order
     const SpecGrid* spec = P->offgrid == GGEM_OFFGRID_SPECTRAL ? &sg : nullptr;
     stage(P, ST_INTERP, 1, [&] {
         if (layer == 0) {
