@@ -104,3 +104,40 @@ def test_normal_density_solution():
     expect = nb / (1.0 + kappa[0] * lam / (4.0 * math.pi))
     # D n = lam n holds up to the mesh/grid error of the operator (~1e-2 here)
     assert ok and np.abs(q - expect).max() < 0.05 * np.abs(expect).max()
+
+
+def test_block_diagonal_preconditioner_ceiling():
+    """What a learned 3x3 block-diagonal preconditioner could at best gain:
+    the exact inverse of every node's 3x3 diagonal block of the discrete
+    operator (I + kappa/4pi D) as a right preconditioner saves no GMRES
+    iteration on two capsules, while the exact inverse of each particle's
+    whole block halves the count -- the operator's spread comes from
+    particle-scale modes (normal and rigid-body densities), not from node-local
+    coupling."""
+    V, F = W.icosphere(1)
+    box = W.Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=16, Ny=17, Nz=16)
+    c1, c2 = np.array([2.2, 0.1, 4.0]), np.array([5.0, -0.4, 4.5])
+    s = W.Suspension(box=box, x=np.concatenate([0.97 * V + c1, 0.97 * V + c2]),
+                     tri=np.concatenate([F, F + len(V)]),
+                     particle=np.repeat([0, 1], len(V)).astype(np.int32),
+                     centres=np.stack([c1, c2]), radius=0.97)
+    n, m = s.x.shape[0], 3 * len(V)
+    for kap in (2.0 / 3.0, -2.0 / 3.0):
+        kappa = np.full(n, kap)
+        A = np.stack([O.bie_operator(s, kappa, e.reshape(n, 3)).ravel()
+                      for e in np.eye(3 * n)], 1)
+        b = np.random.default_rng(0).standard_normal(3 * n)
+
+        def its(M):
+            return O.gmres(lambda y: A @ (M @ y), b, tol=1e-6)[1]
+        node = np.zeros_like(A)
+        for i in range(n):
+            sl = slice(3 * i, 3 * i + 3)
+            node[sl, sl] = np.linalg.inv(A[sl, sl])
+        part = np.zeros_like(A)
+        for p in range(2):
+            sl = slice(p * m, (p + 1) * m)
+            part[sl, sl] = np.linalg.inv(A[sl, sl])
+        plain = its(np.eye(3 * n))
+        assert its(node) >= plain - 1
+        assert its(part) <= plain // 2 + 1
