@@ -14,8 +14,10 @@ FP64 solve, the mixed solve and the mixed solve with the learned warm start
 -- is measured on the same workload and reported under "solve".
 
 Other workloads (--workload capsules1000 or rbc4000: 642,000 and 2,568,000
-points) measure the same step at the larger configurations; the pair counts of
-their roofline are taken on a sample of 20,000 targets.
+points; capsules100_phi and capsules1000_phi: the 100- and 1000-capsule slits
+filled to volume fractions 0.1 and 0.2, 245,244 and 3,923,904 points) measure
+the same step at the larger configurations; the pair counts of their roofline
+are taken on a sample of 20,000 targets.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
@@ -50,10 +52,12 @@ def _args():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_emulated"])
     ap.add_argument("--quadrature", default="element", choices=["nodal", "element"])
     ap.add_argument("--workload", default="capsules100",
-                    choices=["capsules100", "capsules1000", "rbc4000"],
+                    choices=["capsules100", "capsules1000", "rbc4000", "capsules100_phi",
+                             "capsules1000_phi"],
                     help="capsules100 (default, the benchmark configuration), capsules1000 "
-                         "(642,000 points) or rbc4000 (2,568,000 points); the CPU baseline "
-                         "runs on the default only")
+                         "(642,000 points), rbc4000 (2,568,000 points), capsules100_phi / "
+                         "capsules1000_phi (the same slits at volume fractions 0.1 / 0.2); "
+                         "the CPU baseline runs on the default only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--offgrid", default="lagrange", choices=["lagrange", "spectral"],
@@ -69,6 +73,12 @@ WORKLOADS = {
                      "1000 spherical capsules x 642 nodes (642,000 points), slit 80 x [-10,10] x 80"),
     "rbc4000": ("rbc_4000",
                 "4000 biconcave capsules x 642 nodes (2,568,000 points), slit 150 x [-15,15] x 150"),
+    "capsules100_phi": ("capsules_100_phi",
+                        "382 spherical capsules x 642 nodes (245,244 points) at volume "
+                        "fraction 0.1, slit 40 x [-5,5] x 40"),
+    "capsules1000_phi": ("capsules_1000_phi",
+                         "6112 spherical capsules x 642 nodes (3,923,904 points) at volume "
+                         "fraction 0.2, slit 80 x [-10,10] x 80"),
 }
 
 

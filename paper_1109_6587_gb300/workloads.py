@@ -203,6 +203,25 @@ def capsules_1000(seed=0):
     return suspension(1000, box_1000_capsules(), level=3, radius=1.0, seed=seed)
 
 
+def capsules_at_phi(box: Box, phi, seed=0, level=3, radius=1.0):
+    """Spherical capsules filling the slit to the volume fraction phi
+    (n = round(phi Lx Lz W / (4/3 pi a^3)))."""
+    n = int(round(phi * box.Lx * box.Lz * box.W / (4.0 / 3.0 * math.pi * radius ** 3)))
+    return suspension(n, box, level=level, radius=radius, seed=seed)
+
+
+def capsules_100_phi(seed=0):
+    """The 100-capsule slit and grid filled to phi = 0.1: 382 capsules x 642
+    nodes (245,244 points)."""
+    return capsules_at_phi(box_100_capsules(), 0.1, seed=seed)
+
+
+def capsules_1000_phi(seed=0):
+    """The 1000-capsule slit and grid filled to phi = 0.2: 6112 capsules x 642
+    nodes (3,923,904 points)."""
+    return capsules_at_phi(box_1000_capsules(), 0.2, seed=seed)
+
+
 # Evans-Fung biconcave profile of a red blood cell in units of its radius R0:
 # half-thickness h(rho) = (R0/2) sqrt(1 - rho^2) (C0 + C1 rho^2 + C2 rho^4),
 # rho the distance from the axis over R0 (Evans and Fung 1972).
