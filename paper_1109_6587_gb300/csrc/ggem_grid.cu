@@ -349,77 +349,60 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
 }
 
 // Spectral evaluation of the global field at the targets (GGEM_OFFGRID_SPECTRAL),
-// a warp per target.  The oversampled grid holds the field deconvolved by the
-// Gaussian window g(t) = exp(-c t^2) (t in fine spacings), so the window
-// gathered over the 2w nearest fine nodes in x and in z gives the Fourier sum
-// at the target to the window's tolerance (the type-2 non-uniform FFT of
-// Greengard & Lee); in y the values at the Chebyshev-Lobatto nodes are summed
-// with the barycentric weights lambda_j / (y - y_j), lambda_j = (-1)^j halved
-// at both ends, normalised by their sum -- the polynomial through all Ny
-// nodes, i.e. the Chebyshev series (a node hit exactly takes that node).
-// Lanes split into G groups of 32/G: a lane owns one x offset, a group every
-// G-th z row; for each row the y sum runs innermost (one load and one FMA per
-// node and component), then the row's window weight scales it.  The weights
-// (y in T, z in T, row offsets) sit in the warp's shared memory.  Warps take
-// the targets in sg.order (cell order for mesh nodes) so that the stencils of
-// a block overlap in L1.
+// a warp per target: the type-2 non-uniform FFT of Greengard & Lee in all
+// three directions.  In theta = arccos(ybar) the Chebyshev series is a cosine
+// series, even and 2 pi-periodic, so y is treated like x and z: the
+// oversampled grid holds the field deconvolved by the Gaussian window
+// g(t) = exp(-c t^2) (t in fine spacings) on Mx x Mz x the Mt/2 + 1 theta
+// nodes of [0, pi], and the window gathered over the 2w nearest fine nodes in
+// each direction gives the expansion at the target to the window's tolerance
+// (theta nodes beyond 0 or pi are their mirror images).  Lanes split into G
+// groups of 32/G: a lane owns one x offset, a group every G-th z row of each
+// theta plane, so a row's 2w values are one contiguous load per group.  The
+// plane and row offsets and the theta and z weights sit in the warp's shared
+// memory.  Warps take the targets in sg.order (cell order for mesh nodes) so
+// that the stencils of a block overlap in L1.
+template <typename T> __device__ __forceinline__ T wacos(T x);
+template <> __device__ __forceinline__ float wacos<float>(float x) { return acosf(x); }
+template <> __device__ __forceinline__ double wacos<double>(double x) { return acos(x); }
+
 template <typename T>
 __global__ void __launch_bounds__(128, 8) k_interp_spectral(InterpArgs<T> a, SpecGrid sg) {
-    extern __shared__ double spsm[];
+    __shared__ long offs[4][64];                // per warp: 2w theta planes, 2w z rows
+    __shared__ T wts[4][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int k = blockIdx.x * (blockDim.x >> 5) + wib;
     if (k >= a.n) return;                       // warp-uniform
     const int t = sg.order ? sg.order[k] : k;
     const GridGeom& geo = a.geo;
-    const int Ny = geo.Ny, N = Ny - 1, w = sg.w, w2 = 2 * sg.w;
-    // per warp: Ny + 32 T weights, 32 row offsets (laid out in doubles)
-    double* wbase = spsm + (size_t)wib * (Ny + 64);
-    T* by = reinterpret_cast<T*>(wbase);
-    T* wzs = by + Ny;
-    long* roff = reinterpret_cast<long*>(wbase + Ny + 32);
+    const int w = sg.w, w2 = 2 * sg.w, half = sg.Mt / 2;
     const double xt = a.x[3 * (size_t)t], yt = a.x[3 * (size_t)t + 1],
                  zt = a.x[3 * (size_t)t + 2];
-    // Weights in the plan's precision T (GB300 issues FP64 at 1/64 of the FP32
-    // rate; only the coordinate reductions below stay in FP64).
-    T bj[9];                                    // Ny <= 257: at most 9 per lane
-    T part = (T)0;
-    int hit = -1;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-        const int j = lane + 32 * r;
-        bj[r] = (T)0;
-        if (j < Ny) {
-            const T d = (T)(yt - a.yj[j]);
-            T lam = (j & 1) ? (T)-1 : (T)1;
-            if (j == 0 || j == N) lam *= (T)0.5;
-            if (d == (T)0) hit = j;
-            else bj[r] = lam / d;
-            part += bj[r];
-        }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        part += __shfl_xor_sync(0xffffffffu, part, o);
-        hit = max(hit, __shfl_xor_sync(0xffffffffu, hit, o));
-    }
-    const T inv = (T)1 / part;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-        const int j = lane + 32 * r;
-        if (j < Ny) by[j] = bj[r] * inv;
-    }
-    // fine-grid coordinates: integer part wrapped into the period, fraction in T
+    const size_t plane = (size_t)sg.Mz * sg.Mx;
+    const size_t pstride = (size_t)a.ncomp_total * plane;
+    // fine-grid coordinates: integer part wrapped into the period (FP64), the
+    // fraction and the window arithmetic in the plan's precision T
     const double ux = xt * sg.sx, uz = zt * sg.sz;
     const double flx = floor(ux), flz = floor(uz);
     const T fx = (T)(ux - flx), fz = (T)(uz - flz);
     const int px0 = (int)((long long)flx % sg.Mx), pz0 = (int)((long long)flz % sg.Mz);
+    const T yb = (T)fmin(1.0, fmax(-1.0, 2.0 * (yt - geo.y0) / geo.W - 1.0));
+    const T ut = wacos<T>(yb) * (T)sg.st;        // theta in fine spacings, [0, Mt/2]
+    const int pt0 = min((int)floor(ut), half);
+    const T ft = ut - (T)pt0;
     const T cw = (T)sg.c;
     if (lane < w2) {
-        const T tz = fz - (T)(lane - w + 1);
-        wzs[lane] = wexp<T>(-cw * tz * tz);
-        int pz = (pz0 + lane - w + 1) % sg.Mz;
+        const int o = lane - w + 1;
+        const T tt = ft - (T)o, tz = fz - (T)o;
+        int pt = pt0 + o;                       // mirror about 0 and pi
+        pt = pt < 0 ? -pt : pt;
+        pt = pt > half ? sg.Mt - pt : pt;
+        int pz = (pz0 + o) % sg.Mz;
         pz += pz < 0 ? sg.Mz : 0;
-        roff[lane] = (long)pz * sg.Mx;
+        offs[wib][lane] = (long)pt * (long)pstride;
+        offs[wib][32 + lane] = (long)pz * sg.Mx;
+        wts[wib][lane] = wexp<T>(-cw * tt * tt);
+        wts[wib][32 + lane] = wexp<T>(-cw * tz * tz);
     }
     const int lpg = w2 <= 8 ? 8 : (w2 <= 16 ? 16 : 32);
     const int G = 32 / lpg, g = lane / lpg, xl = lane - g * lpg;
@@ -430,32 +413,23 @@ __global__ void __launch_bounds__(128, 8) k_interp_spectral(InterpArgs<T> a, Spe
     px += px < 0 ? sg.Mx : 0;
     __syncwarp();
     const int nc = (a.mode == 0) ? 3 : 6;
-    const size_t plane = (size_t)sg.Mz * sg.Mx;
-    const size_t jstride = (size_t)a.ncomp_total * plane;
     const T* F = (const T*)sg.fine + (size_t)a.comp0 * plane + px;
     T acc[6] = {0, 0, 0, 0, 0, 0};
     if (xv) {
-        for (int jz = g; jz < w2; jz += G) {
-            const T* Fr = F + roff[jz];
+        for (int it = 0; it < w2; ++it) {
+            const T* Ft = F + offs[wib][it];
+            const T wt = wts[wib][it];
             T sum[6] = {0, 0, 0, 0, 0, 0};
-            if (hit >= 0) {                     // on a Chebyshev node (warp-uniform)
-                const T* Fj = Fr + (size_t)hit * jstride;
+#pragma unroll 4
+            for (int iz = g; iz < w2; iz += G) {
+                const T b = wts[wib][32 + iz];
+                const T* Fr = Ft + offs[wib][32 + iz];
 #pragma unroll
                 for (int c = 0; c < 6; ++c)
-                    if (c < nc) sum[c] = Fj[c * plane];
-            } else {
-#pragma unroll 4
-                for (int j = 0; j < Ny; ++j) {
-                    const T b = by[j];
-                    const T* Fj = Fr + (size_t)j * jstride;
-#pragma unroll
-                    for (int c = 0; c < 6; ++c)
-                        if (c < nc) sum[c] += b * Fj[c * plane];
-                }
+                    if (c < nc) sum[c] += b * Fr[c * plane];
             }
-            const T wz = wzs[jz];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) acc[c] += wz * sum[c];
+            for (int c = 0; c < 6; ++c) acc[c] += wt * sum[c];
         }
     }
 #pragma unroll
@@ -466,6 +440,36 @@ __global__ void __launch_bounds__(128, 8) k_interp_spectral(InterpArgs<T> a, Spe
         acc[c] = v;
     }
     if (lane == 0) interp_store<T>(a, t, acc);
+}
+
+// Rectangular contraction out[p][col] = sum_n M[p][n] in[n][col] (M: R x C),
+// for the Chebyshev coefficients -> deconvolved theta-node values of the
+// spectral evaluation; a block takes RT rows of M into shared memory.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_cheb_rect(int R, int C, int RT, const T* __restrict__ M,
+                                                    const T* __restrict__ in,
+                                                    T* __restrict__ out, long cols) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* Ms = reinterpret_cast<T*>(smraw);
+    const int r0 = blockIdx.y * RT, rt = min(RT, R - r0);
+    for (int e = threadIdx.x; e < rt * C; e += blockDim.x) Ms[e] = M[(size_t)r0 * C + e];
+    __syncthreads();
+    const long col = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= cols) return;
+    for (int q0 = 0; q0 < rt; q0 += NB) {
+        T acc[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[b] = 0;
+        for (int n = 0; n < C; ++n) {
+            const T v = in[(long)n * cols + col];
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (q0 + b < rt) acc[b] += Ms[(q0 + b) * C + n] * v;
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (q0 + b < rt) out[(long)(r0 + q0 + b) * cols + col] = acc[b];
+    }
 }
 
 // Deconvolve and zero-pad the spectral planes onto the oversampled grid: fine
@@ -536,13 +540,22 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
     InterpArgs<T> a{geo, yj, grid, ncomp_total, comp0, mode, n_tgt, x_tgt, local,
                     local_stride, nrm, qself, wself, self_coef, out, out_stride};
     if (spec) {
-        // a warp per target, 4 per block; per warp Ny barycentric weights,
-        // 32 z-window values and 32 row offsets in shared memory
-        const size_t smem = (size_t)4 * (geo.Ny + 64) * sizeof(double);
-        k_interp_spectral<T><<<(n_tgt + 3) / 4, 128, smem, st>>>(a, *spec);
+        // a warp per target, 4 per block
+        k_interp_spectral<T><<<(n_tgt + 3) / 4, 128, 0, st>>>(a, *spec);
     } else {
         k_interp<T><<<(n_tgt + 127) / 128, 128, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cheb_rect(int R, int C, const T* M, const T* in, T* out, long cols,
+                      cudaStream_t st) {
+    const int RT = 32;
+    const dim3 grid((unsigned)((cols + 255) / 256), (unsigned)((R + RT - 1) / RT));
+    const size_t smem = (size_t)RT * C * sizeof(T);
+    grant_max_smem((const void*)k_cheb_rect<T, 8>);
+    k_cheb_rect<T, 8><<<grid, 256, smem, st>>>(R, C, RT, M, in, out, cols);
     return cudaGetLastError();
 }
 
@@ -568,7 +581,8 @@ cudaError_t spectral_pad(const GridGeom& geo, const T* spec, int nplanes, int Mx
                                            const double*, const double*, double, int, double*, \
                                            int, cudaStream_t, const SpecGrid*);                   \
     template cudaError_t spectral_pad<T>(const GridGeom&, const T*, int, int, int, const T*,   \
-                                         const T*, T*, cudaStream_t);
+                                         const T*, T*, cudaStream_t);                          \
+    template cudaError_t cheb_rect<T>(int, int, const T*, const T*, T*, long, cudaStream_t);
 GGEM_INST_GRID(float)
 GGEM_INST_GRID(double)
 

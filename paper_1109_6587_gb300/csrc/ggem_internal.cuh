@@ -192,7 +192,9 @@ struct ggem_plan {
     // spectral off-grid evaluation (ggem_set_offgrid)
     int offgrid = 0;                   // GGEM_OFFGRID_*
     int spec_w = 0;                    // Gaussian window half-width (fine points per side)
-    void* d_spec = nullptr;            // [Ny][9][2Nz][2Nx] T oversampled grid
+    void* d_spec = nullptr;            // [2Ny-1][9][2Nz][2Nx] T oversampled grid
+    void* d_spec_mid = nullptr;        // [2Ny-1][9][Nz][Nx] T theta planes, x-z spectral
+    void* d_spec_ct = nullptr;         // [2Ny-1][Ny] T Chebyshev -> theta-node matrix
     void* d_spec_twx = nullptr;        // FFT twiddles of lengths 2Nx and 2Nz, laid out as
     void* d_spec_twz = nullptr;        //   d_tw_x / d_tw_z
     void* d_spec_dx = nullptr;         // [Nx/2] T deconvolution factors, k_x >= 0
@@ -375,13 +377,14 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
 // mode 1: stress (6), out = local + interp
 // mode 2: double layer, out_j = local_j + n_k sigma_jk / mu
 // Oversampled grid of the spectral off-grid evaluation: physical values
-// [Ny][ncomp_total][Mz][Mx] of the field deconvolved by the Gaussian window
-// exp(-c t^2) (t in fine-grid spacings), gathered over w points per side.
+// [Mt/2 + 1][ncomp_total][Mz][Mx] of the field deconvolved by the Gaussian
+// window exp(-c t^2) (t in fine spacings) at theta = 2 pi p / Mt (theta =
+// arccos of the normalised y), gathered over w points per side.
 struct SpecGrid {
     const void* fine;
-    int Mx, Mz, w;
+    int Mx, Mz, Mt, w;
     double c;
-    double sx, sz;      // Mx / Lx, Mz / Lz: fine spacings per unit length
+    double sx, sz, st;  // Mx / Lx, Mz / Lz, Mt / (2 pi): fine spacings per unit
     const int* order;   // target processing order (nullptr: 0..n-1)
 };
 
@@ -402,5 +405,10 @@ cudaError_t interp_combine(const GridGeom& geo, const double* yj, const T* grid,
 template <typename T>
 cudaError_t spectral_pad(const GridGeom& geo, const T* spec, int nplanes, int Mx, int Mz,
                          const T* dx, const T* dz, T* fine, cudaStream_t st);
+
+// out[p][col] = sum_n M[p][n] in[n][col], M: R x C (row-major), in: [C][cols].
+template <typename T>
+cudaError_t cheb_rect(int R, int C, const T* M, const T* in, T* out, long cols,
+                      cudaStream_t st);
 
 }  // namespace ggem

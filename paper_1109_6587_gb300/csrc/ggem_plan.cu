@@ -63,8 +63,10 @@ SpecGrid spec_grid(const ggem_plan_t* P) {
     g.Mz = 2 * P->prm.Nz;
     g.w = P->spec_w;
     g.c = spec_c(P->spec_w);
+    g.Mt = 4 * (P->prm.Ny - 1);
     g.sx = g.Mx / P->prm.Lx;
     g.sz = g.Mz / P->prm.Lz;
+    g.st = g.Mt / (2.0 * kPi);
     g.order = nullptr;
     return g;
 }
@@ -174,24 +176,31 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
                             P->d_ksw, out_sel, A, st));
     });
     int nout = nout_of(out_sel);
-    stage(P, ST_CHEB_INV, 1, [&] {
-        GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
-                              (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm, P->d_tc_inv));
-    });
     if (P->offgrid == GGEM_OFFGRID_SPECTRAL) {
-        // deconvolve onto the oversampled grid and transform there
+        // Chebyshev coefficients -> deconvolved theta-node values, then
+        // deconvolve in x, z onto the oversampled grid and transform there
+        const int nth = 2 * geo.Ny - 1;
+        T* mid = (T*)P->d_spec_mid;
+        stage(P, ST_CHEB_INV, 1, [&] {
+            GG_CUDA(cheb_rect<T>(nth, geo.Ny, (const T*)P->d_spec_ct, A, mid,
+                                 (long)nout * P->nmodes * 2, st));
+        });
         stage(P, ST_FFT_INV, 3, [&] {
             GridGeom fg = geo;
             fg.Nx = 2 * geo.Nx;
             fg.Nz = 2 * geo.Nz;
             fg.nkx = geo.Nx;
-            GG_CUDA(spectral_pad<T>(geo, B, geo.Ny * nout, fg.Nx, fg.Nz, (const T*)P->d_spec_dx,
+            GG_CUDA(spectral_pad<T>(geo, mid, nth * nout, fg.Nx, fg.Nz, (const T*)P->d_spec_dx,
                                     (const T*)P->d_spec_dz, (T*)P->d_spec, st));
-            GG_CUDA(fft_inverse<T>(fg, (T*)P->d_spec, geo.Ny * nout, P->d_spec_twx,
+            GG_CUDA(fft_inverse<T>(fg, (T*)P->d_spec, nth * nout, P->d_spec_twx,
                                    P->d_spec_twz, st));
         });
         return;
     }
+    stage(P, ST_CHEB_INV, 1, [&] {
+        GG_CUDA(cheb_apply<T>(geo.Ny, (const T*)P->d_cheb_inv, A, B,
+                              (long)nout * P->nmodes * 2, st, P->d_tc_err, P->nsm, P->d_tc_inv));
+    });
     stage(P, ST_FFT_INV, 2, [&] {
         GG_CUDA(fft_inverse<T>(geo, B, geo.Ny * nout, P->d_tw_x, P->d_tw_z, st));
     });
@@ -420,17 +429,22 @@ void upload_tables(ggem_plan_t* P, const std::vector<double>& cf, const std::vec
 }
 
 // Oversampled grid, its FFT tables and the deconvolution factors of the
-// spectral off-grid evaluation with window half-width w.  The factor of mode
-// l is 1 / (M ghat(l)) with ghat(l) = sqrt(tau/pi) exp(-l^2 tau) the Fourier
-// coefficient of the periodised window; 1/M is the trapezoidal weight of the
-// gather on M fine nodes.  Nyquist modes get 0.
+// spectral off-grid evaluation with window half-width w.  In x (and z) the
+// factor of mode l is 1 / (M ghat(l)), ghat(l) = sqrt(tau/pi) exp(-l^2 tau)
+// the Fourier coefficient of the periodised window and 1/M the trapezoidal
+// weight of the gather on M fine nodes; Nyquist modes get 0.  In theta the
+// Chebyshev series sum a_n cos(n theta) has frequencies |n| <= N = Ny - 1, so
+// 2N modes oversampled 2x give Mt = 4N nodes over [0, 2 pi), of which the
+// 2N + 1 in [0, pi] are stored (the series is even); the deconvolution of
+// degree n is folded into the matrix taking the coefficients to those nodes.
 template <typename T>
 void spec_setup(ggem_plan_t* P, int w) {
     const int Nx = P->prm.Nx, Nz = P->prm.Nz, Ny = P->prm.Ny;
-    const int Mx = 2 * Nx, Mz = 2 * Nz;
+    const int Mx = 2 * Nx, Mz = 2 * Nz, N = Ny - 1, Mt = 4 * N, nth = 2 * N + 1;
     if (!P->d_spec) {
         // up to 9 components: velocity and stress of ggem_point_forces
-        dalloc(P, (T**)&P->d_spec, (size_t)Ny * 9 * Mz * Mx);
+        dalloc(P, (T**)&P->d_spec, (size_t)nth * 9 * Mz * Mx);
+        dalloc(P, (T**)&P->d_spec_mid, (size_t)nth * 9 * Nz * Nx);
         std::vector<double> twx, twz;
         fft_tables(Mx, Mz, twx, twz);
         std::vector<T> a(twx.begin(), twx.end()), b(twz.begin(), twz.end());
@@ -442,11 +456,14 @@ void spec_setup(ggem_plan_t* P, int w) {
                            cudaMemcpyHostToDevice));
         dalloc(P, (T**)&P->d_spec_dx, (size_t)Nx / 2);
         dalloc(P, (T**)&P->d_spec_dz, (size_t)Nz);
+        dalloc(P, (T**)&P->d_spec_ct, (size_t)nth * Ny);
     }
     if (w == P->spec_w) return;
     const double den = kSpecR * (kSpecR - 0.5);
-    const double taux = kPi * w / ((double)Nx * Nx * den), tauz = kPi * w / ((double)Nz * Nz * den);
-    std::vector<T> dx(Nx / 2), dz(Nz);
+    const double taux = kPi * w / ((double)Nx * Nx * den);
+    const double tauz = kPi * w / ((double)Nz * Nz * den);
+    const double taut = kPi * w / (4.0 * N * N * den);
+    std::vector<T> dx(Nx / 2), dz(Nz), ct((size_t)nth * Ny);
     for (int l = 0; l < Nx / 2; ++l)
         dx[l] = (T)(std::sqrt(kPi / taux) * std::exp((double)l * l * taux) / Mx);
     for (int k = 0; k < Nz; ++k) {
@@ -454,9 +471,16 @@ void spec_setup(ggem_plan_t* P, int w) {
         dz[k] = k == Nz / 2 ? (T)0
                             : (T)(std::sqrt(kPi / tauz) * std::exp((double)m * m * tauz) / Mz);
     }
+    for (int p = 0; p < nth; ++p)
+        for (int n = 0; n < Ny; ++n) {
+            const double d = std::sqrt(kPi / taut) * std::exp((double)n * n * taut) / Mt;
+            const double th = 2.0 * kPi * (double)((long)n * p % Mt) / Mt;
+            ct[(size_t)p * Ny + n] = (T)(d * std::cos(th));
+        }
     GG_CUDA(cudaStreamSynchronize(P->st));     // no launch may still read the old factors
     GG_CUDA(cudaMemcpy(P->d_spec_dx, dx.data(), dx.size() * sizeof(T), cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_spec_dz, dz.data(), dz.size() * sizeof(T), cudaMemcpyHostToDevice));
+    GG_CUDA(cudaMemcpy(P->d_spec_ct, ct.data(), ct.size() * sizeof(T), cudaMemcpyHostToDevice));
     P->spec_w = w;
 }
 
@@ -722,7 +746,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
                     P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
-                    P->d_spec_dz};
+                    P->d_spec_dz, P->d_spec_mid, P->d_spec_ct};
     for (void* p : ptrs) dfree(p);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
