@@ -111,17 +111,19 @@ enum { GGEM_OFFGRID_LAGRANGE = 0, GGEM_OFFGRID_SPECTRAL = 1 };   /* ggem_set_off
  *   GGEM_OFFGRID_SPECTRAL: the Fourier (x, z) x Chebyshev (y) expansion of the
  *     global solution itself, evaluated to a tolerance rather than
  *     interpolated, so that the error off the mesh decays as fast as on it
- *     (the non-uniform FFT route that Sec. 3.2.3 points to).  In x and z the
- *     modes are deconvolved by a Gaussian window, transformed on a grid
- *     oversampled 2x, and gathered with the window over 2 half_width points
- *     per direction (Greengard & Lee's type-2 non-uniform FFT); in y the
- *     Chebyshev polynomial is evaluated by the barycentric formula on all Ny
- *     nodes.  half_width: 0 selects 12 for FP64-accurate plans (window error
- *     ~1e-13) and 6 for GGEM_MIXED (~2e-7); otherwise 2..16.  Cost per target
- *     ~Ny (2 half_width)^2 per output component, against 125 for Lagrange.
- * Allocates the oversampled grid (Ny x 9 x 2Nz x 2Nx values of the plan's
- * precision) on the first switch to GGEM_OFFGRID_SPECTRAL; a mixed plan's
- * FP64 twin follows the setting (with its own default width).
+ *     (the non-uniform FFT route that Sec. 3.2.3 points to): Greengard &
+ *     Lee's type-2 non-uniform FFT with a Gaussian window in x, z and
+ *     theta = arccos of the normalised y (where the Chebyshev series is a
+ *     cosine series) -- modes deconvolved by the window, transformed onto a
+ *     grid oversampled 2x in each direction, and the window gathered over
+ *     2 half_width points per direction at each target.  half_width: 0
+ *     selects 12 for FP64-accurate plans (window error ~1e-13) and 6 for
+ *     GGEM_MIXED (~2e-7); otherwise 2..16.  Cost per target (2 half_width)^3
+ *     per output component, against 125 for Lagrange.
+ * Allocates the oversampled grid ((2Ny - 1) x 9 x 2Nz x 2Nx values of the
+ * plan's precision, plus (2Ny - 1) x 9 x Nz x Nx) on the first switch to
+ * GGEM_OFFGRID_SPECTRAL; a mixed plan's FP64 twin follows the setting (with
+ * its own default width).
  * Returns GGEM_ERR_INVALID_ARG for an unknown mode or width.
  */
 ggem_status ggem_set_offgrid(ggem_plan_t *plan, int mode, int half_width);
