@@ -24,7 +24,9 @@ GOLD = pathlib.Path(__file__).resolve().parent / "golden"
 CASES = {"capsules100_phi": W.capsules_100_phi, "capsules1000_phi": W.capsules_1000_phi}
 RUNS = [("capsules100_phi", "mixed", "nodal"), ("capsules100_phi", "mixed", "element"),
         ("capsules100_phi", "fp64_emulated", "element"), ("capsules100_phi", "fp64", "nodal"),
-        ("capsules100_phi", "fp64", "element")]
+        ("capsules100_phi", "fp64", "element"),
+        ("capsules1000_phi", "mixed", "nodal"), ("capsules1000_phi", "mixed", "element"),
+        ("capsules1000_phi", "fp64_emulated", "element"), ("capsules1000_phi", "fp64", "nodal")]
 
 
 @pytest.fixture(scope="module")
