@@ -123,16 +123,18 @@ __global__ void k_fft_x_c2r(c2_t<T>* data, long nrows, int M, int logM,
     }
 }
 
-// Complex transform along z: planes of [Nz][nkx] complex, TB columns per block.
+// Complex transform along z: planes of [Nz][nkx] complex, TB columns per block;
+// only the first ncols columns of each plane (the others hold zeros and stay
+// zero).
 template <typename T>
-__global__ void k_fft_z(c2_t<T>* data, int nkx, int Nz, int logNz,
+__global__ void k_fft_z(c2_t<T>* data, int nkx, int ncols, int Nz, int logNz,
                         const c2_t<T>* __restrict__ tw, int TB, bool inv) {
     extern __shared__ __align__(16) unsigned char smraw[];
     c2_t<T>* s = reinterpret_cast<c2_t<T>*>(smraw);
-    int ncb = (nkx + TB - 1) / TB;
+    int ncb = (ncols + TB - 1) / TB;
     long plane = blockIdx.x / ncb;
     int col0 = (blockIdx.x - plane * ncb) * TB;
-    int tb = min(TB, nkx - col0);
+    int tb = min(TB, ncols - col0);
     c2_t<T>* base = data + plane * (long)Nz * nkx + col0;
     for (int e = threadIdx.x; e < Nz * TB; e += blockDim.x) {
         int z = e / TB, c = e - z * TB;
@@ -171,16 +173,17 @@ static cudaError_t fft_x(const GridGeom& geo, T* data, int nplanes, const void* 
 
 template <typename T>
 static cudaError_t fft_z(const GridGeom& geo, T* data, int nplanes, const void* tw_z, bool inv,
-                         cudaStream_t st) {
+                         cudaStream_t st, int ncols = 0) {
     int Nz = geo.Nz, logNz = ilog2(Nz), nkx = geo.Nx / 2;
-    int TB = min(nkx, 8);
+    if (ncols <= 0 || ncols > nkx) ncols = nkx;
+    int TB = min(ncols, 8);
     // (the oversampled grids of the spectral evaluation reach Nz = 2048)
     while (TB > 1 && (size_t)TB * Nz * sizeof(c2_t<T>) > (size_t)160 * 1024) TB >>= 1;
     size_t smem = (size_t)TB * Nz * sizeof(c2_t<T>);
-    unsigned nb = (unsigned)((long)nplanes * ((nkx + TB - 1) / TB));
+    unsigned nb = (unsigned)((long)nplanes * ((ncols + TB - 1) / TB));
     grant_max_smem((const void*)k_fft_z<T>);
-    k_fft_z<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nkx, Nz, logNz, (const c2_t<T>*)tw_z, TB,
-                                      inv);
+    k_fft_z<T><<<nb, 256, smem, st>>>((c2_t<T>*)data, nkx, ncols, Nz, logNz,
+                                      (const c2_t<T>*)tw_z, TB, inv);
     return cudaGetLastError();
 }
 
@@ -194,8 +197,8 @@ cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* t
 
 template <typename T>
 cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
-                        const void* tw_z, cudaStream_t st) {
-    cudaError_t e = fft_z<T>(geo, data, nplanes, tw_z, true, st);
+                        const void* tw_z, cudaStream_t st, int active_kx) {
+    cudaError_t e = fft_z<T>(geo, data, nplanes, tw_z, true, st, active_kx);
     if (e != cudaSuccess) return e;
     return fft_x<T>(geo, data, nplanes, tw_x, true, st);
 }
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(128, 8) k_interp_spectral(InterpArgs<T> a, Spe
     const double flx = floor(ux), flz = floor(uz);
     const T fx = (T)(ux - flx), fz = (T)(uz - flz);
     const int px0 = (int)((long long)flx % sg.Mx), pz0 = (int)((long long)flz % sg.Mz);
-    const T yb = (T)fmin(1.0, fmax(-1.0, 2.0 * (yt - geo.y0) / geo.W - 1.0));
+    const T yb = (T)fmin(1.0, fmax(-1.0, (yt - geo.y0) * sg.sy - 1.0));
     const T ut = wacos<T>(yb) * (T)sg.st;        // theta in fine spacings, [0, Mt/2]
     const int pt0 = min((int)floor(ut), half);
     const T ft = ut - (T)pt0;
@@ -573,7 +576,7 @@ cudaError_t spectral_pad(const GridGeom& geo, const T* spec, int nplanes, int Mx
     template cudaError_t fft_forward<T>(const GridGeom&, T*, int, const void*, const void*,    \
                                         cudaStream_t);                                         \
     template cudaError_t fft_inverse<T>(const GridGeom&, T*, int, const void*, const void*,    \
-                                        cudaStream_t);                                         \
+                                        cudaStream_t, int);                                    \
     template cudaError_t cheb_apply<T>(int, const T*, const T*, T*, long, cudaStream_t, int*,  \
                                        int, const void*);                                      \
     template cudaError_t interp_combine<T>(const GridGeom&, const double*, const T*, int, int, \

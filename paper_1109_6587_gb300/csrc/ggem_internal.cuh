@@ -356,7 +356,7 @@ cudaError_t fft_forward(const GridGeom& geo, T* data, int nplanes, const void* t
                         const void* tw_z, cudaStream_t st);
 template <typename T>
 cudaError_t fft_inverse(const GridGeom& geo, T* data, int nplanes, const void* tw_x,
-                        const void* tw_z, cudaStream_t st);
+                        const void* tw_z, cudaStream_t st, int active_kx = 0);
 
 template <typename T>
 cudaError_t cheb_apply(int Ny, const T* M, const T* in, T* out, long cols, cudaStream_t st,
@@ -385,6 +385,7 @@ struct SpecGrid {
     int Mx, Mz, Mt, w;
     double c;
     double sx, sz, st;  // Mx / Lx, Mz / Lz, Mt / (2 pi): fine spacings per unit
+    double sy;          // 2 / W: normalised y = (y - y0) sy - 1
     const int* order;   // target processing order (nullptr: 0..n-1)
 };
 

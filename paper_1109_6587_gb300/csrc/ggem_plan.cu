@@ -67,6 +67,7 @@ SpecGrid spec_grid(const ggem_plan_t* P) {
     g.sx = g.Mx / P->prm.Lx;
     g.sz = g.Mz / P->prm.Lz;
     g.st = g.Mt / (2.0 * kPi);
+    g.sy = 2.0 / P->prm.W;
     g.order = nullptr;
     return g;
 }
@@ -192,8 +193,9 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
             fg.nkx = geo.Nx;
             GG_CUDA(spectral_pad<T>(geo, mid, nth * nout, fg.Nx, fg.Nz, (const T*)P->d_spec_dx,
                                     (const T*)P->d_spec_dz, (T*)P->d_spec, st));
+            // (only the coarse grid's Nx/2 columns in x are nonzero for the z pass)
             GG_CUDA(fft_inverse<T>(fg, (T*)P->d_spec, nth * nout, P->d_spec_twx,
-                                   P->d_spec_twz, st));
+                                   P->d_spec_twz, st, geo.Nx / 2));
         });
         return;
     }
