@@ -2,10 +2,10 @@
 against the oracle's expansion summed at each point.
 
 The GPU evaluates the expansion by a Gaussian-window non-uniform FFT (2x
-oversampling) in x, z and the barycentric Chebyshev formula in y, so it
-differs from the oracle's direct sum by the window's tolerance (~1e-13 at the
-FP64 default half-width 12, ~2e-7 at the mixed default 6) on top of the usual
-parity.  Bars as everywhere: 1e-10 for FP64 and FP64-emulated plans, 1e-5 for
+oversampling) in x, z and theta = arccos of the normalised y (where the
+Chebyshev series is a cosine series), so it differs from the oracle's direct
+sum by the window's tolerance (~1e-13 at the FP64 default half-width 12,
+~2e-7 at the mixed default 6) on top of the usual parity.  Bars as everywhere: 1e-10 for FP64 and FP64-emulated plans, 1e-5 for
 mixed, max |gpu - oracle| / max |oracle|.
 """
 import math
