@@ -1,7 +1,8 @@
-// Grid-side kernels of the GGEM global problem (paper Sec. 3.2.2, 3.4.2, App. C):
-//   spreading of the global density rho_g onto the Fourier x Chebyshev grid,
-//   FFTs in x (real) and z (complex), the Chebyshev transforms in y as a dense
-//   contraction, and 5x5x5 Lagrange interpolation back to the targets.
+// Grid-side kernels of the GGEM global problem (paper Sec. 3.2.2, 3.2.3, 3.4.2,
+// App. C): FFTs in x (real) and z (complex), the Chebyshev transforms in y as a
+// dense contraction, 5x5x5 Lagrange interpolation back to the targets, and the
+// spectral off-grid evaluation (deconvolution onto an oversampled grid and a
+// Gaussian-window gather: a type-2 non-uniform FFT).
 //
 // Grid layout: physical [Ny][comp][Nz][Nx] (real T); after the x transform
 // each row of Nx reals holds Nx/2 complex modes k_x = 0..Nx/2-1 in place (the
