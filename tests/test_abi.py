@@ -63,3 +63,7 @@ def test_null_arguments_rejected(built):
     assert built.ggem_plan(None, None, None) == 1
     assert built.ggem_single_layer(None, None, None) == 1
     assert built.ggem_plan_destroy(None) == 0
+    # every entry point that takes a plan refuses a NULL one before any device work
+    assert built.ggem_set_offgrid(None, 1, 0) == 1
+    assert built.ggem_double_layer(None, None, None) == 1
+    assert built.ggem_mesh_set(None, 0, None, 0, None) == 1
