@@ -826,6 +826,7 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
         GG_CHECK(n_tris >= 0 && n_tris <= P->cap_tris, GGEM_ERR_CAPACITY,
                  "more triangles than max_tris");
         GG_CHECK(n_tris == 0 || tri, GGEM_ERR_INVALID_ARG, "triangles pointer is NULL");
+        P->mesh_ready = false;         // until the new mesh has passed every check
         cudaStream_t st = P->st;
         auto kind = [](const void* p) {
             return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

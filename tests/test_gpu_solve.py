@@ -143,6 +143,31 @@ def test_argument_errors(ggem, case):
         assert e.value.status == 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_non_finite_inputs(ggem, case, prec):
+    """Injected faults on the host: a NaN in the right-hand side ends the solve
+    with GGEM_ERR_NUMERICAL (non-finite residual), a NaN node coordinate is
+    refused by ggem_mesh_set; the plan stays usable after both."""
+    s, kappa, b = case
+    P = _plan(ggem, s, prec, "nodal")
+    bad = b.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(ggem.GGEMError) as e:
+        P.bie_solve(_dev(kappa), _dev(bad), tol=1e-6)
+    assert e.value.status == 4
+    x = s.x.copy()
+    x[3, 0] = np.nan
+    with pytest.raises(ggem.GGEMError) as e:
+        P.mesh_set(_dev(x), torch.as_tensor(s.tri, device="cuda"))
+    assert e.value.status == 1
+    with pytest.raises(ggem.GGEMError):          # the refused mesh leaves none set
+        P.single_layer(_dev(b))
+    P.mesh_set(_dev(s.x), torch.as_tensor(s.tri, device="cuda"))
+    q, its, rr, st = P.bie_solve(_dev(kappa), _dev(b), tol=1e-6)
+    assert st == OK and rr <= 1e-6
+    P.check()
+
+
 def test_mixed_solve_100_capsules_sampled_residual(ggem):
     s = W.capsules_100()
     n = s.x.shape[0]
