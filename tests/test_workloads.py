@@ -57,3 +57,13 @@ def test_single_capsule_meshes(level, nodes):
                      centres=np.array([[4.0, 0.0, 4.0]]))
     _check_suspension(s, 1, nodes)
     assert np.allclose(np.linalg.norm(s.x - s.centres[0], axis=1), 1.0)
+
+
+def test_biconcave_workload():
+    s = W.rbc_4000()
+    _check_suspension(s, 4000, 642)
+    # each cell is the Evans-Fung shape of radius 1: its volume is 1.56 R0^3
+    x = s.x[s.tri]
+    vol = np.einsum("ij,ij->i", x[:, 0], np.cross(x[:, 1], x[:, 2])) / 6.0
+    per = np.bincount(s.particle[s.tri[:, 0]], weights=vol)
+    assert np.allclose(per, per[0]) and abs(per[0] - 1.56) < 0.03
