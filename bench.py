@@ -375,8 +375,8 @@ def cpu_baseline(susp, args, stride=64):
     rc = O.default_rcut(a)
     _, _, _, nb = O.geometry(susp.x, susp.tri)
     t0 = time.perf_counter()
-    O.single_layer(susp, q, quadrature=args.quadrature, targets=idx)
-    O.double_layer(susp, q, quadrature=args.quadrature, targets=idx)
+    O.single_layer(susp, q, quadrature=args.quadrature, targets=idx, offgrid=args.offgrid)
+    O.double_layer(susp, q, quadrature=args.quadrature, targets=idx, offgrid=args.offgrid)
     t_sample = time.perf_counter() - t0
     t0 = time.perf_counter()
     if args.quadrature == "element":
@@ -391,9 +391,10 @@ def cpu_baseline(susp, args, stride=64):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": n / dt / 1e6, "unit": "Mpts/s", "cores": cores,
             "kind": "oracle", "seconds": dt, "measured_seconds": t_sample + t_local,
-            "sample": f"FP64 single + double layer ({args.quadrature} quadrature): both "
-                      f"global parts in full, the local part at every {stride}th node "
-                      f"({len(idx)} of {n}) scaled to all nodes; OpenMP over targets"}
+            "sample": f"FP64 single + double layer ({args.quadrature} quadrature, "
+                      f"{args.offgrid} off-grid evaluation): both global parts in full, the "
+                      f"local part at every {stride}th node ({len(idx)} of {n}) scaled to "
+                      f"all nodes; OpenMP over targets"}
 
 
 def solve_metrics(args, susp, dev, train_steps=3, timed_steps=2):
