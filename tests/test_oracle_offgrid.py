@@ -20,6 +20,7 @@ tolerance) removes that limit.  Facts that fix the oracle's
 import dataclasses
 
 import numpy as np
+import pytest
 
 from oracle import oracle as O
 from paper_1109_6587_gb300 import workloads as W
@@ -120,3 +121,29 @@ def test_layers_at_sampled_nodes_match_all_nodes():
         full = O.single_layer(s, q, quad, offgrid="spectral")
         part = O.single_layer(s, q, quad, targets=tsel, offgrid="spectral")
         assert np.abs(full[tsel] - part).max() < 1e-13 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("mistake", ["sign_kx", "swap_xz", "y_reversed"])
+def test_planted_mistakes_fail_the_pin(monkeypatch, mistake):
+    """The band-limited pin catches the plausible slips of a spectral sum: a
+    wavenumber of the wrong sign, x and z exchanged, the Chebyshev variable
+    running the wrong way."""
+    box = dataclasses.replace(W.box_single_sphere(), Lx=8.0, Lz=6.0)
+    f = _analytic_field(box)
+    Y, Z, X = np.meshgrid(O.grid_y(box), O.grid_z(box), O.grid_x(box), indexing="ij")
+    field = f(X, Y, Z)[None]
+    rng = np.random.default_rng(1)
+    xt = np.stack([rng.uniform(-3, 11, 30), rng.uniform(box.y0, box.y0 + box.W, 30),
+                   rng.uniform(-2, 9, 30)], 1)
+    exact = f(xt[:, 0], xt[:, 1], xt[:, 2])
+    good = O.mode_wavenumbers
+    if mistake == "sign_kx":
+        monkeypatch.setattr(O, "mode_wavenumbers",
+                            lambda b: (lambda KX, KZ, nyq: (-KX, KZ, nyq))(*good(b)))
+        v = O.spectral_eval(box, field, xt)[:, 0]
+    elif mistake == "swap_xz":
+        v = O.spectral_eval(box, field, xt[:, [2, 1, 0]])[:, 0]
+    else:
+        ymir = 2 * box.y0 + box.W - xt[:, 1]
+        v = O.spectral_eval(box, field, np.stack([xt[:, 0], ymir, xt[:, 2]], 1))[:, 0]
+    assert np.abs(v - exact).max() > 1e-3
