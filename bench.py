@@ -19,6 +19,11 @@ filled to volume fractions 0.1 and 0.2, 245,244 and 3,923,904 points) measure
 the same step at the larger configurations; the pair counts of their roofline
 are taken on a sample of 20,000 targets.
 
+The off-grid evaluation of the global part is the paper's 5-point Lagrange
+interpolation by default; --offgrid spectral times the spectrally accurate
+evaluation instead, and the default run reports the other mode's step under
+"offgrid_other".
+
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
 GPU (the evaluation is one problem per GPU; no collective), value = sum of
