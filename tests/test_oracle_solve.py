@@ -111,8 +111,9 @@ def test_block_diagonal_preconditioner_ceiling():
     the exact inverse of every node's 3x3 diagonal block of the discrete
     operator (I + kappa/4pi D) as a right preconditioner saves no GMRES
     iteration on two capsules, while the exact inverse of each particle's
-    whole block halves the count -- the operator's spread comes from
-    particle-scale modes (normal and rigid-body densities), not from node-local
+    whole block halves the count, and so does one block shared by both (the
+    inverse of an isolated capsule's block at the slit centre): the operator's
+    spread comes from coupling across each particle, not from node-local
     coupling."""
     V, F = W.icosphere(1)
     box = W.Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=16, Ny=17, Nz=16)
@@ -141,3 +142,14 @@ def test_block_diagonal_preconditioner_ceiling():
         plain = its(np.eye(3 * n))
         assert its(node) >= plain - 1
         assert its(part) <= plain // 2 + 1
+        # one shared block, from an isolated capsule at the slit centre, for both
+        c = np.array([4.0, 0.0, 4.0])
+        r = W.Suspension(box=box, x=0.97 * V + c, tri=F, particle=np.zeros(len(V), np.int32),
+                         centres=c[None], radius=0.97)
+        Ar = np.stack([O.bie_operator(r, np.full(len(V), kap), e.reshape(len(V), 3)).ravel()
+                       for e in np.eye(m)], 1)
+        shared = np.zeros_like(A)
+        for p in range(2):
+            sl = slice(p * m, (p + 1) * m)
+            shared[sl, sl] = np.linalg.inv(Ar)
+        assert its(shared) <= plain // 2 + 1
