@@ -177,7 +177,8 @@ ggem_status ggem_local_sum(ggem_plan_t *plan, int n_src, const double *x_src,
  * Single-layer integral at the mesh nodes (Sec. 3.4, Eq. (sl_t)):
  *   w_j(z) = int_S q_i(x) G_ji(z, x) dS(x),   q, w: [n_nodes][3].
  * Local part by the plan's quadrature, global part from the trapezoidal
- * nodal strengths A_b q_b spread with rho_g (Eq. (rhog_sum)).
+ * nodal strengths A_b q_b spread with rho_g (Eq. (rhog_sum)) and evaluated at
+ * the nodes by the plan's off-grid mode (ggem_set_offgrid).
  */
 ggem_status ggem_single_layer(ggem_plan_t *plan, const double *q, double *w);
 
