@@ -161,7 +161,15 @@ def _zeros_like_target(ref, shape):
 
 
 class Plan:
-    """A ggem plan (grid, tables, workspaces) bound to one CUDA stream."""
+    """A ggem plan (grid, tables, workspaces) bound to one CUDA stream.
+
+    Lx, Lz, W, y0, Nx, Ny, Nz: periodic box, slit and grid (Nx, Nz powers of
+    two, Ny Chebyshev-Lobatto nodes); alpha, rcut_factor: the GGEM split (0
+    selects alpha = 1/(2h), r_cut = 4/alpha); precision: "fp64", "mixed" or
+    "fp64_emulated"; quadrature: "nodal" or "element"; max_points, max_tris:
+    capacities; stream: a CUDA stream handle (default torch's current one);
+    offgrid: "lagrange" (5-point interpolation) or "spectral" (the expansion
+    evaluated by a non-uniform FFT, half-width offgrid_width, 0 = default)."""
 
     def __init__(self, Lx, Lz, W, y0, Nx, Ny, Nz, alpha=0.0, rcut_factor=0.0, mu=1.0,
                  precision="fp64", quadrature="nodal", max_points=1 << 16, max_tris=0,
