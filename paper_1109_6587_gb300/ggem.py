@@ -165,7 +165,7 @@ class Plan:
 
     Lx, Lz, W, y0, Nx, Ny, Nz: periodic box, slit and grid (Nx, Nz powers of
     two, Ny Chebyshev-Lobatto nodes); alpha, rcut_factor: the GGEM split (0
-    selects alpha = 1/(2h), r_cut = 4/alpha); precision: "fp64", "mixed" or
+    selects alpha = 1/(2h), r_cut = 4/alpha); mu: viscosity; precision: "fp64", "mixed" or
     "fp64_emulated"; quadrature: "nodal" or "element"; max_points, max_tris:
     capacities; stream: a CUDA stream handle (default torch's current one);
     offgrid: "lagrange" (5-point interpolation) or "spectral" (the expansion
