@@ -147,3 +147,34 @@ def test_planted_mistakes_fail_the_pin(monkeypatch, mistake):
         ymir = 2 * box.y0 + box.W - xt[:, 1]
         v = O.spectral_eval(box, field, np.stack([xt[:, 0], ymir, xt[:, 2]], 1))[:, 0]
     assert np.abs(v - exact).max() > 1e-3
+
+
+def test_convergence_study_of_section_3_2_3():
+    """The point-force test of Sec. 3.2.3 (Fig. ggem_conv): a cube slit of side
+    L = 1, force (1, 1, 1) at (0.25, 0.25, 0.25), alpha = 80/3 fixed, targets
+    at the box centre (a mesh point) and at (0.4312, 0.3734, 0.5234) (not one),
+    errors against a fine solution (r_cut = 13/alpha, grid 128 x 129 x 128).
+    As the paper reports: on the mesh point the error falls exponentially with
+    1/(alpha dy_m) and, for r_cut = 4/alpha, levels off near 1e-6 while a
+    larger r_cut keeps falling; off the mesh the 5-point interpolation error
+    dominates at the finer mesh, and the spectral evaluation removes it."""
+    alpha = 80.0 / 3.0
+    xs, g = np.array([[0.25, 0.25, 0.25]]), np.array([[1.0, 1.0, 1.0]])
+    xt = np.array([[0.5, 0.5, 0.5], [0.4312, 0.3734, 0.5234]])
+
+    def ux(n, c, og):
+        b = W.Box(Lx=1.0, Lz=1.0, W=1.0, y0=0.0, Nx=n, Ny=n + 1, Nz=n)
+        return O.point_forces(b, xs, g, xt, alpha=alpha, rcut=c / alpha, offgrid=og)[0][:, 0]
+
+    ref = ux(128, 13.0, "spectral")
+
+    def err(n, c, og):
+        return np.abs(ux(n, c, og) - ref) / np.abs(ref)
+    e32, e64_4, e64_6 = err(32, 4.0, "spectral"), err(64, 4.0, "spectral"), err(64, 6.0, "spectral")
+    # mesh point: 1/(alpha dy_m) 1.2 -> 2.4 gains > 100x (exponential convergence)
+    assert e32[0] > 100 * e64_6[0]
+    # r_cut = 4/alpha levels off at O(1e-6) (truncation of the local part)
+    assert 1e-7 < e64_4[0] < 3e-5 and e64_4[0] > 100 * e64_6[0]
+    # off the mesh: interpolation dominates Lagrange, not the spectral evaluation
+    lag = err(64, 6.0, "lagrange")
+    assert lag[1] > 1e-6 and lag[1] > 100 * e64_6[1]
