@@ -694,6 +694,49 @@ def bie_solve(susp, kappa, b, q0=None, tol=1e-6, restart=30, maxit=300,
     return x.reshape(n, 3), its, rr, ok
 
 
+def assembled_operator(susp, kappa, quadrature="element", mu=1.0, alpha=None, rcut=None):
+    """The matrix of (I + kappa/(4 pi) D) on the flattened [N*3] densities,
+    column by column from unit densities (small meshes only)."""
+    n = susp.x.shape[0]
+    return np.stack([bie_operator(susp, kappa, e.reshape(n, 3), quadrature, mu, alpha,
+                                  rcut).ravel() for e in np.eye(3 * n)], 1)
+
+
+def particle_block_solve(susp, kappa, b, block_inverse, q0=None, tol=1e-6, restart=30,
+                         maxit=300, quadrature="element", mu=1.0, alpha=None, rcut=None):
+    """The Fredholm solve of Sec. 5 with a right preconditioner M that applies
+    the same dense [3 n_p, 3 n_p] matrix block_inverse to every particle's
+    densities (nodes of a particle in increasing index order, n_p nodes each):
+    GMRES on A M y = b - A q0, q = q0 + M y.  The paper uses no
+    preconditioner; this is the reference for a per-particle block one.
+    Returns (q [N, 3], iterations, true relative residual of q, converged)."""
+    n = susp.x.shape[0]
+    parts = [np.flatnonzero(susp.particle == p) for p in range(int(susp.particle.max()) + 1)]
+    cols = [np.stack([3 * idx, 3 * idx + 1, 3 * idx + 2], 1).ravel() for idx in parts]
+
+    def A(v):
+        return bie_operator(susp, kappa, v.reshape(n, 3), quadrature, mu, alpha, rcut).ravel()
+
+    def M(v):
+        out = np.empty_like(v)
+        for c in cols:
+            out[c] = block_inverse @ v[c]
+        return out
+
+    b = np.asarray(b, dtype=np.float64).ravel()
+    q0 = np.zeros_like(b) if q0 is None else np.asarray(q0, dtype=np.float64).ravel()
+    r0 = b - A(q0)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros((n, 3)), 0, 0.0, True
+    # the inner tolerance is relative to ||r0||; the residual of q is that of y
+    y, its, rr, ok = gmres(lambda v: A(M(v)), r0, None, tol * nb / max(np.linalg.norm(r0),
+                                                                      1e-300), restart, maxit)
+    q = q0 + M(y)
+    rel = np.linalg.norm(b - A(q)) / nb
+    return q.reshape(n, 3), its, rel, rel <= tol
+
+
 # ------------------------------------------- rigid particles (Sec. 6.1)
 
 def rigid_scales(susp, mu=1.0):
