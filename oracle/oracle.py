@@ -17,8 +17,9 @@ Paper: Kumar & Graham, arXiv 1109.6587.  Steps, in the paper's order:
      or the expansion summed at each point ............. Sec. 3.2.3, Eq. (u_expn)
   8. u = u^l + u^g ..................................... Eq. (tot_l_g)
 Boundary integral operators (Sec. 3.4, 3.5), the Fredholm solve (Sec. 5,
-restarted GMRES with modified Gram-Schmidt) and the rigid-particle solve
-(Sec. 6.1, Eq. (sl_r) with force and torque balance) are built on top.
+restarted GMRES with modified Gram-Schmidt; a per-particle block-preconditioned
+variant, which the paper does not use, as a reference) and the rigid-particle
+solve (Sec. 6.1, Eq. (sl_r) with force and torque balance) are built on top.
 
 Readings (the paper is silent, ambiguous or garbled here):
   * alpha = 1/(2 h), h = max(Lx/Nx, W/(Ny-1), Lz/Nz); r_cut = 4/alpha.
