@@ -703,14 +703,45 @@ def assembled_operator(susp, kappa, quadrature="element", mu=1.0, alpha=None, rc
                                   rcut).ravel() for e in np.eye(3 * n)], 1)
 
 
+def reference_box(box, ref_nx, ref_nz):
+    """Slit of the isolated reference capsule of the per-particle block
+    preconditioner: the wall gap, y0, Chebyshev grid and x-z grid spacing of
+    `box` on a periodic cell of ref_nx x ref_nz grid intervals."""
+    return type(box)(Lx=ref_nx * box.Lx / box.Nx, Lz=ref_nz * box.Lz / box.Nz, W=box.W,
+                     y0=box.y0, Nx=ref_nx, Ny=box.Ny, Nz=ref_nz)
+
+
+def reference_block_inverse(box, x_ref, tri_ref, kappa, ref_nx, ref_nz, quadrature="element",
+                            mu=1.0, alpha=None, rcut=None):
+    """Inverse of the [3 n, 3 n] matrix of (I + kappa/(4 pi) D) for one capsule
+    alone (nodes x_ref [n, 3] relative to its centre, triangles tri_ref) placed
+    at the centre of reference_box(box, ref_nx, ref_nz), with the splitting
+    parameter and cutoff of `box` (alpha defaults to that of `box`, not of the
+    smaller cell)."""
+    import types
+    rb = reference_box(box, ref_nx, ref_nz)
+    alpha = default_alpha(box) if alpha is None else alpha
+    c = np.array([0.5 * rb.Lx, rb.y0 + 0.5 * rb.W, 0.5 * rb.Lz])
+    x = np.asarray(x_ref, dtype=np.float64) + c
+    s = types.SimpleNamespace(box=rb, x=x, tri=np.asarray(tri_ref, dtype=np.int32),
+                              particle=np.zeros(len(x), np.int32))
+    A = assembled_operator(s, np.full(len(x), float(kappa)), quadrature, mu, alpha, rcut)
+    return np.linalg.inv(A)
+
+
 def particle_block_solve(susp, kappa, b, block_inverse, q0=None, tol=1e-6, restart=30,
-                         maxit=300, quadrature="element", mu=1.0, alpha=None, rcut=None):
+                         maxit=300, quadrature="element", mu=1.0, alpha=None, rcut=None,
+                         rotations=None):
     """The Fredholm solve of Sec. 5 with a right preconditioner M that applies
     the same dense [3 n_p, 3 n_p] matrix block_inverse to every particle's
     densities (nodes of a particle in increasing index order, n_p nodes each):
-    GMRES on A M y = b - A q0, q = q0 + M y.  The paper uses no
-    preconditioner; this is the reference for a per-particle block one.
-    Returns (q [N, 3], iterations, true relative residual of q, converged)."""
+    GMRES on A M y = b - A q0, q = q0 + M y.  With rotations ([Np, 3, 3],
+    particle p's orientation relative to the block's capsule), particle p's
+    block is (I x R_p) block_inverse (I x R_p^T): its densities are turned
+    into the reference orientation node by node, multiplied, and turned back.
+    The paper uses no preconditioner; this is the reference for a
+    per-particle block one.  Returns (q [N, 3], iterations, true relative
+    residual of q, converged)."""
     n = susp.x.shape[0]
     parts = [np.flatnonzero(susp.particle == p) for p in range(int(susp.particle.max()) + 1)]
     cols = [np.stack([3 * idx, 3 * idx + 1, 3 * idx + 2], 1).ravel() for idx in parts]
@@ -720,8 +751,13 @@ def particle_block_solve(susp, kappa, b, block_inverse, q0=None, tol=1e-6, resta
 
     def M(v):
         out = np.empty_like(v)
-        for c in cols:
-            out[c] = block_inverse @ v[c]
+        for p, c in enumerate(cols):
+            if rotations is None:
+                out[c] = block_inverse @ v[c]
+            else:
+                R = rotations[p]
+                u = (v[c].reshape(-1, 3) @ R).ravel()            # R^T v_i at every node
+                out[c] = ((block_inverse @ u).reshape(-1, 3) @ R.T).ravel()
         return out
 
     b = np.asarray(b, dtype=np.float64).ravel()

@@ -182,3 +182,65 @@ def test_particle_block_preconditioned_solve():
     assert ok and rr <= 1e-10
     assert np.abs(q - q_ref).max() < 1e-8 * np.abs(q_ref).max()
     assert its_p <= its_ref // 2 + 2
+
+
+def _rot_y(angle):
+    c, s = np.cos(angle), np.sin(angle)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def test_operator_rotation_about_the_wall_normal():
+    """Pin of the rotation used by the per-particle block preconditioner: a
+    quarter turn about the wall normal maps a square slit's grid (capsule
+    centred on a grid node, Nx = Nz, Lx = Lz) onto itself, so the discrete
+    operator of the turned capsule is (I x R) A (I x R^T) exactly -- the
+    identity that lets one reference block serve particles of any
+    orientation; a wrong transpose or index order fails it."""
+    V, F = W.rbc_mesh(level=1)
+    box = W.Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=16, Ny=17, Nz=16)
+    c = np.array([4.0, 0.0, 4.0])
+    R = _rot_y(0.5 * np.pi)
+    n = len(V)
+    kappa = np.full(n, 2.0 / 3.0)
+
+    def susp(x):
+        return W.Suspension(box=box, x=x + c, tri=F, particle=np.zeros(n, np.int32),
+                            centres=c[None], radius=1.0)
+    A = O.assembled_operator(susp(V), kappa)
+    Ar = O.assembled_operator(susp(V @ R.T), kappa)
+    K = np.kron(np.eye(n), R)
+    assert np.abs(Ar - K @ A @ K.T).max() < 1e-10 * np.abs(A).max()
+    # the reference block of the preconditioner is this capsule's inverse
+    Minv = O.reference_block_inverse(box, V, F, 2.0 / 3.0, 16, 16)
+    assert np.abs(Minv @ A - np.eye(3 * n)).max() < 1e-10
+    rb = O.reference_box(box, 8, 8)
+    assert (rb.Lx, rb.Lz, rb.Nx, rb.Nz, rb.Ny, rb.W) == (4.0, 4.0, 8, 8, 17, 4.0)
+    assert O.default_alpha(rb) == O.default_alpha(box)
+
+
+def test_rotated_block_preconditioner():
+    """Two randomly oriented biconcave capsules: the isolated unrotated
+    capsule's inverse block, turned to each particle's orientation, solves
+    the system to the plain solve's solution in about half its iterations,
+    and in fewer than the same block left unturned."""
+    V, F = W.rbc_mesh(level=1)
+    box = W.Box(Lx=8.0, Lz=8.0, W=4.0, y0=-2.0, Nx=16, Ny=17, Nz=16)
+    rot = W.random_rotations(2, np.random.default_rng(8))
+    cs = [np.array([2.2, 0.1, 4.0]), np.array([5.5, -0.3, 4.5])]
+    x = np.concatenate([V @ rot[p].T + cs[p] for p in range(2)])
+    s = W.Suspension(box=box, x=x, tri=np.concatenate([F, F + len(V)]),
+                     particle=np.repeat([0, 1], len(V)).astype(np.int32),
+                     centres=np.stack(cs), radius=1.0)
+    n = x.shape[0]
+    kappa = np.full(n, 2.0 / 3.0)
+    b = np.random.default_rng(9).standard_normal((n, 3))
+    q_ref, its_ref, _, ok = O.bie_solve(s, kappa, b, tol=1e-10)
+    assert ok
+    Minv = O.reference_block_inverse(box, V, F, 2.0 / 3.0, 16, 16)
+    q, its_rot, rr, ok = O.particle_block_solve(s, kappa, b, Minv, tol=1e-10, rotations=rot)
+    assert ok and rr <= 1e-10
+    assert np.abs(q - q_ref).max() < 1e-8 * np.abs(q_ref).max()
+    _, its_plain_block, _, ok2 = O.particle_block_solve(s, kappa, b, Minv, tol=1e-10)
+    print("plain", its_ref, "rotated block", its_rot, "unrotated block", its_plain_block)
+    assert its_rot <= its_ref // 2 + 2
+    assert its_rot < its_plain_block
