@@ -12,10 +12,14 @@
 // exits).
 //
 // The array's name in host code is only a host-side stand-in for the device
-// symbol; its device address is obtained once per device with
-// cudaGetSymbolAddress (the first call on a device does this, so that call
-// should come before any stream capture).  All calls share the array, so
+// symbol; its device address is obtained with cudaGetSymbolAddress once per
+// device and CUDA context: the first call on a device does this, and so does
+// the first call after that device's context was destroyed and created anew
+// (cudaDeviceReset), whose module image may sit at another address.  Make
+// that first call before any stream capture.  All calls share the array, so
 // calls that overlap on the GPU race with one another.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ggem_internal.cuh"
@@ -46,19 +50,55 @@ namespace {
 
 std::mutex g_mu;
 void* g_addr[128] = {nullptr};
+unsigned long long g_ctx[128] = {0};   // context id the cached address belongs to
 
-// Device address of the scratch array on the current device.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Process-unique id of the current CUDA context (0 when it cannot be read:
+// then the address is looked up afresh on every call).
+unsigned long long current_context_id() {
+    static CtxGetCurrent get_current = nullptr;
+    static CtxGetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetId)f;
+        cudaGetLastError();
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device and context.
 cudaError_t scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = p;
+        g_ctx[dev] = ctx;
     }
     *out = (unsigned char*)g_addr[dev];
     return cudaSuccess;

@@ -45,7 +45,8 @@ def test_noalloc_matches_plan_local_sum_on_two_calls():
     box = s.box
     n = s.x.shape[0]
     stream = torch.cuda.current_stream().cuda_stream
-    plan = ggem.Plan.for_box(box, precision="fp64", max_points=n, stream=stream)
+    n_chunked = 70_000          # more free targets than one chunk of the scratch array
+    plan = ggem.Plan.for_box(box, precision="fp64", max_points=max(n, n_chunked), stream=stream)
     prm = ggem.ggem_params(box.Lx, box.Lz, box.W, box.y0, box.Nx, box.Ny, box.Nz,
                            0.0, 0.0, 1.0, ggem.GGEM_FP64, ggem.GGEM_NODAL, 0, 0)
     rng = np.random.default_rng(21)
@@ -70,9 +71,31 @@ def test_noalloc_matches_plan_local_sum_on_two_calls():
         torch.cuda.synchronize()
         assert float((us - refs).abs().max() / refs.abs().max()) < TOL_FP64
 
+    # free targets beyond one chunk (GGEM_NOALLOC_MAX_POINTS): located and summed
+    # chunk by chunk, same result
+    ns = 30_000
+    xs = _dev(s.x[:ns])
+    g = _dev(W.normal_forces(ns, seed=40))
+    pick = rng.choice(n, n_chunked, replace=True)
+    xt = _dev(s.x[pick] + rng.normal(scale=0.2, size=(n_chunked, 3)) * [1.0, 0.0, 1.0])
+    ref, _ = plan.local_sum(xs, g, xt)
+    u = torch.full((n_chunked, 3), float("nan"), dtype=torch.float64, device="cuda")
+    st = fn(ctypes.byref(prm), ctypes.c_void_p(stream), ns, _p(xs), _p(g), n_chunked, _p(xt), 0,
+            _p(u))
+    assert st == 0, f"chunked targets: status {st}"
+    torch.cuda.synchronize()
+    err = float((u - ref).abs().max() / ref.abs().max())
+    assert err < TOL_FP64, f"chunked targets: rel err {err}"
+
     # beyond the stated maximum: a clear capacity error, no device work
     big = ggem.ggem_params(box.Lx, box.Lz, box.W, box.y0, box.Nx, box.Ny, box.Nz,
                            0.0, 0.0, 1.0, 0, 0, 0, 0)
     u = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
     st = fn(ctypes.byref(big), ctypes.c_void_p(stream), 70_000, _p(u), _p(u), 1, _p(u), 0, _p(u))
+    assert st == 2
+    # a cell grid larger than GGEM_NOALLOC_MAX_CELLS (an 800 x 800 slit with
+    # cells of r_cut = 3.1: 256 x 3 x 256 cells): capacity error, no device work
+    wide = ggem.ggem_params(800.0, 800.0, box.W, box.y0, 2048, box.Ny, 2048,
+                            0.0, 0.0, 1.0, 0, 0, 0, 0)
+    st = fn(ctypes.byref(wide), ctypes.c_void_p(stream), 10, _p(u), _p(u), 1, _p(u), 0, _p(u))
     assert st == 2
