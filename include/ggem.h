@@ -231,6 +231,44 @@ ggem_status bie_solve(ggem_plan_t *plan, const double *kappa, const double *b, d
                       double tol, int restart, int maxit, int use_mlp, int *iters,
                       double *true_relres);
 
+/*
+ * Per-particle block preconditioner of the Fredholm solve (the paper solves
+ * Sec. 5's system by GMRES without one).  ggem_precond_set builds
+ *     B = (I + kappa/(4 pi) D_ref)^-1,
+ * D_ref the discrete double layer (this plan's precision, quadrature and
+ * off-grid evaluation) of one reference capsule alone -- nodes x_ref
+ * [n_ref][3] (any origin: they are centred on their centroid), triangles
+ * tri_ref [n_tri_ref][3] -- placed at the centre of a periodic cell of
+ * ref_nx x ref_nz grid intervals of this plan's x-z spacing, with this
+ * plan's wall gap, Chebyshev grid, alpha and r_cut (ref_nx, ref_nz powers
+ * of two >= 4; the cell must satisfy alpha L > 8).  It costs 3 n_ref
+ * double-layer evaluations on that cell and an FP64 Gauss-Jordan inversion
+ * (partial pivoting) on the device, and enables the preconditioner.
+ *
+ * bie_solve (and the capsule steps, which call it) then runs GMRES on
+ * A M y = r, x += M y (flexible form: the products M V_j are kept), with
+ *     M = blockdiag over particles of (I x R_p) B (I x R_p^T),
+ * R_p the rotation carrying the reference nodes onto particle p's (the
+ * polar factor of their cross-covariance, each particle unwrapped about its
+ * first node in x, z): every particle (ggem_mesh_particles) must have n_ref
+ * nodes, its l-th node (increasing index) matching reference node l.  The
+ * block is best for particles with this kappa and valid for any.  M is
+ * applied as one GEMM over all particles, FP32 in GGEM_MIXED plans, FP64
+ * otherwise.  The solution and its stopping test (the true residual) do not
+ * depend on M; the iteration count does.
+ *
+ * Errors: GGEM_ERR_INVALID_ARG for bad sizes or pointers (host or device),
+ * GGEM_ERR_NUMERICAL for a singular block, a reference-cell plan's error
+ * otherwise; a failed set leaves no preconditioner.  x_ref and tri_ref may be
+ * host or device arrays; the plan keeps B (FP64 and FP32 copies).
+ */
+ggem_status ggem_precond_set(ggem_plan_t *plan, int n_ref, const double *x_ref, int n_tri_ref,
+                             const int *tri_ref, double kappa, int ref_nx, int ref_nz);
+/* Use (on = 1) or stop using (0) the block preconditioner that was set. */
+ggem_status ggem_precond_enable(ggem_plan_t *plan, int on);
+/* The block B [3 n_ref][3 n_ref] (row-major, FP64) into out (host or device). */
+ggem_status ggem_precond_block(ggem_plan_t *plan, double *out);
+
 /* The last bie_solve's initial guess: used_mlp = 1 when it started from the
  * learned guess, and the relative residuals of the caller's and the learned
  * guess (0 when use_mlp was 0). */
@@ -379,17 +417,18 @@ ggem_status ggem_overlap_correct(ggem_plan_t *plan, double h_min, int max_sweeps
  * under stream capture, where allocation calls are not allowed; applications
  * whose device memory belongs to another allocator or a fixed budget; loops
  * that must avoid the device-wide synchronisation of cudaFree -- and that
- * therefore cannot create a plan either.  Computes the same u^l as
- * ggem_local_sum (velocity only, FP64, Eq. (u_loc)) from the geometry and
- * alpha / r_cut rules of *params (its precision, quadrature and capacity
- * fields are ignored), on `stream`.
+ * therefore cannot create a plan either.  Computes the same local velocity
+ * as ggem_local_sum (velocity only, FP64) from the geometry and alpha /
+ * r_cut rules of *params (its precision, quadrature and capacity fields are
+ * ignored), on `stream`.
  *
  * It allocates nothing: its cell list lives in one file-scope device array
  * of the library, sized for at most GGEM_NOALLOC_MAX_POINTS sources and
  * GGEM_NOALLOC_MAX_CELLS cells (about 7.8 MB, held on every GPU that loads
  * the library until the process exits); targets are taken in chunks of
- * GGEM_NOALLOC_MAX_POINTS, so their number is not limited.  The first call on each device looks
- * up that array's device address, so make it before any stream capture.
+ * GGEM_NOALLOC_MAX_POINTS, so their number is not limited.  The first call on each device
+ * (and the first after that device's context was reset) looks up that array's device
+ * address, so make it before any stream capture.
  * Every call reuses the same array: calls that overlap on the GPU (different
  * streams or threads) race and must be serialised by the caller.  The array
  * keeps the last call's contents; each call clears the counters it needs.
@@ -439,6 +478,14 @@ ggem_status ggem_mlp_features(ggem_plan_t *plan, const double *kappa, const doub
 /* delta [n_nodes][3] = the learned estimate of A^-1 r. */
 ggem_status ggem_mlp_guess(ggem_plan_t *plan, const double *kappa, const double *r,
                            double *delta);
+
+/* Arithmetic of the network (forward, guess and training): GGEM_MLP_BF16
+ * (the default; the rounding points above) or GGEM_MLP_FP32 (no rounding
+ * point: FP32 master weights, FP32 inputs and activations), e.g. to check
+ * the kernels entry by entry against an FP64 reference. */
+#define GGEM_MLP_BF16 0
+#define GGEM_MLP_FP32 1
+ggem_status ggem_mlp_precision(ggem_plan_t *plan, int mode);
 
 /* Load / save a model (count = 25 + 35075 doubles, layout above). */
 ggem_status ggem_mlp_load(ggem_plan_t *plan, const double *model, size_t count);

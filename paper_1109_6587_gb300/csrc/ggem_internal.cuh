@@ -254,9 +254,23 @@ struct ggem_plan {
     double* d_mlp_dr = nullptr;        // [3 cap] D r of the features
     double* d_mlp_ssq = nullptr;       // sum of r^2 of the features
     bool mlp_ready = false;
+    bool mlp_fp32 = false;             // FP32 mode: no bfloat16 rounding points
     long mlp_step = 0;
     int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;
+    // per-particle block preconditioner of the Fredholm solve (ggem_precond_set)
+    int pc_n = 0;                      // nodes of the reference capsule (0: none set)
+    bool pc_on = false;                // solves use it
+    double pc_kappa = 0.0;             // kappa the block was built for
+    double* d_pc_B64 = nullptr;        // [3 pc_n][3 pc_n] block inverse, FP64
+    float* d_pc_B32 = nullptr;         //   and FP32
+    double* d_pc_xref = nullptr;       // [pc_n][3] reference nodes about their centroid
+    int pc_np = 0;                     // particles the arrays below hold
+    double* d_pc_R = nullptr;          // [pc_np][9] rotations, reference -> particle
+    double* d_pc_U = nullptr;          // [pc_np][3 pc_n] turned densities (FP64 or FP32)
+    double* d_pc_Z = nullptr;          // [pc_np][3 pc_n] block products (FP64 or FP32)
+    double* d_pc_Zb = nullptr;         // [pc_m][sol_ld] preconditioned Krylov vectors
+    int pc_m = 0;
     int* d_tc_err = nullptr;           // tensor-core kernels: expired waits
     int* d_spread_list = nullptr;      // [cap + 1] sources the paired spread hands back
     void* d_tc_fwd = nullptr;          // split-bf16 Chebyshev matrices (mixed plans)

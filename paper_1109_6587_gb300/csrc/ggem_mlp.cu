@@ -13,7 +13,8 @@
 // activations rounded to bfloat16, products accumulated in FP32; output in
 // units of s s_y.  Training: mean squared error, backpropagation in FP32 with
 // the same bfloat16 weights, gradients accumulated with atomics, Adam on FP32
-// master weights.
+// master weights.  FP32 mode (ggem_mlp_precision): the same kernels with no
+// bfloat16 rounding point -- FP32 master weights, FP32 inputs and activations.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,6 +39,8 @@ constexpr int NSTAT = 2 * NF + 1;            // mu[12], sigma[12], s_y
 
 __device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+// a rounding point of the network: bfloat16 in BF16 mode, none in FP32 mode
+template <bool BF> __device__ __forceinline__ float rp(float x) { return BF ? bfr(x) : x; }
 
 // ------------------------------------------------------------- features
 // sum of squares of n doubles into *acc (FP64 atomics of block sums)
@@ -129,20 +132,32 @@ __global__ void k_feat_crowd(int n, GridGeom geo, CellGrid cg, const double* __r
 }
 
 // ------------------------------------------------------------- network
-// out[n][j] = relu(bias[j] + sum_k in[n][k] W[k][j]) rounded to bfloat16;
-// thread j of the block, TN nodes
-template <int K>
-__device__ __forceinline__ void hidden_layer(const __nv_bfloat16* __restrict__ Wf,
-                                             const float* __restrict__ bias,
-                                             const float* in, float* out) {
+struct Net {
+    const float* p;               // FP32 master parameters (biases; weights in FP32 mode)
+    const __nv_bfloat16* wf;      // bfloat16 weights, [fan_in][fan_out]
+    const __nv_bfloat16* wt;      // bfloat16 weights, [fan_out][fan_in] (layers 2-4)
+    const float* stats;           // mu[12], sigma[12], s_y
+};
+
+// weight W[k][j] of the layer at offset ow with fan_out fo, as the mode uses it
+template <bool BF>
+__device__ __forceinline__ float wgt(const Net& net, int ow, int fo, int k, int j) {
+    return BF ? ld(net.wf + ow + k * fo + j) : net.p[ow + k * fo + j];
+}
+
+// out[n][j] = relu(bias[j] + sum_k in[n][k] W[k][j]) (rounded to bfloat16 in
+// BF16 mode); thread j of the block, TN nodes
+template <int K, bool BF>
+__device__ __forceinline__ void hidden_layer(const Net& net, int ow, int ob, const float* in,
+                                             float* out) {
     const int j = threadIdx.x;
     float acc[TN];
-    const float bj = bias[j];
+    const float bj = net.p[ob + j];
 #pragma unroll
     for (int m = 0; m < TN; ++m) acc[m] = bj;
     for (int k = 0; k < K; k += 4) {
-        const float w0 = ld(Wf + (k + 0) * H + j), w1 = ld(Wf + (k + 1) * H + j);
-        const float w2 = ld(Wf + (k + 2) * H + j), w3 = ld(Wf + (k + 3) * H + j);
+        const float w0 = wgt<BF>(net, ow, H, k + 0, j), w1 = wgt<BF>(net, ow, H, k + 1, j);
+        const float w2 = wgt<BF>(net, ow, H, k + 2, j), w3 = wgt<BF>(net, ow, H, k + 3, j);
 #pragma unroll
         for (int m = 0; m < TN; ++m) {
             const float4 h = *reinterpret_cast<const float4*>(in + m * K + k);
@@ -153,15 +168,8 @@ __device__ __forceinline__ void hidden_layer(const __nv_bfloat16* __restrict__ W
         }
     }
 #pragma unroll
-    for (int m = 0; m < TN; ++m) out[m * H + j] = bfr(fmaxf(acc[m], 0.f));
+    for (int m = 0; m < TN; ++m) out[m * H + j] = rp<BF>(fmaxf(acc[m], 0.f));
 }
-
-struct Net {
-    const float* p;               // FP32 master parameters (biases)
-    const __nv_bfloat16* wf;      // bfloat16 weights, [fan_in][fan_out]
-    const __nv_bfloat16* wt;      // bfloat16 weights, [fan_out][fan_in] (layers 2-4)
-    const float* stats;           // mu[12], sigma[12], s_y
-};
 
 struct Acts {
     float a0[TN][NF];
@@ -172,40 +180,43 @@ struct Acts {
 };
 
 // forward pass of TN nodes (rows >= nv are zero inputs)
+template <bool BF>
 __device__ void forward_tile(const Net& net, const float* __restrict__ feat, int row0, int nv,
                              Acts& A) {
     for (int t = threadIdx.x; t < TN * NF; t += blockDim.x) {
         const int m = t / NF, k = t - m * NF;
         float v = 0.f;
         if (m < nv) v = (feat[(size_t)(row0 + m) * NF + k] - net.stats[k]) / net.stats[NF + k];
-        A.a0[m][k] = bfr(v);
+        A.a0[m][k] = rp<BF>(v);
     }
     __syncthreads();
-    hidden_layer<NF>(net.wf + OW1, net.p + OB1, &A.a0[0][0], &A.a1[0][0]);
+    hidden_layer<NF, BF>(net, OW1, OB1, &A.a0[0][0], &A.a1[0][0]);
     __syncthreads();
-    hidden_layer<H>(net.wf + OW2, net.p + OB2, &A.a1[0][0], &A.a2[0][0]);
+    hidden_layer<H, BF>(net, OW2, OB2, &A.a1[0][0], &A.a2[0][0]);
     __syncthreads();
-    hidden_layer<H>(net.wf + OW3, net.p + OB3, &A.a2[0][0], &A.a3[0][0]);
+    hidden_layer<H, BF>(net, OW3, OB3, &A.a2[0][0], &A.a3[0][0]);
     __syncthreads();
     if (threadIdx.x < 3 * TN) {
         const int m = threadIdx.x / 3, j = threadIdx.x - 3 * m;
         float acc = net.p[OB4 + j];
-        for (int k = 0; k < H; ++k) acc = fmaf(A.a3[m][k], ld(net.wf + OW4 + k * 3 + j), acc);
+        for (int k = 0; k < H; ++k) acc = fmaf(A.a3[m][k], wgt<BF>(net, OW4, 3, k, j), acc);
         A.out[m][j] = acc;
     }
     __syncthreads();
 }
 
 // raw network output (units of s_y) of n feature rows
+template <bool BF>
 __global__ void __launch_bounds__(H) k_mlp_forward(int n, Net net, const float* __restrict__ feat,
                                                    float* __restrict__ out) {
     __shared__ Acts A;
     const int row0 = blockIdx.x * TN, nv = min(TN, n - row0);
-    forward_tile(net, feat, row0, nv, A);
+    forward_tile<BF>(net, feat, row0, nv, A);
     if (threadIdx.x < 3 * nv) out[(size_t)row0 * 3 + threadIdx.x] = (&A.out[0][0])[threadIdx.x];
 }
 
 // out = base + r + s s_y MLP (the A^-1 r estimate added to base), caller order
+template <bool BF>
 __global__ void __launch_bounds__(H) k_mlp_guess(int n, Net net, const float* __restrict__ feat,
                                                  const double* __restrict__ r,
                                                  const double* __restrict__ ssq,
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(H) k_mlp_guess(int n, Net net, const float* __
                                                  double* __restrict__ out) {
     __shared__ Acts A;
     const int row0 = blockIdx.x * TN, nv = min(TN, n - row0);
-    forward_tile(net, feat, row0, nv, A);
+    forward_tile<BF>(net, feat, row0, nv, A);
     if (threadIdx.x < 3 * nv) {
         const double s = sqrt(*ssq / (3.0 * n));
         const size_t e = (size_t)row0 * 3 + threadIdx.x;
@@ -224,6 +235,7 @@ __global__ void __launch_bounds__(H) k_mlp_guess(int n, Net net, const float* __
 
 // One minibatch (rows idx[0..nb) of feat/target, target in raw units): forward,
 // loss sum((out - target/s_y)^2) / (3 nb) into *loss, gradients added to grad.
+template <bool BF>
 __global__ void __launch_bounds__(H) k_mlp_train(int nb, const int* __restrict__ idx, Net net,
                                                  const float* __restrict__ feat,
                                                  const float* __restrict__ target,
@@ -241,7 +253,7 @@ __global__ void __launch_bounds__(H) k_mlp_train(int nb, const int* __restrict__
         fbuf[m][k] = m < nv ? feat[(size_t)idx[row0 + m] * NF + k] : 0.f;
     }
     __syncthreads();
-    forward_tile(net, &fbuf[0][0], 0, nv, A);
+    forward_tile<BF>(net, &fbuf[0][0], 0, nv, A);
     const float scale = 2.f / (3.f * (float)nb), isy = 1.f / net.stats[2 * NF];
     float lsum = 0.f;
     if (threadIdx.x < 3 * TN) {
@@ -266,8 +278,8 @@ __global__ void __launch_bounds__(H) k_mlp_train(int nb, const int* __restrict__
     // layer 4: dW4[k][j] = sum_m a3[m][k] d4[m][j]; d3 = (W4 d4) * (a3 > 0)
     {
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        const float w0 = ld(net.wf + OW4 + t * 3), w1 = ld(net.wf + OW4 + t * 3 + 1),
-                    w2 = ld(net.wf + OW4 + t * 3 + 2);
+        const float w0 = wgt<BF>(net, OW4, 3, t, 0), w1 = wgt<BF>(net, OW4, 3, t, 1),
+                    w2 = wgt<BF>(net, OW4, 3, t, 2);
 #pragma unroll
         for (int m = 0; m < TN; ++m) {
             const float a = A.a3[m][t];
@@ -318,10 +330,12 @@ __global__ void __launch_bounds__(H) k_mlp_train(int nb, const int* __restrict__
 #pragma unroll
             for (int m = 0; m < TN; ++m) acc[m] = 0.f;
             for (int j = 0; j < H; j += 4) {
-                const float w0 = ld(net.wt + ow + (j + 0) * H + t),
-                            w1 = ld(net.wt + ow + (j + 1) * H + t),
-                            w2 = ld(net.wt + ow + (j + 2) * H + t),
-                            w3 = ld(net.wt + ow + (j + 3) * H + t);
+                // W_l[t][j .. j + 3]: the transposed bfloat16 copy (coalesced) or
+                // the FP32 masters
+                const float w0 = BF ? ld(net.wt + ow + (j + 0) * H + t) : net.p[ow + t * H + j],
+                            w1 = BF ? ld(net.wt + ow + (j + 1) * H + t) : net.p[ow + t * H + j + 1],
+                            w2 = BF ? ld(net.wt + ow + (j + 2) * H + t) : net.p[ow + t * H + j + 2],
+                            w3 = BF ? ld(net.wt + ow + (j + 3) * H + t) : net.p[ow + t * H + j + 3];
 #pragma unroll
                 for (int m = 0; m < TN; ++m) {
                     const float4 dv = *reinterpret_cast<const float4*>(&dcur[m][j]);
@@ -439,6 +453,17 @@ Net net_of(ggem_plan_t* P) {
                P->d_mlp_stats};
 }
 
+// one minibatch's forward, loss and gradient (added to P->d_mlp_grad)
+void train_batch(ggem_plan_t* P, int nb, const int* idx, const float* f, const float* t,
+                 float* dloss) {
+    if (P->mlp_fp32)
+        k_mlp_train<false><<<nblk(nb, TN), H, 0, P->st>>>(nb, idx, net_of(P), f, t,
+                                                          P->d_mlp_grad, dloss);
+    else
+        k_mlp_train<true><<<nblk(nb, TN), H, 0, P->st>>>(nb, idx, net_of(P), f, t,
+                                                         P->d_mlp_grad, dloss);
+}
+
 // features of the right-hand side r (device [n][3]) on the current mesh into
 // P->d_feat; P->d_mlp_ssq gets sum(r^2)
 void features_impl(ggem_plan_t* P, const double* kappa, const double* r) {
@@ -473,8 +498,14 @@ void mlp_guess_dev(ggem_plan_t* P, const double* kappa, const double* r, const d
     GG_CHECK(P->mlp_ready, GGEM_ERR_INVALID_ARG, "no learned warm start is loaded");
     GG_CHECK(P->d_particle, GGEM_ERR_INVALID_ARG, "particle ids not set (ggem_mesh_particles)");
     features_impl(P, kappa, r);
-    k_mlp_guess<<<nblk(P->n_nodes, TN), H, 0, P->st>>>(P->n_nodes, net_of(P), P->d_feat, r,
-                                                       P->d_mlp_ssq, base, out);
+    if (P->mlp_fp32)
+        k_mlp_guess<false><<<nblk(P->n_nodes, TN), H, 0, P->st>>>(P->n_nodes, net_of(P),
+                                                                  P->d_feat, r, P->d_mlp_ssq,
+                                                                  base, out);
+    else
+        k_mlp_guess<true><<<nblk(P->n_nodes, TN), H, 0, P->st>>>(P->n_nodes, net_of(P),
+                                                                 P->d_feat, r, P->d_mlp_ssq,
+                                                                 base, out);
     GG_CUDA(cudaGetLastError());
     P->launches += 1;
 }
@@ -556,6 +587,15 @@ ggem_status ggem_mlp_guess(ggem_plan_t* P, const double* kappa, const double* r,
     });
 }
 
+ggem_status ggem_mlp_precision(ggem_plan_t* P, int mode) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(mode == GGEM_MLP_BF16 || mode == GGEM_MLP_FP32, GGEM_ERR_INVALID_ARG,
+                 "mode must be GGEM_MLP_BF16 or GGEM_MLP_FP32");
+        P->mlp_fp32 = mode == GGEM_MLP_FP32;
+    });
+}
+
 ggem_status ggem_mlp_load(ggem_plan_t* P, const double* blob, size_t count) {
     if (!P) return GGEM_ERR_INVALID_ARG;
     return guarded(P, [&] {
@@ -615,7 +655,8 @@ ggem_status ggem_mlp_forward(ggem_plan_t* P, int n, const double* feat, double* 
         GG_CUDA(cudaMemcpyAsync(fd, feat, (size_t)n * NF * sizeof(double), cudaMemcpyDefault,
                                 P->st));
         k_to_float<<<nblk((size_t)n * NF), 256, 0, P->st>>>((size_t)n * NF, fd, f);
-        k_mlp_forward<<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
+        if (P->mlp_fp32) k_mlp_forward<false><<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
+        else k_mlp_forward<true><<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
         k_to_double<<<nblk((size_t)n * 3), 256, 0, P->st>>>((size_t)n * 3, o, od);
         GG_CUDA(cudaMemcpyAsync(out, od, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault,
                                 P->st));
@@ -707,8 +748,7 @@ ggem_status ggem_mlp_train(ggem_plan_t* P, int n, const double* feat, const doub
                                         cudaMemcpyHostToDevice, st));
                 GG_CUDA(cudaMemsetAsync(dloss, 0, sizeof(float), st));
                 GG_CUDA(cudaMemsetAsync(P->d_mlp_grad, 0, NP * sizeof(float), st));
-                k_mlp_train<<<nblk(n, TN), H, 0, st>>>(n, idx, net_of(P), f, t, P->d_mlp_grad,
-                                                       dloss);
+                train_batch(P, n, idx, f, t, dloss);
                 float hl = 0.f;
                 GG_CUDA(cudaMemcpyAsync(&hl, dloss, sizeof(float), cudaMemcpyDeviceToHost, st));
                 if (grad_out) {
@@ -735,8 +775,7 @@ ggem_status ggem_mlp_train(ggem_plan_t* P, int n, const double* feat, const doub
                 int nbatches = 0;
                 for (int r0 = 0; r0 < n; r0 += batch) {
                     const int nb = std::min(batch, n - r0);
-                    k_mlp_train<<<nblk(nb, TN), H, 0, st>>>(nb, idx + r0, net_of(P), f, t,
-                                                            P->d_mlp_grad, dloss);
+                    train_batch(P, nb, idx + r0, f, t, dloss);
                     P->mlp_step++;
                     const float c1 = 1.f - std::pow(0.9f, (float)P->mlp_step);
                     const float c2 = 1.f - std::pow(0.999f, (float)P->mlp_step);

@@ -52,7 +52,8 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_membrane_traction", "ggem_undisturbed", "ggem_capsule_velocity",
            "ggem_capsule_step", "ggem_mesh_positions", "ggem_min_separation",
            "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct",
-           "ggem_set_offgrid"]
+           "ggem_set_offgrid", "ggem_mlp_precision", "ggem_precond_set",
+           "ggem_precond_enable", "ggem_precond_block"]
 
 GGEM_OFFGRID = {"lagrange": 0, "spectral": 1}
 
@@ -113,6 +114,10 @@ def lib():
         L.ggem_overlap_correct.argtypes = [P, D, I, ctypes.POINTER(I)]
         L.ggem_set_offgrid.argtypes = [P, I, I]
         L.ggem_mlp_load.argtypes = [P, P, ctypes.c_size_t]
+        L.ggem_mlp_precision.argtypes = [P, I]
+        L.ggem_precond_set.argtypes = [P, I, P, I, P, D, I, I]
+        L.ggem_precond_enable.argtypes = [P, I]
+        L.ggem_precond_block.argtypes = [P, P]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
         L.ggem_mlp_train.argtypes = [P, I, P, P, I, ctypes.c_ulonglong, I, I, D,
@@ -500,6 +505,46 @@ class Plan:
         if ko is not out and not hasattr(out, "data_ptr"):
             out[...] = ko
         return out
+
+    def precond_set(self, x_ref, tri_ref, kappa, ref_nx=0, ref_nz=0):
+        """Build and enable the per-particle block preconditioner of the
+        Fredholm solve from one reference capsule (nodes x_ref [n, 3], any
+        origin; triangles tri_ref [m, 3]).  ref_nx / ref_nz = 0 pick the
+        smallest power of two >= 16 whose cell spans the capsule plus 2 r_cut
+        in that direction."""
+        x = np.ascontiguousarray(np.asarray(x_ref, dtype=np.float64))
+        t = np.ascontiguousarray(np.asarray(tri_ref, dtype=np.int32))
+        prm = self.params
+        _, rc = self.info()
+
+        def pick(extent, dx):
+            nx = 16
+            while nx * dx < extent + 2.0 * rc:
+                nx *= 2
+            return nx
+        ext = x.max(0) - x.min(0)
+        nx = ref_nx or pick(ext[0], prm.Lx / prm.Nx)
+        nz = ref_nz or pick(ext[2], prm.Lz / prm.Nz)
+        _check(lib().ggem_precond_set(self.h, x.shape[0], x.ctypes.data_as(ctypes.c_void_p),
+                                      t.shape[0], t.ctypes.data_as(ctypes.c_void_p),
+                                      float(kappa), int(nx), int(nz)), self.h)
+        self._pc_n = x.shape[0]
+        return nx, nz
+
+    def precond_enable(self, on=True):
+        _check(lib().ggem_precond_enable(self.h, int(bool(on))), self.h)
+
+    def precond_block(self):
+        """The block B = (I + kappa/4 pi D_ref)^-1 [3 n_ref, 3 n_ref] (FP64)."""
+        n3 = 3 * getattr(self, "_pc_n", 0)
+        out = np.zeros((n3, n3))
+        _check(lib().ggem_precond_block(self.h, out.ctypes.data_as(ctypes.c_void_p)), self.h)
+        return out
+
+    def mlp_precision(self, mode):
+        """Network arithmetic: "bf16" (the bfloat16 rounding points, default) or
+        "fp32" (none)."""
+        _check(lib().ggem_mlp_precision(self.h, {"bf16": 0, "fp32": 1}[mode]), self.h)
 
     def mlp_load(self, model):
         m = np.ascontiguousarray(np.asarray(model), dtype=np.float64)

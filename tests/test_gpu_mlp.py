@@ -9,7 +9,12 @@ it gains in the Fredholm solve.
     bfloat16 step: 1e-2 of the output scale);
   * gradient of one full-batch pass against the oracle's backpropagation
     (2e-2 relative per parameter tensor), and the loss (1e-3);
-  * one Adam step moves the parameters in the oracle's direction;
+  * one Adam step moves the parameters in the oracle's direction, and its
+    values equal the oracle's Adam applied to the kernel's own gradient;
+  * FP32 mode (no bfloat16 rounding point): forward output and every
+    gradient entry against the oracle's FP64 network entry by entry, each
+    within 2e-5 of the sum of the magnitudes of its terms (the FP32 error
+    bound of a sum), and one Adam step entry by entry;
   * the Fredholm operator (I + kappa/4 pi D) against the oracle's;
   * warm start: trained on emulated time-step series of suspensions, on a
     held-out series the learned guess has a lower residual than the caller's
@@ -136,6 +141,122 @@ def test_gradient_and_adam_match_oracle(ggem, susp):
     moved_ref = np.concatenate([p.ravel() for p in pf]) - blob[25:].astype(np.float32)
     big = np.abs(np.concatenate([x.ravel() for x in ref_g])) > 1e-6
     assert (np.sign(moved_gpu[big]) == np.sign(moved_ref[big])).mean() > 0.99
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _abs_forward(params, X):
+    """Per-entry magnitude scales of the forward pass: |X| through |W| and
+    |b| (the sums of the magnitudes of the terms of every activation)."""
+    h = np.abs(X)
+    for layer in range(4):
+        h = h @ np.abs(params[2 * layer]) + np.abs(params[2 * layer + 1])
+    return h
+
+
+def test_fp32_mode_forward_entrywise(ggem, susp):
+    P = _plan(ggem, susp)
+    P.mlp_precision("fp32")
+    params, mu, sigma, s_y, blob = _model(31)
+    P.mlp_load(blob)
+    X = np.random.default_rng(32).standard_normal((1000, 12))
+    out = P.mlp_forward(X)
+    pf = [_f32(p) for p in params]
+    Z = (_f32(X) - _f32(mu)) / _f32(sigma)
+    _, ref = M.forward(pf, Z, bf16_round=False)
+    scale = _abs_forward(pf, Z)
+    err = np.abs(out - ref)
+    assert (err <= 2e-5 * scale + 1e-12).all(), float((err / scale).max())
+    # the rounding points matter: the BF16 network differs by far more
+    P.mlp_precision("bf16")
+    out_bf = P.mlp_forward(X)
+    assert np.abs(out_bf - ref).max() > 1e2 * err.max()
+
+
+def test_fp32_mode_gradient_and_adam_entrywise(ggem, susp):
+    P = _plan(ggem, susp)
+    P.mlp_precision("fp32")
+    params, mu, sigma, s_y, blob = _model(41)
+    P.mlp_load(blob)
+    rng = np.random.default_rng(42)
+    X = rng.standard_normal((700, 12))
+    T = rng.standard_normal((700, 3)) * 0.3
+    loss, g = P.mlp_train(X, T, init=False, epochs=0, want_grad=True)
+    pf = [_f32(p) for p in params]
+    Z = (_f32(X) - _f32(mu)) / _f32(sigma)
+    Y = _f32(T) / _f32(s_y)
+    ref_loss, ref_g = M.loss_and_grads(pf, Z, Y, bf16_round=False)
+    assert abs(loss - ref_loss) < 1e-5 * ref_loss
+    # magnitude scale of every gradient entry: the same backpropagation with
+    # magnitudes (|activations|, |deltas|, |weights|)
+    acts, out = M.forward(pf, Z)
+    delta = np.abs(2.0 * (out - Y) / out.size)
+    scales = [None] * 8
+    for layer in range(3, -1, -1):
+        h = np.abs(acts[layer])
+        scales[2 * layer] = h.T @ delta
+        scales[2 * layer + 1] = delta.sum(0)
+        if layer > 0:
+            delta = (delta @ np.abs(pf[2 * layer]).T) * (acts[layer] > 0)
+    off = 0
+    tols = []
+    for k, rg in enumerate(ref_g):
+        gg = g[off:off + rg.size].reshape(rg.shape)
+        off += rg.size
+        tol = 2e-5 * scales[k] + 1e-12
+        bad = np.abs(gg - rg) > tol
+        assert not bad.any(), (k, int(bad.sum()), float((np.abs(gg - rg) / tol).max()))
+        tols.append(tol.ravel())
+    tol = np.concatenate(tols)
+    # one Adam step on the same full batch: entries whose gradient sign is
+    # decided (|g| far above its error bound) move by the oracle's value
+    P.mlp_load(blob)
+    P.mlp_train(X, T, init=False, epochs=1, batch=700, lr=1e-3)
+    new = P.mlp_save()[25:]
+    p0 = np.concatenate([p.ravel() for p in pf])
+    state = []
+    pr = [p.copy() for p in pf]
+    M.adam_step(pr, ref_g, state, lr=1e-3, step=1)
+    pr = np.concatenate([p.ravel() for p in pr])
+    gr = np.concatenate([x.ravel() for x in ref_g])
+    sure = np.abs(gr) > 100 * tol
+    assert sure.mean() > 0.9
+    assert (np.abs(new[sure] - pr[sure]) <= 2.5e-7 * np.abs(pr[sure]) + 2e-8).all()
+    assert (np.abs(new - p0) <= 1e-3 * (1 + 1e-6) + 2.5e-7 * np.abs(p0)).all()
+
+
+def test_bf16_adam_values_match_oracle_on_the_kernel_gradient(ggem, susp):
+    """The Adam kernel entry by entry: the oracle's Adam step applied to the
+    gradient the kernels computed gives the parameters the GPU step wrote
+    (entries whose gradient is not tiny: the step's own pass accumulates its
+    atomics in another order, which can flip the sign of a near-zero one)."""
+    P = _plan(ggem, susp)
+    params, mu, sigma, s_y, blob = _model(51)
+    P.mlp_load(blob)
+    rng = np.random.default_rng(52)
+    X = rng.standard_normal((500, 12))
+    T = rng.standard_normal((500, 3)) * 0.3
+    _, g = P.mlp_train(X, T, init=False, epochs=0, want_grad=True)
+    P.mlp_load(blob)
+    P.mlp_train(X, T, init=False, epochs=1, batch=500, lr=1e-3)
+    new = P.mlp_save()[25:]
+    pf = [_f32(p) for p in params]
+    shapes = [p.shape for p in pf]
+    gl, off = [], 0
+    for sh in shapes:
+        k = int(np.prod(sh))
+        gl.append(g[off:off + k].reshape(sh))
+        off += k
+    state = []
+    M.adam_step(pf, gl, state, lr=1e-3, step=1)
+    pr = np.concatenate([p.ravel() for p in pf])
+    p0 = np.concatenate([_f32(p).ravel() for p in params])
+    sure = np.abs(g) > 1e-4 * np.abs(g).max()
+    assert sure.mean() > 0.9
+    assert (np.abs(new[sure] - pr[sure]) <= 2.5e-7 * np.abs(pr[sure]) + 2e-8).all()
+    assert (np.abs(new - p0) <= 1e-3 * (1 + 1e-6) + 2.5e-7 * np.abs(p0)).all()
 
 
 def test_learned_warm_start_reduces_iterations(ggem):
