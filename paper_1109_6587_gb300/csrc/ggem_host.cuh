@@ -104,12 +104,12 @@ inline void finish_out(ggem_plan_t* P, const OutMap& m) {
 // ------------------------------------------------------------- tracing
 enum Stage {
     ST_CELLS, ST_GATHER, ST_LOCAL, ST_WALL, ST_SPREAD, ST_FFT_FWD, ST_CHEB_FWD, ST_KS,
-    ST_CHEB_INV, ST_FFT_INV, ST_INTERP, ST_ELEM, ST_KRYLOV, ST_COUNT
+    ST_CHEB_INV, ST_FFT_INV, ST_INTERP, ST_ELEM, ST_KRYLOV, ST_PRECOND, ST_COUNT
 };
 inline const char* const kStageNames[ST_COUNT] = {
     "cell_list",   "gather",      "local_sum",    "wall_local_sum", "spread",
     "fft_forward", "cheb_forward", "tau_solve",   "cheb_inverse",   "fft_inverse",
-    "interpolate", "element_correction", "krylov_vectors"};
+    "interpolate", "element_correction", "krylov_vectors", "block_preconditioner"};
 
 // Run one stage (nk kernel launches); with tracing on, time it with events.
 template <typename F>
@@ -137,6 +137,12 @@ void double_layer_dev(ggem_plan_t* P, const double* q, double* v);
 // CSR, nodes ascending), built on first use after the ids change; also sizes
 // the per-particle arrays d_rc / d_rscale
 void particle_node_lists(ggem_plan_t* P);
+
+// per-particle block preconditioner (ggem_precond.cu): rotations and node
+// lists for the current mesh; out = M in; release of its arrays
+void precond_prepare(ggem_plan_t* P);
+void precond_apply(ggem_plan_t* P, const double* in, double* out);
+void precond_free(ggem_plan_t* P);
 
 // out = base + A^-1 r estimated by the learned warm start (device arrays;
 // base may be NULL); defined with the network kernels

@@ -750,6 +750,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
                     P->d_spec_dz, P->d_spec_mid, P->d_spec_ct};
     for (void* p : ptrs) dfree(p);
+    precond_free(P);
+    dfree(P->d_pc_Zb);
     if (P->h_sh) cudaFreeHost(P->h_sh);
     if (P->twin) ggem_plan_destroy(P->twin);
 }

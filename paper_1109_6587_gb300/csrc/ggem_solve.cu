@@ -137,6 +137,8 @@ struct Solver {
     const double* b;
     double* x;
     double* hs;          // pinned host copy of d_sh
+    bool pc = false;     // right preconditioner M (per-particle blocks): A M y = r,
+    double* Zb = nullptr;  //   Zb[j] = M V_j kept for the update x += Z y (flexible form)
     // out = A in (b == nullptr) or b - A in, A applied with plan Q's layers
     std::function<void(ggem_plan_t* Q, const double* in, double* out, const double* b)> op;
 
@@ -150,8 +152,8 @@ struct Solver {
         GG_CUDA(cudaGetLastError());
         launched(2);
     }
-    void mupdate(int k, const double* h, double sgn, double* w) {
-        k_mupdate<<<grid_for(n3), KB, 0, P->st>>>(n3, k, P->d_V, ld, h, sgn, w);
+    void mupdate(int k, const double* h, double sgn, double* w, const double* basis = nullptr) {
+        k_mupdate<<<grid_for(n3), KB, 0, P->st>>>(n3, k, basis ? basis : P->d_V, ld, h, sgn, w);
         GG_CUDA(cudaGetLastError());
         launched(1);
     }
@@ -207,7 +209,13 @@ struct Solver {
         for (int j = 0; j < m; ++j) {
             double* vj = P->d_V + (size_t)j * ld;
             double* w = P->d_V + (size_t)(j + 1) * ld;
-            apply(Ainner, vj, w, false);
+            if (pc) {
+                double* zj = Zb + (size_t)j * ld;
+                stage(P, ST_PRECOND, 0, [&] { precond_apply(P, vj, zj); });
+                apply(Ainner, zj, w, false);
+            } else {
+                apply(Ainner, vj, w, false);
+            }
             stage(P, ST_KRYLOV, 0, [&] {
                 mdot(j + 1, P->d_V, w, hA);          // classical Gram-Schmidt ...
                 mupdate(j + 1, hA, -1.0, w);
@@ -256,7 +264,7 @@ struct Solver {
         }
         GG_CUDA(cudaMemcpyAsync(P->d_sh, y.data(), k * sizeof(double), cudaMemcpyHostToDevice,
                                 P->st));
-        stage(P, ST_KRYLOV, 0, [&] { mupdate(k, P->d_sh, 1.0, x); });
+        stage(P, ST_KRYLOV, 0, [&] { mupdate(k, P->d_sh, 1.0, x, pc ? Zb : nullptr); });
         GG_CUDA(cudaStreamSynchronize(P->st));           // y lives on this stack frame
         return steps;
     }
@@ -393,6 +401,17 @@ ggem_status bie_solve(ggem_plan_t* P, const double* kappa, const double* b, doub
         ensure_twin(P);
         P->sol_cycles = P->sol_mv64 = P->sol_mvmix = 0;
         Solver S = make_solver(P, n3);
+        if (P->pc_on) {
+            precond_prepare(P);
+            if (P->pc_m < restart || !P->d_pc_Zb) {
+                dfree(P->d_pc_Zb);
+                P->d_pc_Zb = nullptr;
+                dalloc(P, &P->d_pc_Zb, (size_t)restart * P->sol_ld);
+                P->pc_m = restart;
+            }
+            S.pc = true;
+            S.Zb = P->d_pc_Zb;
+        }
         const double* kd = stage_in(P, kappa, P->d_sk, (size_t)n);
         // (I + kappa/(4 pi) D) in, or b - that
         S.op = [P, n, kd](ggem_plan_t* Q, const double* in, double* out, const double* bb) {
