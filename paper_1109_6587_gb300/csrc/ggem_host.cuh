@@ -144,6 +144,24 @@ void precond_prepare(ggem_plan_t* P);
 void precond_apply(ggem_plan_t* P, const double* in, double* out);
 void precond_free(ggem_plan_t* P);
 
+// tensor-core forward of the learned warm start's network (ggem_mlp_tc.cu):
+// weight image size (bfloat16 elements), its preparation from the FP32
+// masters, and the forward (mode 0: raw outputs into out32 [n][3]; mode 1:
+// out64 = base + r + s s_y y)
+size_t mlp_tc_image_elems();
+cudaError_t mlp_tc_prepare(const float* p, void* img, cudaStream_t st);
+cudaError_t mlp_tc_forward(int n, int mode, const void* img, const float* p, const float* stats,
+                           const float* feat, float* out32, const double* r, const double* ssq,
+                           const double* base, double* out64, int* err, int nsm,
+                           cudaStream_t st);
+// tensor-core training of one minibatch (ggem_mlp_tc.cu): scratch bytes for
+// minibatches of up to nb rows, and the minibatch (loss added to *loss,
+// gradient added to grad)
+size_t mlp_tc_train_scratch(int nb);
+cudaError_t mlp_tc_train_batch(int nb, const int* idx, const float* feat, const float* target,
+                               const float* p, const float* stats, float* grad, float* loss,
+                               void* scratch, int* err, cudaStream_t st);
+
 // out = base + A^-1 r estimated by the learned warm start (device arrays;
 // base may be NULL); defined with the network kernels
 void mlp_guess_dev(ggem_plan_t* P, const double* kappa, const double* r, const double* base,

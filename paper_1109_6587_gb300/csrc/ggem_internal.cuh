@@ -255,6 +255,9 @@ struct ggem_plan {
     double* d_mlp_ssq = nullptr;       // sum of r^2 of the features
     bool mlp_ready = false;
     bool mlp_fp32 = false;             // FP32 mode: no bfloat16 rounding points
+    unsigned short* d_mlp_tc = nullptr;  // bfloat16 weight image of the tensor-core forward
+    void* d_mlp_tcs = nullptr;         // tensor-core training scratch (one minibatch)
+    int mlp_tcs_rows = 0;              // rows it holds
     long mlp_step = 0;
     int sol_guess_mlp = 0;             // last solve: 1 if it started from the learned guess
     double sol_rel_plain = 0.0, sol_rel_mlp = 0.0;

@@ -445,6 +445,7 @@ void ensure_mlp(ggem_plan_t* P) {
     dalloc(P, &P->d_mlp_out, (size_t)P->cap * 3);
     dalloc(P, &P->d_mlp_dr, (size_t)P->cap * 3);
     dalloc(P, &P->d_mlp_ssq, 1);
+    dalloc(P, &P->d_mlp_tc, mlp_tc_image_elems());
     GG_CUDA(cudaMemsetAsync(P->d_mlp_grad, 0, NP * sizeof(float), P->st));
 }
 
@@ -453,15 +454,30 @@ Net net_of(ggem_plan_t* P) {
                P->d_mlp_stats};
 }
 
-// one minibatch's forward, loss and gradient (added to P->d_mlp_grad)
+// one minibatch's forward, loss and gradient (added to P->d_mlp_grad): FP32
+// mode on the SIMT kernel, BF16 mode as tensor-core GEMMs (ggem_mlp_tc.cu)
 void train_batch(ggem_plan_t* P, int nb, const int* idx, const float* f, const float* t,
                  float* dloss) {
-    if (P->mlp_fp32)
+    if (P->mlp_fp32) {
         k_mlp_train<false><<<nblk(nb, TN), H, 0, P->st>>>(nb, idx, net_of(P), f, t,
                                                           P->d_mlp_grad, dloss);
-    else
-        k_mlp_train<true><<<nblk(nb, TN), H, 0, P->st>>>(nb, idx, net_of(P), f, t,
-                                                         P->d_mlp_grad, dloss);
+        P->launches += 1;
+    } else {
+        GG_CHECK(nb <= P->mlp_tcs_rows, GGEM_ERR_INVALID_ARG, "training scratch too small");
+        GG_CUDA(mlp_tc_train_batch(nb, idx, f, t, P->d_mlp, P->d_mlp_stats, P->d_mlp_grad, dloss,
+                                   P->d_mlp_tcs, P->d_tc_err, P->st));
+        P->launches += 15;
+    }
+}
+
+// tensor-core training scratch for minibatches of up to rows rows
+void ensure_train_scratch(ggem_plan_t* P, int rows) {
+    if (P->mlp_fp32 || P->mlp_tcs_rows >= rows) return;
+    dfree(P->d_mlp_tcs);
+    P->d_mlp_tcs = nullptr;
+    P->mlp_tcs_rows = 0;
+    dalloc(P, reinterpret_cast<unsigned char**>(&P->d_mlp_tcs), mlp_tc_train_scratch(rows));
+    P->mlp_tcs_rows = rows;
 }
 
 // features of the right-hand side r (device [n][3]) on the current mesh into
@@ -498,16 +514,20 @@ void mlp_guess_dev(ggem_plan_t* P, const double* kappa, const double* r, const d
     GG_CHECK(P->mlp_ready, GGEM_ERR_INVALID_ARG, "no learned warm start is loaded");
     GG_CHECK(P->d_particle, GGEM_ERR_INVALID_ARG, "particle ids not set (ggem_mesh_particles)");
     features_impl(P, kappa, r);
-    if (P->mlp_fp32)
+    if (P->mlp_fp32) {
         k_mlp_guess<false><<<nblk(P->n_nodes, TN), H, 0, P->st>>>(P->n_nodes, net_of(P),
                                                                   P->d_feat, r, P->d_mlp_ssq,
                                                                   base, out);
-    else
-        k_mlp_guess<true><<<nblk(P->n_nodes, TN), H, 0, P->st>>>(P->n_nodes, net_of(P),
-                                                                 P->d_feat, r, P->d_mlp_ssq,
-                                                                 base, out);
+        P->launches += 1;
+    } else {
+        // BF16 network on the tensor cores (ggem_mlp_tc.cu)
+        GG_CUDA(mlp_tc_prepare(P->d_mlp, P->d_mlp_tc, P->st));
+        GG_CUDA(mlp_tc_forward(P->n_nodes, 1, P->d_mlp_tc, P->d_mlp, P->d_mlp_stats, P->d_feat,
+                               nullptr, r, P->d_mlp_ssq, base, out, P->d_tc_err, P->nsm,
+                               P->st));
+        P->launches += 2;
+    }
     GG_CUDA(cudaGetLastError());
-    P->launches += 1;
 }
 }  // namespace ggem
 
@@ -640,6 +660,41 @@ ggem_status ggem_mlp_save(ggem_plan_t* P, double* blob, size_t count) {
     });
 }
 
+ggem_status ggem_mlp_adam_state(ggem_plan_t* P, int set, double* m, double* v,
+                                long long* step) {
+    if (!P) return GGEM_ERR_INVALID_ARG;
+    return guarded(P, [&] {
+        GG_CHECK(P->mlp_ready, GGEM_ERR_INVALID_ARG, "no model");
+        GG_CHECK(m && v && step, GGEM_ERR_INVALID_ARG, "NULL argument");
+        std::vector<float> hm(NP), hv(NP);
+        if (set) {
+            GG_CHECK(*step >= 0, GGEM_ERR_INVALID_ARG, "step must be >= 0");
+            std::vector<double> dm(NP), dv(NP);
+            GG_CUDA(cudaMemcpy(dm.data(), m, NP * sizeof(double), cudaMemcpyDefault));
+            GG_CUDA(cudaMemcpy(dv.data(), v, NP * sizeof(double), cudaMemcpyDefault));
+            for (int i = 0; i < NP; ++i) {
+                GG_CHECK(std::isfinite(dm[i]) && std::isfinite(dv[i]) && dv[i] >= 0.0,
+                         GGEM_ERR_INVALID_ARG, "moments must be finite, second moments >= 0");
+                hm[i] = (float)dm[i];
+                hv[i] = (float)dv[i];
+            }
+            GG_CUDA(cudaMemcpy(P->d_mlp_m, hm.data(), NP * sizeof(float), cudaMemcpyHostToDevice));
+            GG_CUDA(cudaMemcpy(P->d_mlp_v, hv.data(), NP * sizeof(float), cudaMemcpyHostToDevice));
+            P->mlp_step = (long)*step;
+        } else {
+            GG_CUDA(cudaMemcpyAsync(hm.data(), P->d_mlp_m, NP * sizeof(float),
+                                    cudaMemcpyDeviceToHost, P->st));
+            GG_CUDA(cudaMemcpyAsync(hv.data(), P->d_mlp_v, NP * sizeof(float),
+                                    cudaMemcpyDeviceToHost, P->st));
+            GG_CUDA(cudaStreamSynchronize(P->st));
+            std::vector<double> dm(hm.begin(), hm.end()), dv(hv.begin(), hv.end());
+            GG_CUDA(cudaMemcpy(m, dm.data(), NP * sizeof(double), cudaMemcpyDefault));
+            GG_CUDA(cudaMemcpy(v, dv.data(), NP * sizeof(double), cudaMemcpyDefault));
+            *step = P->mlp_step;
+        }
+    });
+}
+
 ggem_status ggem_mlp_forward(ggem_plan_t* P, int n, const double* feat, double* out) {
     if (!P) return GGEM_ERR_INVALID_ARG;
     return guarded(P, [&] {
@@ -655,8 +710,13 @@ ggem_status ggem_mlp_forward(ggem_plan_t* P, int n, const double* feat, double* 
         GG_CUDA(cudaMemcpyAsync(fd, feat, (size_t)n * NF * sizeof(double), cudaMemcpyDefault,
                                 P->st));
         k_to_float<<<nblk((size_t)n * NF), 256, 0, P->st>>>((size_t)n * NF, fd, f);
-        if (P->mlp_fp32) k_mlp_forward<false><<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
-        else k_mlp_forward<true><<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
+        if (P->mlp_fp32) {
+            k_mlp_forward<false><<<nblk(n, TN), H, 0, P->st>>>(n, net_of(P), f, o);
+        } else {
+            GG_CUDA(mlp_tc_prepare(P->d_mlp, P->d_mlp_tc, P->st));
+            GG_CUDA(mlp_tc_forward(n, 0, P->d_mlp_tc, P->d_mlp, P->d_mlp_stats, f, o, nullptr,
+                                   nullptr, nullptr, nullptr, P->d_tc_err, P->nsm, P->st));
+        }
         k_to_double<<<nblk((size_t)n * 3), 256, 0, P->st>>>((size_t)n * 3, o, od);
         GG_CUDA(cudaMemcpyAsync(out, od, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault,
                                 P->st));
@@ -709,6 +769,9 @@ ggem_status ggem_mlp_train(ggem_plan_t* P, int n, const double* feat, const doub
                 GG_CUDA(cudaMemcpyAsync(hm.data(), mom, NSTAT * sizeof(double),
                                         cudaMemcpyDeviceToHost, st));
                 GG_CUDA(cudaStreamSynchronize(st));
+                for (int k = 0; k < NSTAT; ++k)
+                    GG_CHECK(std::isfinite(hm[k]), GGEM_ERR_NUMERICAL,
+                             "non-finite training features or targets");
                 std::vector<float> sv(NSTAT);
                 for (int k = 0; k < NF; ++k) {
                     const double mu = hm[k] / n, var = hm[NF + k] / n - mu * mu;
@@ -742,6 +805,7 @@ ggem_status ggem_mlp_train(ggem_plan_t* P, int n, const double* feat, const doub
             }
             std::vector<int> order(n);
             for (int i = 0; i < n; ++i) order[i] = i;
+            ensure_train_scratch(P, epochs == 0 ? n : std::min(batch, n));
             if (epochs == 0) {
                 // one full-batch gradient, rows in order
                 GG_CUDA(cudaMemcpyAsync(idx, order.data(), (size_t)n * sizeof(int),

@@ -748,7 +748,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
                     P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
-                    P->d_spec_dz, P->d_spec_mid, P->d_spec_ct};
+                    P->d_spec_dz, P->d_spec_mid, P->d_spec_ct, P->d_mlp_tc,
+                    P->d_mlp_tcs};
     for (void* p : ptrs) dfree(p);
     precond_free(P);
     dfree(P->d_pc_Zb);

@@ -58,13 +58,16 @@ class Suspension:
         """Checkpoint (numpy .npz): node positions, triangles, membrane
         reference, the density that seeds the next solve, initial volumes,
         time, step count, viscosity ratios, particle ids and the run's
-        parameters; plus the learned model when the plan holds one (its Adam
-        moments are not kept: a resumed run trains afresh)."""
+        parameters; plus, when the plan holds a learned model, the model and
+        its Adam moments and step count (a resumed run continues training
+        where the saved one stopped)."""
         if self.tri is None:
             raise ValueError("checkpoints need the triangles (pass tri= at construction)")
         extra = {}
         try:
             extra["mlp"] = self.P.mlp_save()
+            m, v, st = self.P.mlp_adam_state()
+            extra["mlp_m"], extra["mlp_v"], extra["mlp_step"] = m, v, np.array(st)
         except GGEMError:                 # the plan holds no model
             pass
         np.savez(path, x=self.P.mesh_positions(), tri=self.tri, x_ref=self.x_ref,
@@ -84,6 +87,8 @@ class Suspension:
         plan.mesh_set(np.ascontiguousarray(z["x"]), np.ascontiguousarray(z["tri"]))
         if "mlp" in z:
             plan.mlp_load(z["mlp"])
+            if "mlp_m" in z:
+                plan.mlp_adam_state((z["mlp_m"], z["mlp_v"], int(z["mlp_step"])))
         S = cls(plan, z["particle"], len(z["lam"]), z["lam"], ca=ca, radius=radius,
                 flow=str(z["flow"]), strength=strength, mu=mu, h_gap=h_gap,
                 vol_threshold=vol_threshold, tri=z["tri"], x_ref=z["x_ref"], v0=z["v0"])

@@ -52,6 +52,10 @@ def solve_series(plan, susp0, n_steps, seed, lam=5.0, tol=1e-6, use_mlp=0, devic
             for x0 in ([bd] if q_prev is None else [bd, q_prev]):
                 r = bd - plan.bie_operator(kd, x0)
                 feat, sc = plan.mlp_features(kd, r)
+                if not sc > 0.0:
+                    # the guess solves the system exactly (e.g. kappa = 0, where
+                    # A = I and b is the solution): no residual to learn from
+                    continue
                 target = ((q - x0 - r) / sc).cpu().numpy()
                 rec["samples"].append((feat, target))
         out.append(rec)
@@ -70,6 +74,29 @@ def training_set(plan, suspensions, n_steps, seed, lam=5.0, tol=1e-6, device="cu
                 F.append(f)
                 T.append(t)
     return np.concatenate(F), np.concatenate(T)
+
+
+def generated_training_set(make_plan, pairs, n_steps, seed, tol=1e-6, device="cuda"):
+    """Samples from series of generated suspensions of different sizes,
+    volume fractions and viscosity ratios (pairs [(suspension, lambda)],
+    e.g. workloads.training_suspensions()): each suspension is solved on a
+    plan of its own slit, make_plan(suspension), closed afterwards.  The
+    features do not depend on the plan, so the samples train any plan's
+    model.  Returns (features [n, 12], targets [n, 3])."""
+    F, T = [], []
+    for i, (s, lam) in enumerate(pairs):
+        P = make_plan(s)
+        try:
+            for rec in solve_series(P, s, n_steps, seed + i, lam=lam, tol=tol, device=device,
+                                    collect=True):
+                for f, t in rec["samples"]:
+                    F.append(f)
+                    T.append(t)
+        finally:
+            P.close()
+    F, T = np.concatenate(F), np.concatenate(T)
+    ok = np.isfinite(F).all(1) & np.isfinite(T).all(1)
+    return F[ok], T[ok]
 
 
 def train(plan, feat, target, seed=0, epochs=100, batch=512, lr=1e-3):

@@ -222,6 +222,30 @@ def capsules_1000_phi(seed=0):
     return capsules_at_phi(box_1000_capsules(), 0.2, seed=seed)
 
 
+# ---- generated suspensions for the learned warm start ---------------------
+
+def box_training(nx=64):
+    """Slit of the training suspensions: gap 10a, x-z spacing and Chebyshev
+    grid of the 100-capsule workload (alpha = 1.6, r_cut = 2.5), a periodic
+    cell of nx x nx intervals (20 x 20 for nx = 64)."""
+    return Box(Lx=0.3125 * nx, Lz=0.3125 * nx, W=10.0, y0=-5.0, Nx=nx, Ny=65, Nz=nx)
+
+
+# (volume fraction, viscosity ratio, cell intervals) of the training suspensions:
+# 48 to 382 capsules of 642 nodes, phi from 0.05 to 0.3, lambda in {0.2, 1, 5}
+TRAINING_SET = ((0.05, 5.0, 64), (0.1, 0.2, 64), (0.2, 1.0, 64), (0.3, 5.0, 64),
+                (0.1, 1.0, 128), (0.2, 5.0, 64))
+
+
+def training_suspensions(seed=1):
+    """Generated suspensions for training the learned warm start: for each
+    entry of TRAINING_SET, spherical level-3 capsules filling box_training(nx)
+    to that volume fraction (seed, seed + 1, ...), with its viscosity ratio.
+    Returns [(suspension, lambda)]."""
+    return [(capsules_at_phi(box_training(nx), phi, seed=seed + k), lam)
+            for k, (phi, lam, nx) in enumerate(TRAINING_SET)]
+
+
 # Evans-Fung biconcave profile of a red blood cell in units of its radius R0:
 # half-thickness h(rho) = (R0/2) sqrt(1 - rho^2) (C0 + C1 rho^2 + C2 rho^4),
 # rho the distance from the axis over R0 (Evans and Fung 1972).

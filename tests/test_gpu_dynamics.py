@@ -107,3 +107,35 @@ def test_checkpoint_resume(ggem, tmp_path):
     assert moved > 1e-3
     assert np.abs(x_b - x_a).max() < 1e-10 * moved
     assert rec_b["iters"] == rec_a["iters"] and rec_b["dt"] == pytest.approx(rec_a["dt"], rel=1e-14)
+
+
+def test_checkpoint_keeps_the_learned_model_and_its_adam_state(ggem, tmp_path):
+    """A checkpoint of a plan holding a learned model keeps the model, its
+    Adam moments and step count: the resumed plan holds the same state, and
+    one more training epoch on the same samples moves both plans'
+    parameters alike."""
+    from paper_1109_6587_gb300 import dynamics as D
+    s = _capsule()
+    P, S = _suspension(ggem, s, "mixed", lam=5.0)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((600, 12))
+    T = 0.3 * rng.standard_normal((600, 3))
+    P.mlp_train(X, T, init=True, seed=2, epochs=3, batch=200, lr=1e-3)
+    m, v, step = P.mlp_adam_state()
+    assert step == 9 and np.abs(m).max() > 0 and v.min() >= 0
+    path = tmp_path / "ckpt.npz"
+    S.save(path)
+    P2 = ggem.Plan.for_box(s.box, precision="mixed", quadrature="element",
+                           max_points=len(s.x), max_tris=len(s.tri))
+    D.Suspension.resume(P2, path)
+    m2, v2, step2 = P2.mlp_adam_state()
+    assert step2 == step and np.array_equal(m2, m) and np.array_equal(v2, v)
+    assert np.array_equal(P2.mlp_save(), P.mlp_save())
+    before = P.mlp_save()[25:]
+    P.mlp_train(X, T, init=False, seed=5, epochs=1, batch=600, lr=1e-3)
+    P2.mlp_train(X, T, init=False, seed=5, epochs=1, batch=600, lr=1e-3)
+    a, b = P.mlp_save()[25:], P2.mlp_save()[25:]
+    assert np.abs(a - before).max() > 1e-5
+    assert np.abs(a - b).max() <= 1e-6 * (1.0 + np.abs(a).max())
+    P.check()
+    P2.check()

@@ -4,9 +4,11 @@ it gains in the Fredholm solve.
   * features: FP32 copies of the oracle's FP64 values (1e-6 relative), the
     double-layer columns at the mixed parity (1e-5); the crowding count, an
     integer decided in FP64 on both sides, exactly;
-  * forward: the bfloat16 network against the oracle with the same rounding
-    points (FP32 vs FP64 accumulation can move a hidden activation by one
-    bfloat16 step: 1e-2 of the output scale);
+  * forward: the bfloat16 network (tensor-core kernel) against the oracle
+    with the same rounding points (FP32 vs FP64 accumulation can move a
+    hidden activation by one bfloat16 step: 1e-2 of the output scale), most
+    rows, those with no such step, within 1e-5; the learned guess equals
+    r + s s_y times the forward output of its own features;
   * gradient of one full-batch pass against the oracle's backpropagation
     (2e-2 relative per parameter tensor), and the loss (1e-3);
   * one Adam step moves the parameters in the oracle's direction, and its
@@ -113,6 +115,29 @@ def test_forward_matches_oracle(ggem, susp):
     out = P.mlp_forward(X)
     _, ref = M.forward(params, (X - mu) / sigma, bf16_round=True)
     assert np.abs(out - ref).max() < 1e-2 * np.abs(ref).max()
+
+
+def test_tensor_core_forward_rows_and_guess(ggem, susp):
+    P = _plan(ggem, susp)
+    params, mu, sigma, s_y, blob = _model(13)
+    P.mlp_load(blob)
+    X = np.random.default_rng(14).standard_normal((3000, 12))
+    out = P.mlp_forward(X)
+    pf = [_f32(p) for p in params]
+    _, ref = M.forward(pf, (_f32(X) - _f32(mu)) / _f32(sigma), bf16_round=True)
+    scale = np.abs(ref).max()
+    row_err = np.abs(out - ref).max(1) / scale
+    assert row_err.max() < 1e-2
+    assert (row_err < 1e-5).mean() > 0.8, float((row_err < 1e-5).mean())
+    # the learned guess of the solve: r + s s_y y(features of r), same kernel
+    kappa, b = W.bie_rhs(susp, seed=15)
+    r = np.random.default_rng(16).standard_normal(susp.x.shape)
+    f, sc = P.mlp_features(_dev(kappa), _dev(r))
+    y = P.mlp_forward(f)
+    g = P.mlp_guess(_dev(kappa), _dev(r)).cpu().numpy()
+    expect = r + sc * s_y * y
+    assert np.abs(g - expect).max() < 1e-6 * np.abs(expect).max()
+    P.check()
 
 
 def test_gradient_and_adam_match_oracle(ggem, susp):
@@ -257,6 +282,43 @@ def test_bf16_adam_values_match_oracle_on_the_kernel_gradient(ggem, susp):
     assert sure.mean() > 0.9
     assert (np.abs(new[sure] - pr[sure]) <= 2.5e-7 * np.abs(pr[sure]) + 2e-8).all()
     assert (np.abs(new - p0) <= 1e-3 * (1 + 1e-6) + 2.5e-7 * np.abs(p0)).all()
+
+
+def test_tensor_core_training_gradient(ggem, susp):
+    """BF16 mode trains with tensor-core GEMMs (deltas split into two
+    bfloat16 terms): its full-batch gradient against the oracle's with the
+    same rounding points, per tensor within 5e-3 in norm, and 99 % of the
+    entries within 1e-3 of the sum of their terms' magnitudes (the rest can
+    see a hidden activation one bfloat16 step away)."""
+    P = _plan(ggem, susp)
+    params, mu, sigma, s_y, blob = _model(61)
+    P.mlp_load(blob)
+    rng = np.random.default_rng(62)
+    X = rng.standard_normal((700, 12))
+    T = rng.standard_normal((700, 3)) * 0.3
+    loss, g = P.mlp_train(X, T, init=False, epochs=0, want_grad=True)
+    pf = [_f32(p) for p in params]
+    Z = (_f32(X) - _f32(mu)) / _f32(sigma)
+    Y = _f32(T) / _f32(s_y)
+    ref_loss, ref_g = M.loss_and_grads(pf, Z, Y, bf16_round=True)
+    assert abs(loss - ref_loss) < 1e-3 * ref_loss
+    acts, out = M.forward(pf, Z, bf16_round=True)
+    delta = np.abs(2.0 * (out - Y) / out.size)
+    off, near, total = 0, 0, 0
+    for layer in range(3, -1, -1):
+        h = np.abs(acts[layer])
+        sW, sb = h.T @ delta, delta.sum(0)
+        for k, sc in ((2 * layer, sW), (2 * layer + 1, sb)):
+            rg = ref_g[k]
+            o = sum(x.size for x in ref_g[:k])
+            gg = g[o:o + rg.size].reshape(rg.shape)
+            assert np.linalg.norm(gg - rg) < 5e-3 * np.linalg.norm(rg), k
+            near += int((np.abs(gg - rg) <= 1e-3 * sc + 1e-9).sum())
+            total += rg.size
+        if layer > 0:
+            delta = (delta @ np.abs(M.bf16(pf[2 * layer])).T) * (acts[layer] > 0)
+    assert near >= 0.99 * total, near / total
+    P.check()
 
 
 def test_learned_warm_start_reduces_iterations(ggem):
