@@ -407,7 +407,9 @@ ggem_status ggem_volume_correct(ggem_plan_t *plan, const double *v0, double thre
  * (at most max_sweeps) until no pair is nearer than h_min (1 - 1e-9).  Gaps
  * are node to node: they see near contacts, not deep overlaps.  h_min must be
  * at most a cell width of the plan (pairs are searched in neighbouring
- * cells).  Moves the plan's mesh; moves (out, may be NULL): pair moves made. */
+ * cells).  Moves the plan's mesh; moves (out, may be NULL): pair moves made.
+ * GGEM_ERR_CAPACITY when a node lies within h_min of more than 4 other
+ * particles (their pairs could not all be recorded). */
 ggem_status ggem_overlap_correct(ggem_plan_t *plan, double h_min, int max_sweeps, int *moves);
 
 /*
@@ -491,6 +493,13 @@ ggem_status ggem_mlp_precision(ggem_plan_t *plan, int mode);
 ggem_status ggem_mlp_load(ggem_plan_t *plan, const double *model, size_t count);
 ggem_status ggem_mlp_save(ggem_plan_t *plan, double *model, size_t count);
 
+/* Adam state of the model (first and second moments [35075], FP32 on the
+ * device, and the step count that sets the bias corrections): set = 0 reads
+ * it into m, v, *step; set = 1 replaces it (checkpoint / resume of training).
+ * m, v host or device. */
+ggem_status ggem_mlp_adam_state(ggem_plan_t *plan, int set, double *m, double *v,
+                                long long *step);
+
 /* Raw network output [n][3] (units of s_y) for n feature rows [n][12]. */
 ggem_status ggem_mlp_forward(ggem_plan_t *plan, int n, const double *feat, double *out);
 
@@ -504,17 +513,26 @@ ggem_status ggem_mlp_forward(ggem_plan_t *plan, int n, const double *feat, doubl
  * weights.  *loss (may be NULL) gets the mean minibatch loss of the last
  * epoch.  With epochs = 0, one full-batch pass in row order computes *loss
  * and, when grad_out is not NULL, the gradient [35075] without updating.
- * Allocates and frees its own staging buffers.
+ * Allocates and frees its own staging buffers.  GGEM_ERR_NUMERICAL when init
+ * finds a non-finite feature or target.
  */
 ggem_status ggem_mlp_train(ggem_plan_t *plan, int n, const double *feat, const double *target,
                            int init, unsigned long long seed, int epochs, int batch, double lr,
                            double *loss, double *grad_out);
 
 /* Device-side status of the plan's kernels: waits with an iteration limit
- * (the tensor-core transforms' mbarrier waits) record a failure instead of
+ * (the tensor-core kernels' mbarrier waits) record a failure instead of
  * hanging; GGEM_ERR_CUDA here means results since the plan was created are
  * invalid.  Synchronises the plan's stream. */
 ggem_status ggem_check(ggem_plan_t *plan);
+
+/* Failure injection for tests of the bounded waits (no counterpart in the
+ * paper): the next tensor-core Chebyshev transform launched in this process
+ * (by any plan) issues no MMA for the first tile of each CTA and polls its
+ * mbarrier at most `polls` times (1 .. 2^24), so its wait expires with no
+ * work in flight: the kernel records the failure (seen by ggem_check),
+ * releases its tensor memory and returns; the CUDA context stays usable. */
+ggem_status ggem_inject_tc_wait_expiry(long polls);
 
 /*
  * Tracing (no counterpart in the paper).  With tracing enabled, each stage
@@ -528,6 +546,17 @@ int ggem_trace_stage_count(void);
 const char *ggem_trace_stage_name(int stage);
 ggem_status ggem_trace_read(const ggem_plan_t *plan, int stage, double *total_ms,
                             long *calls);
+/* Measurement probe (no counterpart in the paper): the throughput of float4
+ * vector reductions (atomic adds) into an L2-resident buffer of nvec 16-byte
+ * vectors (a multiple of 32, at most 2^28) -- the operation the spreading is
+ * bound by: 8 blocks of 256 threads per SM, every warp adding into 32
+ * consecutive vectors at a pseudo-random position, `iters` times each; one
+ * untimed launch, then one timed by CUDA events on `stream`.  *ms: the
+ * timed launch; *vec_per_s: vector reductions per second.  Allocates and
+ * frees its buffer. */
+ggem_status ggem_probe_l2_reduction(long nvec, int iters, void *stream, double *ms,
+                                    double *vec_per_s);
+
 /* Number of library kernels launched by this plan since creation or the
  * last ggem_trace_enable. */
 ggem_status ggem_launch_count(const ggem_plan_t *plan, long *launches);

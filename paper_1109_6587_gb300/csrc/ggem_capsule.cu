@@ -282,7 +282,8 @@ constexpr int kGapSlots = 4;   // other particles recorded per node
 
 // every node: the closest node of each (of up to kGapSlots) other particles
 // nearer than hthr in its own or a neighbouring cell; records (p, q, gap) for
-// q > p, p the node's own particle
+// q > p, p the node's own particle.  count[0]: records; count[1] set when a
+// node meets more than kGapSlots other particles (a record would be lost).
 __global__ void k_gap_pairs(int n, GridGeom geo, CellGrid cg, const int* __restrict__ cell,
                             const int* __restrict__ start, const int* __restrict__ perm,
                             const int* __restrict__ part, const double* __restrict__ x,
@@ -320,6 +321,8 @@ __global__ void k_gap_pairs(int n, GridGeom geo, CellGrid cg, const int* __restr
                         sq[ns] = q;
                         sd[ns] = d;
                         ++ns;
+                    } else {
+                        atomicOr(count + 1, 1);
                     }
                 }
             }
@@ -681,7 +684,7 @@ ggem_status ggem_overlap_correct(ggem_plan_t* P, double h_min, int max_sweeps, i
         if (!P->d_orec) {
             dalloc(P, &P->d_orec, (size_t)2 * cap);
             dalloc(P, &P->d_orecd, (size_t)cap);
-            dalloc(P, &P->d_ocount, 1);
+            dalloc(P, &P->d_ocount, 2);
         }
         dfree(P->d_odisp);
         P->d_odisp = nullptr;
@@ -692,7 +695,7 @@ ggem_status ggem_overlap_correct(ggem_plan_t* P, double h_min, int max_sweeps, i
         const double hthr = h_min * (1.0 - 1e-9);   // corrected gaps land on h_min
         int total = 0;
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-            GG_CUDA(cudaMemsetAsync(P->d_ocount, 0, sizeof(int), P->st));
+            GG_CUDA(cudaMemsetAsync(P->d_ocount, 0, 2 * sizeof(int), P->st));
             k_gap_pairs<<<nblk(n), CB, 0, P->st>>>(n, P->geo, P->cg, P->d_mesh_cell,
                                                    P->d_mesh_start, P->d_mesh_perm,
                                                    P->d_particle, P->d_x, hthr, cap, P->d_orec,
@@ -700,13 +703,16 @@ ggem_status ggem_overlap_correct(ggem_plan_t* P, double h_min, int max_sweeps, i
             k_centroids<<<np, CB, 0, P->st>>>(P->d_pstart, P->d_pnodes, P->d_x, P->d_odisp);
             GG_CUDA(cudaGetLastError());
             P->launches += 2;
-            int cnt = 0;
-            GG_CUDA(cudaMemcpyAsync(&cnt, P->d_ocount, sizeof(int), cudaMemcpyDeviceToHost,
+            int cnt2[2] = {0, 0};
+            GG_CUDA(cudaMemcpyAsync(cnt2, P->d_ocount, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                     P->st));
             GG_CUDA(cudaMemcpyAsync(c.data(), P->d_odisp, c.size() * sizeof(double),
                                     cudaMemcpyDeviceToHost, P->st));
             GG_CUDA(cudaStreamSynchronize(P->st));
+            const int cnt = cnt2[0];
             GG_CHECK(cnt <= cap, GGEM_ERR_CAPACITY, "overlap records overflowed");
+            GG_CHECK(cnt2[1] == 0, GGEM_ERR_CAPACITY,
+                     "a node is within h_min of more than 4 other particles");
             if (cnt == 0) break;
             rec.resize(2 * (size_t)cnt);
             recd.resize(cnt);

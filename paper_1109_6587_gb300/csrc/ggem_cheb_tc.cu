@@ -25,6 +25,7 @@
 // stops, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "ggem_internal.cuh"
@@ -35,6 +36,11 @@ namespace {
 
 constexpr int TCT = 128;                 // threads per CTA (4 warps = 128 TMEM lanes)
 constexpr long kWaitLimit = 1L << 24;    // mbarrier polls before giving up
+
+// Failure injection for tests (ggem_inject_tc_wait_expiry): when > 0, the next
+// launch skips issuing and committing the MMAs of every CTA's first tile and
+// polls at most this many times, so that its wait expires with nothing in flight.
+std::atomic<long> g_inject_polls{0};
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -64,9 +70,9 @@ __device__ __forceinline__ void split(float v, __nv_bfloat16& h, __nv_bfloat16& 
     l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, long limit) {
     uint32_t done = 0;
-    for (long it = 0; it < kWaitLimit && !done; ++it)
+    for (long it = 0; it < limit && !done; ++it)
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}\n"
@@ -92,7 +98,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __global__ void __launch_bounds__(TCT)
     k_cheb_tc(int Ny, int Kp, int MB, int NT, uint32_t tcols, const uint4* __restrict__ Mprep,
               const float* __restrict__ in, float* __restrict__ out, long cols, long ntiles,
-              int* __restrict__ err) {
+              int* __restrict__ err, long wait_limit, int skip_first) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __nv_bfloat16* Ah = reinterpret_cast<__nv_bfloat16*>(sm);
     __nv_bfloat16* Al = Ah + (size_t)MB * 128 * Kp;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(TCT)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
+        if (tid == 0 && !(skip_first && tile == blockIdx.x)) {
             const uint32_t bh = saddr(Bh), bl = saddr(Bl);
             for (int mb = 0; mb < MB; ++mb) {
                 const uint32_t ah = saddr(Ah + (size_t)mb * 128 * Kp),
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(TCT)
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     saddr(mbar)));
         }
-        const bool ok = wait_phase(saddr(mbar), parity);
+        const bool ok = wait_phase(saddr(mbar), parity, wait_limit);
         parity ^= 1u;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(TCT)
     }
     // on a failed wait the MMAs may still be running: give them one more
     // bounded wait before the tensor memory is released
-    if (s_fail && tid == 0) wait_phase(saddr(mbar), parity ^ 1u);
+    if (s_fail && tid == 0) wait_phase(saddr(mbar), parity ^ 1u, wait_limit);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -283,10 +289,18 @@ cudaError_t cheb_apply_tc(int Ny, const void* prep, const float* in, float* out,
     // computes); each holds at most 256 of the SM's 512 tensor-memory columns
     const long per_sm = (2 * smem <= 227 * 1024) ? 2 : 1;
     const long grid = ntiles < per_sm * nsm ? ntiles : per_sm * nsm;
+    const long inject = g_inject_polls.exchange(0);
     k_cheb_tc<<<(unsigned)grid, TCT, smem, st>>>(Ny, Kp, MB, NT, tcols,
                                                  static_cast<const uint4*>(prep), in, out, cols,
-                                                 ntiles, err);
+                                                 ntiles, err, inject > 0 ? inject : kWaitLimit,
+                                                 inject > 0 ? 1 : 0);
     return cudaGetLastError();
 }
 
 }  // namespace ggem
+
+extern "C" ggem_status ggem_inject_tc_wait_expiry(long polls) {
+    if (polls < 1 || polls > (1L << 24)) return GGEM_ERR_INVALID_ARG;
+    ggem::g_inject_polls.store(polls);
+    return GGEM_OK;
+}

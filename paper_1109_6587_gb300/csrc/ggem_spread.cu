@@ -336,4 +336,60 @@ cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, co
 GGEM_INST_SPREAD(float)
 GGEM_INST_SPREAD(double)
 
+// ------------------------------------------------------------------ probe
+// Throughput of float4 vector reductions into an L2-resident buffer, the
+// operation the spreading is bound by: every warp adds into 32 consecutive
+// 16-byte vectors (one per lane, as lanes on consecutive grid columns do) at a
+// pseudo-random position of the buffer, `iters` times.  The roof the
+// spreading's reduction rate is measured against.
+namespace {
+__global__ void k_red_probe(float4* __restrict__ buf, unsigned nvec, int iters, unsigned seed) {
+    const unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    unsigned h = (w + 1u) * 2654435761u ^ seed;
+    for (int it = 0; it < iters; ++it) {
+        h = h * 1664525u + 1013904223u;
+        const unsigned base = (h % (nvec >> 5)) << 5;
+        atomicAdd(buf + base + lane, make_float4(1.f, 1.f, 1.f, 0.f));
+    }
+}
+}  // namespace
+
 }  // namespace ggem
+
+extern "C" ggem_status ggem_probe_l2_reduction(long nvec, int iters, void* stream, double* ms,
+                                               double* vec_per_s) {
+    if (nvec < 32 || (nvec & 31) || nvec > (1L << 28) || iters < 1 || !ms || !vec_per_s)
+        return GGEM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GGEM_ERR_CUDA;
+    float4* buf = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ggem_status s = GGEM_OK;
+    if (cudaMalloc((void**)&buf, (size_t)nvec * sizeof(float4)) != cudaSuccess)
+        return GGEM_ERR_CUDA;
+    const int blocks = 8 * nsm, threads = 256;
+    if (cudaMemsetAsync(buf, 0, (size_t)nvec * sizeof(float4), st) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        s = GGEM_ERR_CUDA;
+    } else {
+        ggem::k_red_probe<<<blocks, threads, 0, st>>>(buf, (unsigned)nvec, iters, 7u);  // warm
+        cudaEventRecord(a, st);
+        ggem::k_red_probe<<<blocks, threads, 0, st>>>(buf, (unsigned)nvec, iters, 11u);
+        cudaEventRecord(b, st);
+        float t = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess) {
+            s = GGEM_ERR_CUDA;
+        } else {
+            *ms = t;
+            *vec_per_s = (double)blocks * threads * iters / (t * 1e-3);
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(buf);
+    return s;
+}

@@ -53,7 +53,8 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_capsule_step", "ggem_mesh_positions", "ggem_min_separation",
            "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct",
            "ggem_set_offgrid", "ggem_mlp_precision", "ggem_precond_set",
-           "ggem_precond_enable", "ggem_precond_block"]
+           "ggem_precond_enable", "ggem_precond_block", "ggem_inject_tc_wait_expiry",
+           "ggem_mlp_adam_state", "ggem_probe_l2_reduction"]
 
 GGEM_OFFGRID = {"lagrange": 0, "spectral": 1}
 
@@ -118,6 +119,10 @@ def lib():
         L.ggem_precond_set.argtypes = [P, I, P, I, P, D, I, I]
         L.ggem_precond_enable.argtypes = [P, I]
         L.ggem_precond_block.argtypes = [P, P]
+        L.ggem_inject_tc_wait_expiry.argtypes = [ctypes.c_long]
+        L.ggem_probe_l2_reduction.argtypes = [ctypes.c_long, I, P, ctypes.POINTER(D),
+                                              ctypes.POINTER(D)]
+        L.ggem_mlp_adam_state.argtypes = [P, I, P, P, ctypes.POINTER(ctypes.c_longlong)]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
         L.ggem_mlp_train.argtypes = [P, I, P, P, I, ctypes.c_ulonglong, I, I, D,
@@ -555,6 +560,23 @@ class Plan:
         _check(lib().ggem_mlp_save(self.h, m.ctypes.data_as(ctypes.c_void_p), m.size), self.h)
         return m
 
+    def mlp_adam_state(self, state=None):
+        """The model's Adam moments and step count (m, v, step); with state =
+        (m, v, step), replace them instead."""
+        st = ctypes.c_longlong(0)
+        if state is None:
+            m, v = np.zeros(35075), np.zeros(35075)
+            _check(lib().ggem_mlp_adam_state(self.h, 0, m.ctypes.data_as(ctypes.c_void_p),
+                                             v.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.byref(st)), self.h)
+            return m, v, int(st.value)
+        m = np.ascontiguousarray(state[0], dtype=np.float64)
+        v = np.ascontiguousarray(state[1], dtype=np.float64)
+        st.value = int(state[2])
+        _check(lib().ggem_mlp_adam_state(self.h, 1, m.ctypes.data_as(ctypes.c_void_p),
+                                         v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st)),
+               self.h)
+
     def mlp_forward(self, feat):
         f = np.ascontiguousarray(np.asarray(feat.cpu() if hasattr(feat, "cpu") else feat),
                                  dtype=np.float64)
@@ -614,3 +636,14 @@ def ggem_point_forces(plan, xs, g, xt=None, want_u=True, want_sigma=False):
 
 def ggem_mesh_set(plan, x, tri=None):
     return plan.mesh_set(x, tri)
+
+
+def probe_l2_reduction(nvec=1 << 21, iters=256, stream=None):
+    """Throughput of float4 vector reductions into an L2-resident buffer
+    (ggem_probe_l2_reduction): (milliseconds, vector reductions per second)."""
+    ms, rate = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().ggem_probe_l2_reduction(int(nvec), int(iters), ctypes.c_void_p(stream or 0),
+                                       ctypes.byref(ms), ctypes.byref(rate))
+    if st != 0:
+        raise GGEMError(st, "L2 reduction probe failed")
+    return ms.value, rate.value
