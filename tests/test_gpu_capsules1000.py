@@ -9,6 +9,7 @@ import pathlib
 
 import numpy as np
 import pytest
+from _parity import assert_close
 
 from paper_1109_6587_gb300 import workloads as W
 
@@ -47,10 +48,10 @@ def test_capsules1000_layers(case, prec, quad):
     qd = torch.as_tensor(q, device=dev)
     w = P.single_layer(qd).cpu().numpy()[idx]
     if quad == "nodal":
-        assert _rel(w, ref["w_nodal"]) < TOL[prec]
+        assert_close(w, ref["w_nodal"], TOL[prec])
     else:
-        assert _rel(w, ref["w_elem"]) < TOL[prec]
+        assert_close(w, ref["w_elem"], TOL[prec])
         v = P.double_layer(qd).cpu().numpy()[idx]
-        assert _rel(v, ref["v_elem"]) < TOL[prec]
+        assert_close(v, ref["v_elem"], TOL[prec])
     P.check()
     P.close()

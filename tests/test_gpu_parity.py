@@ -7,6 +7,7 @@ Tolerances (max |gpu - oracle| / max |oracle| over all outputs):
 """
 import numpy as np
 import pytest
+from _parity import assert_close
 
 from oracle import oracle as O
 from paper_1109_6587_gb300 import workloads as W
@@ -58,8 +59,8 @@ def test_point_forces_self_targets(ggem, sphere, prec):
     P = ggem.Plan.for_box(s.box, precision=prec, max_points=1000)
     u, sig = P.point_forces(_dev(s.x), _dev(g), want_sigma=True)
     torch.cuda.synchronize()
-    assert _rel(u, u_ref) < TOL[prec]
-    assert _rel(sig, s_ref) < TOL[prec]
+    assert_close(u, u_ref, TOL[prec])
+    assert_close(sig, s_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -77,8 +78,8 @@ def test_point_forces_free_targets_including_walls(ggem, prec):
     P = ggem.Plan.for_box(box, precision=prec, max_points=1000)
     u, sig = P.point_forces(_dev(s.x), _dev(g), _dev(xt), want_sigma=True)
     torch.cuda.synchronize()
-    assert _rel(u, u_ref) < TOL[prec]
-    assert _rel(sig, _sym6(s_ref)) < TOL[prec]
+    assert_close(u, u_ref, TOL[prec])
+    assert_close(sig, _sym6(s_ref), TOL[prec])
 
 
 def test_point_forces_host_buffers_match_device(ggem, sphere):
@@ -86,7 +87,7 @@ def test_point_forces_host_buffers_match_device(ggem, sphere):
     P = ggem.Plan.for_box(s.box, precision="fp64", max_points=1000)
     u_host, _ = P.point_forces(s.x, g)           # numpy in, numpy out
     assert isinstance(u_host, np.ndarray)
-    assert _rel(u_host, u_ref) < TOL["fp64"]
+    assert_close(u_host, u_ref, TOL["fp64"])
 
 
 def test_exact_single_sphere_workload_up_to_pairs_at_rcut(ggem):
@@ -118,7 +119,7 @@ def test_single_source_and_empty(ggem):
     u_ref, _ = O.point_forces(box, xs, g, xt)
     P = ggem.Plan.for_box(box, precision="fp64", max_points=10)
     u, _ = P.point_forces(_dev(xs), _dev(g), _dev(xt))
-    assert _rel(u, u_ref) < TOL["fp64"]
+    assert_close(u, u_ref, TOL["fp64"])
     u0, _ = P.point_forces(_dev(np.zeros((0, 3))), _dev(np.zeros((0, 3))), _dev(xt))
     assert float(u0.abs().max()) == 0.0
 
@@ -143,8 +144,8 @@ def test_nodal_single_and_double_layer(ggem, prec):
     w = P.single_layer(_dev(q))
     v = P.double_layer(_dev(q))
     torch.cuda.synchronize()
-    assert _rel(w, w_ref) < TOL[prec]
-    assert _rel(v, v_ref) < TOL[prec]
+    assert_close(w, w_ref, TOL[prec])
+    assert_close(v, v_ref, TOL[prec])
     area, nrm = P.mesh_geometry()
     _, _, Ab, nb = O.geometry(s.x, s.tri)
     assert np.abs(area - Ab).max() < 1e-14 and np.abs(nrm - nb).max() < 1e-13
@@ -174,8 +175,8 @@ def test_100_capsules_sampled(ggem, prec):
     w = P.single_layer(_dev(q))
     v = P.double_layer(_dev(q))
     torch.cuda.synchronize()
-    assert _rel(w[idx], w_ref) < TOL[prec]
-    assert _rel(v[idx], v_ref) < TOL[prec]
+    assert_close(w[idx], w_ref, TOL[prec])
+    assert_close(v[idx], v_ref, TOL[prec])
     P.check()          # no expired device-side wait (tensor-core transforms)
 
 
@@ -197,12 +198,12 @@ def test_local_sum_alone(ggem, prec):
     P = ggem.Plan.for_box(box, precision=prec, max_points=s.x.shape[0])
     u, sig = P.local_sum(_dev(s.x), _dev(g), _dev(xt), want_sigma=True)
     torch.cuda.synchronize()
-    assert _rel(u, u_ref) < TOL[prec]
-    assert _rel(sig, _sym6(s_ref)) < TOL[prec]
+    assert_close(u, u_ref, TOL[prec])
+    assert_close(sig, _sym6(s_ref), TOL[prec])
     # self targets: the self pair (r = 0) is left out
     us, _ = P.local_sum(_dev(s.x), _dev(g))
     us_ref, _ = O.local_point(box, alpha, rcut, 1.0, s.x, g, s.x[idx])
-    assert _rel(us[idx], us_ref) < TOL[prec]
+    assert_close(us[idx], us_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_emulated"])
@@ -219,8 +220,8 @@ def test_element_single_and_double_layer(ggem, prec):
     w = P.single_layer(_dev(q))
     v = P.double_layer(_dev(q))
     torch.cuda.synchronize()
-    assert _rel(w, w_ref) < TOL[prec]
-    assert _rel(v, v_ref) < TOL[prec]
+    assert_close(w, w_ref, TOL[prec])
+    assert_close(v, v_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_emulated"])
@@ -237,8 +238,8 @@ def test_element_100_capsules_sampled(ggem, prec):
     w = P.single_layer(_dev(q))
     v = P.double_layer(_dev(q))
     torch.cuda.synchronize()
-    assert _rel(w[idx], w_ref) < TOL[prec]
-    assert _rel(v[idx], v_ref) < TOL[prec]
+    assert_close(w[idx], w_ref, TOL[prec])
+    assert_close(v[idx], v_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -261,6 +262,6 @@ def test_point_forces_anisotropic_grids(ggem, prec, shape):
     P = ggem.Plan.for_box(box, precision=prec, max_points=300)
     u, sig = P.point_forces(_dev(xs), _dev(g), _dev(xt), want_sigma=True)
     torch.cuda.synchronize()
-    assert _rel(u, u_ref) < TOL[prec]
-    assert _rel(sig, _sym6(s_ref)) < TOL[prec]
+    assert_close(u, u_ref, TOL[prec])
+    assert_close(sig, _sym6(s_ref), TOL[prec])
     P.check()
