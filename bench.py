@@ -4,20 +4,23 @@ Step: one pass of the matvec hot path over the workload -- the single-layer
 and the double-layer operators evaluated at every node (Sec. 3.4, 3.5 of
 Kumar & Graham, arXiv 1109.6587) for fresh N(0,1) densities.
 
-Workload (default): 100 spherical capsules x 642 nodes = 64,200 points in a
-40 x [-5,5] x 40 slit, grid 128 x 65 x 128, mixed precision, element
+Workload (default): 4000 biconcave capsules x 642 nodes = 2,568,000 points in
+a 150 x [-15,15] x 150 slit, grid 512 x 129 x 512, mixed precision, element
 quadrature (the paper's layer rule; --quadrature nodal for point forces).
 Metric: Mpts/s = nodes / (time of one single + one double layer evaluation).
 The second half of the metric -- GMRES iterations and seconds per Fredholm
-solve at true relative residual 1e-6, per emulated time step, for the plain
-FP64 solve, the mixed solve and the mixed solve with the learned warm start
--- is measured on the same workload and reported under "solve".
+solve at true relative residual 1e-6 -- is reported under "solve" on the
+1000-capsule workload (642,000 points, viscosity ratio 5) per emulated time
+step for the plain FP64 solve, the FP64-accurate emulated one and the mixed
+solve with and without the per-particle block preconditioner and the
+learned warm start (trained on generated suspensions), and under "dynamics"
+as seconds per capsule time step of the default workload in shear.
 
-Other workloads (--workload capsules1000 or rbc4000: 642,000 and 2,568,000
+Other workloads (--workload capsules100 or capsules1000: 64,200 and 642,000
 points; capsules100_phi and capsules1000_phi: the 100- and 1000-capsule slits
 filled to volume fractions 0.1 and 0.2, 245,244 and 3,923,904 points) measure
-the same step at the larger configurations; the pair counts of their roofline
-are taken on a sample of 20,000 targets.
+the same step; the pair counts of the roofline are taken on a sample of
+20,000 targets for workloads above 100,000 points.
 
 The off-grid evaluation of the global part is the paper's 5-point Lagrange
 interpolation by default; --offgrid spectral times the spectrally accurate
@@ -27,7 +30,8 @@ evaluation instead, and the default run reports the other mode's step under
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 under torchrun each rank runs an independent replica on its own
 GPU (the evaluation is one problem per GPU; no collective), value = sum of
-the ranks' points / the slowest rank's time.
+the ranks' points / the slowest rank's time.  --impl reference times the FP64
+oracle on the host cores, each step a proportional sample of every stage.
 """
 from __future__ import annotations
 
@@ -56,15 +60,18 @@ def _args():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_emulated"])
     ap.add_argument("--quadrature", default="element", choices=["nodal", "element"])
-    ap.add_argument("--workload", default="capsules100",
+    ap.add_argument("--workload", default="rbc4000",
                     choices=["capsules100", "capsules1000", "rbc4000", "capsules100_phi",
                              "capsules1000_phi"],
-                    help="capsules100 (default, the benchmark configuration), capsules1000 "
-                         "(642,000 points), rbc4000 (2,568,000 points), capsules100_phi / "
-                         "capsules1000_phi (the same slits at volume fractions 0.1 / 0.2); "
-                         "the CPU baseline runs on the default only")
+                    help="rbc4000 (default: 4000 biconcave capsules, 2,568,000 points, the "
+                         "largest configuration), capsules100 (64,200 points), capsules1000 "
+                         "(642,000 points), capsules100_phi / capsules1000_phi (the same "
+                         "slits at volume fractions 0.1 / 0.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--fp64-step", action="store_true",
+                    help="also time one capsule time step with the plain native-FP64 solver "
+                         "(minutes on the largest workload)")
     ap.add_argument("--offgrid", default="lagrange", choices=["lagrange", "spectral"],
                     help="off-grid evaluation of the global part (5-point Lagrange or the "
                          "spectral non-uniform FFT evaluation)")
@@ -163,6 +170,19 @@ def _peaks():
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
+
+# Algorithmic flops of one (target, source) pair of the local sum (see roofline)
+FLOPS_PAIR_SINGLE = 67
+FLOPS_PAIR_DOUBLE = 87
+# DRAM bytes (read + write) of one local-sum launch, the single- and the
+# double-layer launch averaged as the stage is, from ncu captures of the
+# kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum; the
+# summaries are kept with the profiles), per (workload, precision, quadrature);
+# none for other configurations
+LOCAL_TRAFFIC = {
+    ("rbc4000", "mixed", "element"): (3904399104 + 41290240 + 4067564288 + 39082752) / 2,
+    ("capsules100", "mixed", "element"): (93218304 + 3518208 + 94636288 + 4180736) / 2,
+}
 
 SAMPLE_ABOVE = 100_000      # larger workloads count pairs on a sample of targets
 SAMPLE_TARGETS = 20_000
@@ -327,27 +347,29 @@ def roofline(res, args):
     plane = b.Nz * b.Nx
     if name == "local_sum":
         pairs = _elem_pair_count(susp, rc) if args.quadrature == "element" else _pair_count(susp, rc)
-        # FP32 operations per pair of the kernel's formula (distance, rsqrt and
-        # exp2 as one each, the 17-FMA erfcx polynomial, the G^l or n.T^l
-        # contraction): single layer 74, double layer 99; the stage averages
-        # one launch of each
-        flops = pairs * (74.0 + 99.0) / 2.0
-        sm_mhz = res["clocks"]["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        # algorithmic flops per (target, source) pair within r_cut, counting
+        # add, sub, mul and rsqrt / exp2 as 1 and a fused multiply-add as 2
+        # (the peak below counts an FMA as 2): displacement, r^2, 1/r, r,
+        # exp(-alpha^2 r^2), erfc(alpha r) = exp(-alpha^2 r^2) erfcx(alpha r)
+        # with the degree-14 erfcx polynomial, x.g -- 48 -- then the single
+        # layer's A = erfc/r - c1 e, B = (erfc/r^3 + c1 e/r^2) x.g and
+        # u += A g + B x (19: 67 in all) or the double layer's D, E, x.n, g.n
+        # and v += x (D x.g x.n + E g.n) + g E x.n + n E x.g with the last
+        # term summed as a scalar (39: 87 in all); the stage averages one
+        # launch of each
+        flops = pairs * (FLOPS_PAIR_SINGLE + FLOPS_PAIR_DOUBLE) / 2.0
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = flops / avg_s / 1e12
         if args.precision != "mixed":
             peak = 1.25           # FP64-accurate work against the nominal FP64 rate
-        # dram read + write bytes of one double-layer launch of the mixed
-        # element-rule kernel on this workload, from one ncu capture of that
-        # launch (its ncu summary is kept with the profiles); other
-        # configurations have no capture
-        traffic = (94.9e6 + 4.2e6) if (args.precision == "mixed"
-                                       and args.quadrature == "element"
-                                       and args.workload == "capsules100") else None
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
-                if args.precision == "mixed" else
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": LOCAL_TRAFFIC.get(
+                    (args.workload, args.precision, args.quadrature)),
+                "pairs_per_launch": pairs, "pairs_per_s": pairs / avg_s,
+                "flops_per_pair": [FLOPS_PAIR_SINGLE, FLOPS_PAIR_DOUBLE],
+                "launch_ms": avg_s * 1e3,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM "
+                               "clock" if args.precision == "mixed" else
                 "nominal FP64 (the emulated kernel issues FP32 pair arithmetic)"
                 if args.precision == "fp64_emulated" else "nominal FP64"}
     # memory-bound stages: algorithmic bytes per launch
@@ -368,151 +390,404 @@ def roofline(res, args):
             "frac": ach / peak, "traffic": None, "peak_source": kind}
 
 
-def cpu_baseline(susp, args, stride=64):
-    """The FP64 oracle as it stands on the host cores, on a bounded sample:
-    the single and double layer with their full global parts, the local part
-    at every stride-th node, scaled to all nodes."""
+# Sample sizes of one oracle step (see oracle_sample_step)
+ORACLE_SAMPLE = {"targets": 48, "wall_nodes": 64, "sources": 2048, "triangles": 65536,
+                 "planes": 2, "columns": 4096, "modes": 256, "interp_targets": 4096}
+
+
+def oracle_sample_step(susp, args, seed, aux):
+    """One step of the FP64 oracle on a bounded, proportional sample of the
+    workload: every stage of the single- and the double-layer evaluation
+    (Sec. 3.2-3.5, element quadrature) runs through the oracle's own functions
+    on a seeded sample of its independent units -- triangles (geometry),
+    target nodes (element-rule local sums), wall grid nodes (wall data),
+    sources (spreading), y-planes (x-z FFTs), (x, z) columns (Chebyshev
+    transforms), Fourier modes (tau solves, spectral stress) and targets
+    (interpolation) -- each stage's time scaled by its units / sampled units.
+    Returns (measured seconds, extrapolated seconds of the full step, per-stage
+    {name: [sample seconds, scale]})."""
     from oracle import oracle as O
-    q = np.random.default_rng(99).standard_normal((susp.x.shape[0], 3))
-    n = susp.x.shape[0]
-    idx = np.arange(0, n, stride)
+    S = ORACLE_SAMPLE
+    box = susp.box
+    n, m = susp.x.shape[0], susp.tri.shape[0]
+    Ny, Nz, Nx = box.Ny, box.Nz, box.Nx
+    rng = np.random.default_rng(seed)
+    a, rc, nb, g = aux["alpha"], aux["rcut"], aux["nb"], aux["g"]
+    q = aux["q"]
+    stages = {}
+
+    def run(name, scale, fn, reps=1):
+        t0 = time.perf_counter()
+        out = fn()
+        stages[name] = [time.perf_counter() - t0, float(scale) * reps]
+        return out
+
+    pick = lambda total, k: np.sort(rng.choice(total, min(k, total), replace=False))
+    tri_s = pick(m, S["triangles"])
+    # geometry: once per layer evaluation
+    run("geometry", m / len(tri_s), lambda: O.geometry(susp.x, susp.tri[tri_s]), reps=2)
+    tg = pick(n, S["targets"]).astype(np.int32)
+    run("local_single", n / len(tg),
+        lambda: O.local_elem(box, a, rc, 0, susp.x, susp.tri, q, targets=tg))
+    run("local_double", n / len(tg),
+        lambda: O.local_elem(box, a, rc, 1, susp.x, susp.tri, q, nrm=nb, targets=tg))
+    bot, top = O.wall_nodes(box)
+    wn = pick(2 * Nx * Nz, S["wall_nodes"])
+    walls = np.concatenate([bot, top])[wn]
+    run("wall_data", 2 * Nx * Nz / len(wn),
+        lambda: O.local_point(box, a, rc, 1.0, susp.x, g, walls), reps=2)
+    src = pick(n, S["sources"])
+    f = run("spread", n / len(src), lambda: O.spread(box, a, rc, susp.x[src], g[src]), reps=2)
+    planes = pick(Ny, S["planes"])
+    scale = 1.0 / (Nx * Nz)
+    # forward x-z transforms of the 3 forcing planes and the 2 x 3 wall planes
+    run("fft_forward", Ny / len(planes),
+        lambda: np.fft.fft2(f[:, planes], axes=(2, 3)) * scale, reps=2)
+    run("fft_walls", 1.0, lambda: np.fft.fft2(np.zeros((6, Nz, Nx)), axes=(1, 2)) * scale,
+        reps=2)
+    cols = pick(Nz * Nx, S["columns"])
+    Fcol = rng.standard_normal((3, Ny, len(cols))) + 1j * rng.standard_normal((3, Ny, len(cols)))
+    Cf = O.cheb_forward(Ny)
+    run("cheb_forward", Nz * Nx / len(cols), lambda: np.einsum("nj,cjk->kcn", Cf, Fcol), reps=2)
+    KX, KZ, nyq = O.mode_wavenumbers(box)
+    sel = np.argwhere((~nyq) & (KX ** 2 + KZ ** 2 > 0))
+    md = sel[pick(len(sel), S["modes"])]
+    zz, xx = md[:, 0], md[:, 1]
+    M = len(md)
+    Fh = rng.standard_normal((M, 3, Ny)) + 1j * rng.standard_normal((M, 3, Ny))
+    gw = rng.standard_normal((M, 3)) + 0j
+    uvwp = run("tau_solve", len(sel) / M,
+               lambda: O.ks_solve(box, Fh, gw, gw, 1.0, KX[zz, xx], KZ[zz, xx]), reps=2)
+    Ci = O.cheb_inverse(Ny)
+    Ccol = rng.standard_normal((len(cols), Ny)) + 1j * rng.standard_normal((len(cols), Ny))
+    spec = rng.standard_normal((len(planes), Nz, Nx)) + 1j * rng.standard_normal(
+        (len(planes), Nz, Nx))
+    # inverse transforms of 14 fields: u, v, w, p for each layer and the 6
+    # stress fields of the double layer
+    run("cheb_inverse", Nz * Nx / len(cols), lambda: np.einsum("jn,kn->jk", Ci, Ccol), reps=14)
+    run("fft_inverse", Ny / len(planes),
+        lambda: np.real(np.fft.ifft2(spec, axes=(1, 2)) * (Nx * Nz)), reps=14)
+    Dy = (2.0 / box.W) * O.cheb_deriv(Ny)
+    U, V, Wc, Pc = uvwp
+    ikx, ikz = 1j * KX[zz, xx][:, None], 1j * KZ[zz, xx][:, None]
+
+    def stress():
+        dU, dV, dW = U @ Dy.T, V @ Dy.T, Wc @ Dy.T
+        return [-Pc + 2 * ikx * U, ikx * V + dU, ikz * U + ikx * Wc, -Pc + 2 * dV,
+                ikz * V + dW, -Pc + 2 * ikz * Wc]
+    run("spectral_stress", len(sel) / M, stress)
+    it = pick(n, S["interp_targets"])
+    # 3 velocity components (single layer) + 6 stress components (double layer)
+    run("interp", n / len(it), lambda: O.interp(box, aux["F3"], susp.x[it]), reps=3)
+    measured = sum(v[0] for v in stages.values())
+    extrapolated = sum(v[0] * v[1] for v in stages.values())
+    return measured, extrapolated, stages
+
+
+def oracle_aux(susp):
+    """Inputs of the sampled oracle step that are not part of its timing:
+    alpha, r_cut, node normals and strengths (computed once)."""
+    from oracle import oracle as O
     a = O.default_alpha(susp.box)
-    rc = O.default_rcut(a)
-    _, _, _, nb = O.geometry(susp.x, susp.tri)
-    t0 = time.perf_counter()
-    O.single_layer(susp, q, quadrature=args.quadrature, targets=idx, offgrid=args.offgrid)
-    O.double_layer(susp, q, quadrature=args.quadrature, targets=idx, offgrid=args.offgrid)
-    t_sample = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    if args.quadrature == "element":
-        O.local_elem(susp.box, a, rc, 0, susp.x, susp.tri, q, targets=idx)
-        O.local_elem(susp.box, a, rc, 1, susp.x, susp.tri, q, nrm=nb, targets=idx)
-    else:
-        g = 8.0 * math.pi * np.asarray(O.geometry(susp.x, susp.tri)[2])[:, None] * q
-        O.local_point(susp.box, a, rc, 1.0, susp.x, g, susp.x[idx], want_u=True,
-                      want_sig=True)
-    t_local = time.perf_counter() - t0
-    dt = t_sample + t_local * (n / len(idx) - 1.0)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": n / dt / 1e6, "unit": "Mpts/s", "cores": cores,
-            "kind": "oracle", "seconds": dt, "measured_seconds": t_sample + t_local,
-            "sample": f"FP64 single + double layer ({args.quadrature} quadrature, "
-                      f"{args.offgrid} off-grid evaluation): both global parts in full, the "
-                      f"local part at every {stride}th node ({len(idx)} of {n}) scaled to "
-                      f"all nodes; OpenMP over targets"}
+    q = np.random.default_rng(99).standard_normal((susp.x.shape[0], 3))
+    _, _, Ab, nb = O.geometry(susp.x, susp.tri)
+    b = susp.box
+    return {"alpha": a, "rcut": O.default_rcut(a), "nb": nb, "q": q,
+            "g": 8.0 * math.pi * Ab[:, None] * q, "F3": np.zeros((3, b.Ny, b.Nz, b.Nx))}
 
 
-def solve_metrics(args, susp, dev, train_steps=3, timed_steps=2):
-    """GMRES iterations and seconds per Fredholm solve (Sec. 5) at true relative
-    residual 1e-6, per emulated time step of the workload (capsules moved
-    rigidly by 0.01 radius per step, membrane load drifting; kappa = 2/3,
-    viscosity ratio 5; b from Eq. (qa)), each step solved from the previous
-    step's density:
-      fp64   plain GMRES with the FP64 operator;
-      fp64_emulated  plain GMRES with the FP64-accurate operator whose
-             element-rule local sum runs in double-float arithmetic;
-      mixed  mixed operator with FP64 refinement;
-      mixed_learned  mixed, starting from the learned guess when its residual
-             is lower (the network trained on steps 0..train_steps-1 of the
-             same run, as a running simulation would).
-    Steps train_steps .. train_steps + timed_steps - 1 are timed."""
-    import torch
-    from paper_1109_6587_gb300 import ggem
-    from paper_1109_6587_gb300 import warmstart as WS
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
+
+def _sample_note(susp):
+    S = ORACLE_SAMPLE
+    return (f"FP64 oracle, single + double layer (element quadrature, Lagrange off-grid "
+            f"evaluation) on a seeded proportional sample of each stage's independent units: "
+            f"{S['targets']} target nodes (element-rule local sums), {S['wall_nodes']} wall "
+            f"nodes, {S['sources']} sources (spreading), {S['triangles']} triangles "
+            f"(geometry), {S['planes']} y-planes (x-z FFTs), {S['columns']} columns "
+            f"(Chebyshev transforms), {S['modes']} Fourier modes (tau solves, spectral "
+            f"stress), {S['interp_targets']} targets (interpolation); each stage's time x "
+            f"(its units / sampled units); OpenMP in the C parts")
+
+
+def _spread_updates(susp, rc, sample=2000):
+    """Grid-node updates of one spreading call (Eq. (rhog_sum)): the number of
+    (source, grid node) pairs with |node - x*| < r_cut, minimum image in x and
+    z, Chebyshev nodes in y; counted on a seeded sample of sources and scaled."""
+    from oracle import oracle as O
+    b = susp.box
+    yg = O.grid_y(b)
     n = susp.x.shape[0]
-    mk = lambda prec: ggem.Plan.for_box(susp.box, precision=prec, quadrature=args.quadrature,
-                                        max_points=n, max_tris=susp.tri.shape[0])
-    Pm = mk("mixed")
+    idx = np.random.default_rng(5).choice(n, min(sample, n), replace=False)
+    dx, dz = b.Lx / b.Nx, b.Lz / b.Nz
+    total = 0
+    for x, y, z in susp.x[idx]:
+        ix = np.arange(int(np.floor((x - rc) / dx)), int(np.ceil((x + rc) / dx)) + 1)
+        iz = np.arange(int(np.floor((z - rc) / dz)), int(np.ceil((z + rc) / dz)) + 1)
+        ex = (ix * dx - x) ** 2
+        ez = (iz * dz - z) ** 2
+        ey = (yg - y) ** 2
+        d2 = ex[:, None, None] + ez[None, :, None] + ey[None, None, :]
+        total += int((d2 < rc * rc).sum())
+    return total * n / len(idx)
+
+
+def _stencil(b, yg, rc, x, y, z):
+    """Flat indices (j, k, i) of the grid nodes within r_cut of (x, y, z)."""
+    dx, dz = b.Lx / b.Nx, b.Lz / b.Nz
+    ix = np.arange(int(np.floor((x - rc) / dx)), int(np.ceil((x + rc) / dx)) + 1)
+    iz = np.arange(int(np.floor((z - rc) / dz)), int(np.ceil((z + rc) / dz)) + 1)
+    d2 = ((ix * dx - x) ** 2)[None, None, :] + ((iz * dz - z) ** 2)[None, :, None] + \
+        ((yg - y) ** 2)[:, None, None]
+    j, k, i = np.nonzero(d2 < rc * rc)
+    return (j * b.Nz + (iz[k] % b.Nz)) * b.Nx + (ix[i] % b.Nx)
+
+
+def _spread_pair_reductions(susp, rc, sample=1000):
+    """Vector reductions the paired spreading issues per call: sources in
+    cell order (cells of r_cut/3, as the mesh nodes are sorted), taken two
+    at a time, one reduction per node of the union of the two stencils;
+    counted on a seeded sample of pairs and scaled."""
+    from oracle import oracle as O
+    b = susp.box
+    yg = O.grid_y(b)
+    x = susp.x.copy()
+    x[:, 0] %= b.Lx
+    x[:, 2] %= b.Lz
+    h = rc / 3.0
+    ncx, ncy, ncz = int(b.Lx // h), max(1, int(b.W // h)), int(b.Lz // h)
+    cx = np.minimum((x[:, 0] / (b.Lx / ncx)).astype(int), ncx - 1)
+    cy = np.clip(((x[:, 1] - b.y0) / (b.W / ncy)).astype(int), 0, ncy - 1)
+    cz = np.minimum((x[:, 2] / (b.Lz / ncz)).astype(int), ncz - 1)
+    order = np.lexsort((np.arange(len(x)), cx, cy, cz))
+    npairs = len(x) // 2
+    pick = np.random.default_rng(6).choice(npairs, min(sample, npairs), replace=False)
+    tot = 0
+    for p in pick:
+        a, c = order[2 * p], order[2 * p + 1]
+        tot += len(np.union1d(_stencil(b, yg, rc, *x[a]), _stencil(b, yg, rc, *x[c])))
+    return tot * npairs / len(pick)
+
+
+def spread_roofline(res, args):
+    """The spreading stage against the measured throughput of float4 vector
+    reductions into L2 (ggem_probe_l2_reduction): algorithmic node updates per
+    call (one vector reduction each) / the stage's time per call."""
+    from paper_1109_6587_gb300 import ggem
+    stages = res["stages"]
+    if "spread" not in stages:
+        return None
+    tot, calls = stages["spread"]
+    avg_s = tot / calls * 1e-3
+    _, rc = res["P"].info()
+    upd = _spread_updates(res["susp"], rc)
+    red = _spread_pair_reductions(res["susp"], rc) if args.precision == "mixed" else upd
+    _, peak = ggem.probe_l2_reduction()
+    ach = red / avg_s
+    return {"kernel": "spread", "bound": "l2_reduction", "achieved": ach, "peak": peak,
+            "unit": "vector reductions/s", "frac": ach / peak,
+            "reductions_per_call": red, "node_updates_per_call": upd,
+            "node_updates_per_s": upd / avg_s, "call_ms": avg_s * 1e3,
+            "peak_source": "measured: ggem_probe_l2_reduction (float4 atomic adds, 32 MB "
+                           "L2-resident buffer, warps on 32 consecutive vectors)"}
+
+
+def cpu_baseline(susp, args):
+    """The FP64 oracle as it stands on the host cores: one sampled step
+    (oracle_sample_step); value = points / extrapolated full-step time."""
+    aux = oracle_aux(susp)
+    measured, full, stages = oracle_sample_step(susp, args, 1, aux)
+    n = susp.x.shape[0]
+    return {"value": n / full / 1e6, "unit": "Mpts/s", "cores": _cores(), "kind": "oracle",
+            "sample": _sample_note(susp), "measured_seconds": measured,
+            "extrapolated_seconds": full, "extrapolation_factor": full / measured,
+            "stages": {k: {"sample_s": v[0], "scale": v[1]} for k, v in stages.items()}}
+
+
+def _mk_plan(susp, prec, quadrature):
+    from paper_1109_6587_gb300 import ggem
+    return ggem.Plan.for_box(susp.box, precision=prec, quadrature=quadrature,
+                             max_points=susp.x.shape[0], max_tris=susp.tri.shape[0])
+
+
+def train_warm_start(args, model_plan, epochs=20):
+    """The learned warm start trained on generated suspensions (none of them
+    a timed workload): workloads.training_suspensions -- 48 to 382
+    capsules, volume fractions 0.05 to 0.3, viscosity ratios 0.2, 1, 5 --
+    each a series of 3 emulated steps solved to 1e-6 (the mixed solver),
+    samples from every guess the solver meets; the model lives on
+    model_plan."""
+    import torch
+    from paper_1109_6587_gb300 import warmstart as WS
+    from paper_1109_6587_gb300 import workloads as W
     t0 = time.perf_counter()
-    recs = WS.solve_series(Pm, susp, train_steps, seed=500, collect=True)
-    F = np.concatenate([f for r in recs for f, _ in r["samples"]])
-    T = np.concatenate([t for r in recs for _, t in r["samples"]])
+    pairs = W.training_suspensions(seed=1)
     t1 = time.perf_counter()
-    loss = WS.train(Pm, F, T, seed=1, epochs=20, batch=2048, lr=1e-3)
-    torch.cuda.synchronize()
+    F, T = WS.generated_training_set(lambda s: _mk_plan(s, "mixed", args.quadrature), pairs,
+                                     n_steps=3, seed=1000)
     t2 = time.perf_counter()
-    out = {"tol": 1e-6, "kappa": 2.0 / 3.0, "rhs": "Eq. (qa), synthetic membrane load + shear",
-           "guess": "previous step's density", "restart": 30, "quadrature": args.quadrature,
-           "steps_timed": timed_steps,
-           "training": {"samples": int(F.shape[0]), "data_s": t1 - t0, "train_s": t2 - t1,
-                        "loss": loss, "epochs": 20}}
-    P64 = mk("fp64")
-    Pem = mk("fp64_emulated")
-    variants = (("fp64", P64, 0), ("fp64_emulated", Pem, 0), ("mixed", Pm, 0),
-                ("mixed_learned", Pm, 1))
-    for name, P, use in variants:
-        total = train_steps + timed_steps
-        # the series up to the last training step, untimed (warm state), then timed steps
-        q_prev = None
-        tri = torch.as_tensor(susp.tri, device=dev)
+    loss = WS.train(model_plan, F, T, seed=1, epochs=epochs, batch=2048, lr=1e-3)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    return {"suspensions": [{"capsules": int(len(s.centres)), "lambda": lam,
+                             "box": [s.box.Lx, s.box.W, s.box.Lz]} for s, lam in pairs],
+            "samples": int(F.shape[0]), "epochs": epochs, "loss": loss,
+            "generate_s": t1 - t0, "data_s": t2 - t1, "train_s": t3 - t2}
+
+
+def solve_metrics(args, dev, model_plan_box=None, warm_steps=2, timed_steps=2):
+    """GMRES iterations and seconds per Fredholm solve (Sec. 5) at true
+    relative residual 1e-6 on the 1000-capsule workload (642,000 nodes,
+    80 x [-10,10] x 80, grid 256 x 97 x 256, viscosity ratio 5: kappa = 2/3,
+    b from Eq. (qa)), per emulated time step (capsules moved rigidly by 0.01
+    radius, membrane load drifting), each solve from the previous step's
+    density.  Steps 0..warm_steps-1 run once with the mixed solver (untimed,
+    the warm state every variant starts from); then per variant:
+      fp64            plain GMRES, FP64 operator (1 timed step);
+      fp64_emulated   plain GMRES, FP64-accurate operator whose element-rule
+                      local sum runs in double-float arithmetic (1 step);
+      mixed           mixed operator, FP64 refinement (timed_steps steps);
+      mixed_precond   the same with the per-particle block preconditioner;
+      mixed_learned   mixed, starting from the learned guess when its
+                      residual is lower (model trained on generated
+                      suspensions, train_warm_start);
+      mixed_learned_precond  both."""
+    import torch
+    from paper_1109_6587_gb300 import workloads as W
+    susp = W.capsules_1000(seed=0)
+    n = susp.x.shape[0]
+    tri = torch.as_tensor(susp.tri, device=dev)
+    Pm = _mk_plan(susp, "mixed", args.quadrature)
+    training = train_warm_start(args, Pm)
+    V, F = W.icosphere(3)
+
+    def prepare(P, t):
+        s = W_rigid(susp, t)
+        kappa, b = W_rhs(s, t)
+        P.mesh_set(torch.as_tensor(s.x, device=dev), tri)
+        P.mesh_particles(s.particle, len(s.centres))
+        return torch.as_tensor(kappa, device=dev), torch.as_tensor(b, device=dev)
+
+    q = None
+    for t in range(warm_steps):
+        kd, bd = prepare(Pm, t)
+        q, _, _, _ = Pm.bie_solve(kd, bd, q=bd.clone() if q is None else q.clone(), tol=1e-6)
+    q_warm = q.clone()
+    out = {"workload": "1000 spherical capsules x 642 nodes (642,000 points), slit 80 x "
+                       "[-10,10] x 80, grid 256 x 97 x 256", "tol": 1e-6, "kappa": 2.0 / 3.0,
+           "rhs": "Eq. (qa), synthetic membrane load + shear", "guess": "previous step's density",
+           "restart": 30, "quadrature": args.quadrature, "warm_steps": warm_steps,
+           "training": training}
+    P64 = _mk_plan(susp, "fp64", args.quadrature)
+    Pem = _mk_plan(susp, "fp64_emulated", args.quadrature)
+    t0 = time.perf_counter()
+    Pm.mesh_set(torch.as_tensor(susp.x, device=dev), tri)
+    Pm.mesh_particles(susp.particle, len(susp.centres))
+    Pm.precond_set(V, F, 2.0 / 3.0)
+    out["precond_setup_s"] = time.perf_counter() - t0
+    variants = (("fp64", P64, 0, False, 1), ("fp64_emulated", Pem, 0, False, 1),
+                ("mixed", Pm, 0, False, timed_steps), ("mixed_precond", Pm, 0, True, timed_steps),
+                ("mixed_learned", Pm, 1, False, timed_steps),
+                ("mixed_learned_precond", Pm, 1, True, timed_steps))
+    for name, P, use, pc, steps in variants:
+        if P is Pm:
+            P.precond_enable(pc)
+        q = q_warm.clone()
         times, its, rrs, used = [], [], [], []
-        for t in range(total):
-            s = W_rigid(susp, t)
-            kappa, b = W_rhs(s, t)
-            P.mesh_set(torch.as_tensor(s.x, device=dev), tri)
-            P.mesh_particles(s.particle, len(s.centres))
-            kd = torch.as_tensor(kappa, device=dev)
-            bd = torch.as_tensor(b, device=dev)
-            q0 = bd.clone() if q_prev is None else q_prev.clone()
-            timed = t >= train_steps
-            if name.startswith("fp64") and not timed and t < train_steps - 1:
-                q_prev = None          # FP64 plain: only the last untimed step is needed
-                continue
+        for t in range(warm_steps, warm_steps + steps):
+            kd, bd = prepare(P, t)
             torch.cuda.synchronize()
             a = time.perf_counter()
-            q, it, rr, st = P.bie_solve(kd, bd, q=q0, tol=1e-6, use_mlp=use if timed else 0)
+            q, it, rr, st = P.bie_solve(kd, bd, q=q, tol=1e-6, use_mlp=use)
             torch.cuda.synchronize()
-            if timed:
-                times.append(time.perf_counter() - a)
-                its.append(it)
-                rrs.append(rr)
-                used.append(P.solve_guess()[0])
-            q_prev = q
+            times.append(time.perf_counter() - a)
+            its.append(it)
+            rrs.append(rr)
+            used.append(P.solve_guess()[0])
         cyc, m64, mmix = P.solve_stats()
-        out[name] = {"iters": float(np.mean(its)), "s_per_solve": float(np.mean(times)),
+        out[name] = {"steps_timed": steps, "iters": float(np.mean(its)),
+                     "s_per_solve": float(np.mean(times)),
                      "true_relres_max": float(np.max(rrs)), "learned_guess_used": used,
                      "last_solve_matvec_fp64": m64, "last_solve_matvec_mixed": mmix}
         P.check()
-    Pm.close()
-    P64.close()
-    Pem.close()
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_solve"] / out["mixed"]["s_per_solve"]
-    out["speedup_learned_vs_fp64"] = (out["fp64"]["s_per_solve"] /
-                                      out["mixed_learned"]["s_per_solve"])
+    out["_model"] = Pm.mlp_save()
+    for P in (Pm, P64, Pem):
+        P.close()
+    for k in ("mixed", "mixed_precond", "mixed_learned", "mixed_learned_precond"):
+        out[f"speedup_{k}_vs_fp64"] = out["fp64"]["s_per_solve"] / out[k]["s_per_solve"]
+        out[f"speedup_{k}_vs_fp64_emulated"] = (out["fp64_emulated"]["s_per_solve"] /
+                                               out[k]["s_per_solve"])
     return out
 
 
-def dynamics_metrics(args, susp, dev, warm=1, timed=3):
+def dynamics_metrics(args, susp, dev, timed=2, model=None):
     """Capsule time steps of the workload (Sec. 5, 7.1): simple shear of rate
-    1, viscosity ratio 5, Ca = 0.3, membranes stress-free in the initial
-    spherical shape.  One step: the dt rule from the smallest node
-    separation, the midpoint step (per stage: traction jump, right side of
-    Eq. (qa), Fredholm solve to 1e-6 from the previous density, single
-    layer), the volume correction and the minimum-gap correction.  `warm`
-    untimed steps, then `timed` timed ones; mixed precision."""
+    1, viscosity ratio 5, Ca = 0.3, membranes stress-free in their initial
+    shape.  One step: the dt rule from the smallest node separation, the
+    midpoint step (per stage: traction jump, right side of Eq. (qa), Fredholm
+    solve to 1e-6 from the previous density, single layer), the volume
+    correction and the minimum-gap correction.  One untimed mixed step from
+    the initial state, checkpointed; every variant resumes that checkpoint on
+    a plan of its own and times its steps from the same state:
+      mixed (timed steps), mixed_precond (the per-particle block
+      preconditioner of the workload's own capsule shape), mixed_learned_precond
+      (plus the learned warm start, `model`), fp64_emulated (1 step: plain
+      GMRES with the FP64-accurate operator)."""
+    import tempfile
+
     import torch
     from paper_1109_6587_gb300 import dynamics as D
-    from paper_1109_6587_gb300 import ggem
+    from paper_1109_6587_gb300 import workloads as W
 
     n = susp.x.shape[0]
-    P = ggem.Plan.for_box(susp.box, precision="mixed", quadrature=args.quadrature,
-                          max_points=n, max_tris=susp.tri.shape[0])
+    P = _mk_plan(susp, "mixed", args.quadrature)
     P.mesh_set(torch.as_tensor(susp.x, device=dev), torch.as_tensor(susp.tri, device=dev))
-    S = D.Suspension(P, susp.particle, len(susp.centres), lam=np.full(len(susp.centres), 5.0),
-                     ca=0.3, flow="shear", strength=1.0)
-    for _ in range(warm):
-        S.step()
-    recs = [S.step() for _ in range(timed)]
-    P.check()
-    out = {"flow": "simple shear, rate 1", "lambda": 5.0, "Ca": 0.3, "tol": 1e-6,
-           "steps_timed": timed, "s_per_step": float(np.mean([r["seconds"] for r in recs])),
-           "gmres_iters_per_step": float(np.mean([r["iters"] for r in recs])),
-           "dt": float(np.mean([r["dt"] for r in recs])),
-           "volume_passes": int(sum(r["volume_passes"] for r in recs)),
-           "overlap_moves": int(sum(r["overlap_moves"] for r in recs)),
-           "taylor_D_mean": float(S.deformation().mean()), "strain": S.t}
+    np_ = len(susp.centres)
+    S = D.Suspension(P, susp.particle, np_, lam=np.full(np_, 5.0), ca=0.3, flow="shear",
+                     strength=1.0, tri=susp.tri)
+    warm = S.step()
+    ckpt = os.path.join(tempfile.mkdtemp(), "dyn.npz")
+    S.save(ckpt)
     P.close()
+    rbc = susp.box.Lx == 150.0
+    V, F = W.rbc_mesh(3) if rbc else W.icosphere(3)
+    out = {"flow": "simple shear, rate 1", "lambda": 5.0, "Ca": 0.3, "tol": 1e-6,
+           "warm_step": {"iters": warm["iters"], "seconds": warm["seconds"]},
+           "reference_capsule": "biconcave (Evans-Fung), 642 nodes" if rbc else
+           "sphere, 642 nodes"}
+    variants = (("mixed", "mixed", False, 0, timed), ("mixed_precond", "mixed", True, 0, timed),
+                ("mixed_learned_precond", "mixed", True, 1, timed),
+                ("fp64_emulated", "fp64_emulated", False, 0, 1))
+    if args.fp64_step:
+        variants += (("fp64", "fp64", False, 0, 1),)
+    for name, prec, pc, use, steps in variants:
+        if use and model is None:
+            continue
+        P = _mk_plan(susp, prec, args.quadrature)
+        S = D.Suspension.resume(P, ckpt)
+        if use:
+            P.mlp_load(model)
+        rec = {}
+        if pc:
+            t0 = time.perf_counter()
+            P.precond_set(V, F, 2.0 / 3.0)
+            rec["precond_setup_s"] = time.perf_counter() - t0
+        recs = [S.step(use_mlp=use) for _ in range(steps)]
+        P.check()
+        rec.update({"steps_timed": steps,
+                    "s_per_step": float(np.mean([r["seconds"] for r in recs])),
+                    "gmres_iters_per_step": float(np.mean([r["iters"] for r in recs])),
+                    "dt": float(np.mean([r["dt"] for r in recs])),
+                    "volume_passes": int(sum(r["volume_passes"] for r in recs)),
+                    "overlap_moves": int(sum(r["overlap_moves"] for r in recs))})
+        out[name] = rec
+        P.close()
+    for k in ("mixed", "mixed_precond", "mixed_learned_precond"):
+        for base in ("fp64_emulated", "fp64"):
+            if k in out and base in out:
+                out[f"speedup_{k}_vs_{base}"] = out[base]["s_per_step"] / out[k]["s_per_step"]
     return out
 
 
@@ -583,21 +858,33 @@ def main():
         if rank != 0:
             return
         susp = _workload(args)
-        times = []
-        for _ in range(args.warmup):
-            pass       # the oracle has no warm-up state
-        cb = None
-        for _ in range(max(1, min(args.steps, 3))):
-            cb = cpu_baseline(susp, args)
-            times.append(cb["seconds"])
-        ms = float(np.median(times)) * 1e3
-        val = susp.x.shape[0] / (ms * 1e-3) / 1e6
-        cb["value"] = val
+        aux = oracle_aux(susp)
+        for i in range(args.warmup):
+            oracle_sample_step(susp, args, 1000 + i, aux)
+        meas, full, last = [], [], None
+        for i in range(args.steps):
+            m_s, f_s, last = oracle_sample_step(susp, args, i, aux)
+            meas.append(m_s)
+            full.append(f_s)
+        n = susp.x.shape[0]
+        t_full = float(np.mean(full))
+        val = n / t_full / 1e6
+        ms = float(np.mean(meas)) * 1e3
+        cfg = _config(susp, args)
+        cfg["precision"] = "fp64"
+        cb = {"value": val, "unit": "Mpts/s", "cores": _cores(), "kind": "oracle",
+              "sample": _sample_note(susp), "measured_seconds_per_step": ms * 1e-3,
+              "extrapolated_seconds_per_step": t_full,
+              "extrapolation_factor": t_full / (ms * 1e-3),
+              "stages_last_step": {k: {"sample_s": v[0], "scale": v[1]} for k, v in last.items()}}
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpts/s",
-                "n_gpus": args.gpus, "steps": len(times), "warmup": 0, "ms_per_step": ms,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms,
+                "ms_per_step_note": "measured wall time of one sampled oracle step; value = "
+                                    "points / (the step's stage times x their scale "
+                                    "factors), i.e. extrapolated to the full workload",
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": _config(susp, args),
-                "cpu_baseline": cb,
+                "dtype": "f64", "data": "synthetic", "config": cfg, "cpu_baseline": cb,
                 "e2e": {"value": val, "unit": "Mpts/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -618,12 +905,16 @@ def main():
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "stages_ms": {k: v[0] / v[1] for k, v in res["stages"].items()}}
     line["roofline"] = roofline(res, args)
+    line["roofline_spread"] = spread_roofline(res, args)
     if not args.no_solve:
         import torch
-        line["solve"] = solve_metrics(args, res["susp"], torch.device("cuda"))
-        line["dynamics"] = dynamics_metrics(args, res["susp"], torch.device("cuda"))
-        line["offgrid_other"] = offgrid_metrics(args, res["susp"], torch.device("cuda"))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "capsules100":
+        dev = torch.device("cuda")
+        res["P"].close()
+        line["offgrid_other"] = offgrid_metrics(args, res["susp"], dev)
+        line["solve"] = solve_metrics(args, dev)
+        model = line["solve"].pop("_model", None)
+        line["dynamics"] = dynamics_metrics(args, res["susp"], dev, model=model)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(res["susp"], args)
     if world > 1:
         import torch.distributed as dist

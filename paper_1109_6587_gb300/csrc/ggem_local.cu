@@ -288,6 +288,7 @@ __device__ __forceinline__ void pair_terms(const LocalConst<T>& k, T dx, T dy, T
 // explicit FMA.
 struct PairAcc2 {
     f2 ux = {0ull}, uy = {0ull}, uz = {0ull};
+    f2 sn = {0ull};     // double layer: sum of E x.g (times the target normal at the end)
 };
 
 __device__ __forceinline__ float rsqrt_ftz(float x) {
@@ -326,17 +327,19 @@ __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f
     if (MODE & OUT_DBL) {
         // D = -6 ec/r^5 - c2 ex/r^4 - c3 ex/r^2 = ir2 (ir2 (-6 ec ir - c2 ex) - c3 ex),
         // E = c4 ex; the update D xg xn d + E (d gn + g xn + n xg) regrouped as
-        // d (D xg xn + E gn) + g (E xn) + n (E xg)
+        // d (D xg xn + E gn) + g (E xn) + n (E xg), the last term's scalar E xg
+        // summed over the pairs and multiplied by the (fixed) target normal once
         const f2 ir2 = ir * ir;
         const f2 t = fma2(f2_splat(-6.0f), ec * ir, f2_splat(-k.c2) * ex);
         const f2 D = ir2 * fma2(ir2, t, f2_splat(-k.c3) * ex);
         const f2 E = f2_splat(k.c4) * ex;
         const f2 xn = fma2(dz, nz, fma2(dy, ny, dx * nx));
         const f2 gn = fma2(gz, nz, fma2(gy, ny, gx * nx));
-        const f2 cd = fma2(D * xg, xn, E * gn), cg = E * xn, cn = E * xg;
-        a.ux = fma2(dx, cd, fma2(gx, cg, fma2(nx, cn, a.ux)));
-        a.uy = fma2(dy, cd, fma2(gy, cg, fma2(ny, cn, a.uy)));
-        a.uz = fma2(dz, cd, fma2(gz, cg, fma2(nz, cn, a.uz)));
+        const f2 cd = fma2(D * xg, xn, E * gn), cg = E * xn;
+        a.sn = fma2(E, xg, a.sn);
+        a.ux = fma2(dx, cd, fma2(gx, cg, a.ux));
+        a.uy = fma2(dy, cd, fma2(gy, cg, a.uy));
+        a.uz = fma2(dz, cd, fma2(gz, cg, a.uz));
     }
 }
 
@@ -639,6 +642,12 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
         }
     }
     float ux = f2_sum(acc.ux), uy = f2_sum(acc.uy), uz = f2_sum(acc.uz);
+    if (MODE & OUT_DBL) {
+        const float sn = f2_sum(acc.sn);
+        ux = fmaf(nx, sn, ux);
+        uy = fmaf(ny, sn, uy);
+        uz = fmaf(nz, sn, uz);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ux += __shfl_xor_sync(0xffffffffu, ux, o);
