@@ -180,8 +180,7 @@ FLOPS_PAIR_DOUBLE = 87
 # summaries are kept with the profiles), per (workload, precision, quadrature);
 # none for other configurations
 LOCAL_TRAFFIC = {
-    ("rbc4000", "mixed", "element"): (3904399104 + 41290240 + 4067564288 + 39082752) / 2,
-    ("capsules100", "mixed", "element"): (93218304 + 3518208 + 94636288 + 4180736) / 2,
+    ("rbc4000", "mixed", "element"): (3816876032 + 41026560 + 4464229888 + 95442944) / 2,
 }
 
 SAMPLE_ABOVE = 100_000      # larger workloads count pairs on a sample of targets

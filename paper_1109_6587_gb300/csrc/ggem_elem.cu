@@ -48,23 +48,39 @@ __global__ void k_qp_gen(int m, const double* __restrict__ x, const int* __restr
     qw[e] = w;
 }
 
-// strengths of the sorted quadrature points: g = scale * sum_v (phi_v w) q_v
+// strengths of the sorted quadrature points: g = scale * sum_v (phi_v w) q_v,
+// from the vertex indices and weights already in point order (qv, qw); into
+// interleaved v4 (g) or, for the FP32 element rule, straight into the
+// structure-of-arrays planes x, y, z of stride ld (soa)
 template <typename T>
-__global__ void k_qp_strength(int n, const int* __restrict__ perm, const int4* __restrict__ qv,
-                              const v4_t<T>* __restrict__ qw, const double* __restrict__ q,
-                              double scale, v4_t<T>* __restrict__ g) {
+__global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>* __restrict__ qw,
+                              const double* __restrict__ q, double scale, v4_t<T>* __restrict__ g,
+                              T* __restrict__ soa, size_t ld) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int e = perm[s];
-    int4 v = qv[e];
-    v4_t<T> w = qw[e];
+    int4 v = qv[s];
+    v4_t<T> w = qw[s];
     double a = scale * (double)w.x, b = scale * (double)w.y, c = scale * (double)w.z;
-    v4_t<T> r;
-    r.x = (T)(a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z]);
-    r.y = (T)(a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1]);
-    r.z = (T)(a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2]);
-    r.w = (T)0;
-    g[s] = r;
+    T rx = (T)(a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z]);
+    T ry = (T)(a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1]);
+    T rz = (T)(a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2]);
+    if (soa) {
+        soa[s] = rx;
+        soa[ld + s] = ry;
+        soa[2 * ld + s] = rz;
+    } else {
+        v4_t<T> r;
+        r.x = rx; r.y = ry; r.z = rz; r.w = (T)0;
+        g[s] = r;
+    }
+}
+
+// out[s] = in[perm[s]] (the quadrature weights into point order)
+template <typename T>
+__global__ void k_gather_v4(int n, const int* __restrict__ perm, const v4_t<T>* __restrict__ in,
+                            v4_t<T>* __restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) out[s] = in[perm[s]];
 }
 
 // node -> triangle adjacency (CSR)
@@ -231,10 +247,17 @@ cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri
 }
 
 template <typename T>
-cudaError_t qp_strengths(int nq, const int* perm, const int4* qv, const v4_t<T>* qw,
-                         const double* q, double scale, v4_t<T>* g, cudaStream_t st) {
+cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    k_gather_v4<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, perm, qw, tmp);
+    return cudaMemcpyAsync(qw, tmp, (size_t)nq * sizeof(v4_t<T>), cudaMemcpyDeviceToDevice, st);
+}
+
+template <typename T>
+cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
+                         double scale, v4_t<T>* g, T* soa, size_t ld, cudaStream_t st) {
     if (nq > 0)
-        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, perm, qv, qw, q, scale, g);
+        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, q, scale, g, soa, ld);
     return cudaGetLastError();
 }
 
@@ -254,8 +277,9 @@ cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x,
     template cudaError_t elem_setup<T>(int, const double*, const int*, const double*,          \
                                        const QuadRule&, double*, int4*, v4_t<T>*, int, int*,    \
                                        int*, int*, int*, cudaStream_t);                         \
-    template cudaError_t qp_strengths<T>(int, const int*, const int4*, const v4_t<T>*,         \
-                                         const double*, double, v4_t<T>*, cudaStream_t);       \
+    template cudaError_t qp_sort_weights<T>(int, const int*, v4_t<T>*, v4_t<T>*, cudaStream_t); \
+    template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, const double*,      \
+                                         double, v4_t<T>*, T*, size_t, cudaStream_t);          \
     template cudaError_t elem_correct<T>(int, int, const GridGeom&, const double*, const int*, \
                                          const double*, const double*, const int*, const int*,  \
                                          const double*, const QuadRule&, T*, int, cudaStream_t);

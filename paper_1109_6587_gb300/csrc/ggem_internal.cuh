@@ -110,7 +110,6 @@ struct ggem_plan {
     void* d_gridA = nullptr;           // max(9,3)*Ny*Nz*Nx T
     void* d_gridB = nullptr;
     void* d_wall = nullptr;            // [2][3][Nz][Nx] T
-    void* d_ksw = nullptr;             // tau-solve scratch (see ks_modes)
     double* d_thom = nullptr;          // [4][Ny][nmodes] Thomas factors
     double* d_isq = nullptr;           // [2][nmodes]
     size_t grid_elems = 0;
@@ -163,7 +162,7 @@ struct ggem_plan {
     int4* d_qv = nullptr;              // [cap_qp] triangle vertices
     int4* d_qv_sorted = nullptr;       // [cap_qp] the same, in sorted point order
     double near_edge = 0.0;            // longest triangle edge of the mesh
-    void* d_qw = nullptr;              // [cap_qp] v4 T: phi_v * weight
+    void* d_qw = nullptr;              // [cap_qp] v4 T: phi_v * weight (point order once sorted)
     int* d_qp_cell = nullptr;          // sorted points: cell / perm / offsets / start
     int* d_qp_perm = nullptr;
     int* d_qp_start = nullptr;
@@ -326,6 +325,10 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
                            const double* nrm_tgt, int layer, T* out, int out_stride,
                            cudaStream_t st, const void* aux_pos = nullptr,
                            const void* aux_g = nullptr, size_t aux_ld = 0);
+// FP32 element rule: sub-sort the sorted points within each cell (4 x 4 x 4
+// sub-cells in Morton order; tmp_* of n entries as scratch)
+cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start, float4* pos,
+                         int* perm, float4* tmp_pos, int* tmp_perm, cudaStream_t st);
 // structure-of-arrays planes (x, y, z; stride ld) of n float4 values
 cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st);
 // float-pair copy of n double4 (x, y, z, w) values: out[2 i] = hi, out[2 i + 1] = lo
@@ -341,10 +344,14 @@ template <typename T>
 cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri_area,
                        const QuadRule& rule, double* xq, int4* qv, v4_t<T>* qw, int nnodes,
                        int* adj_cnt, int* adj_start, int* adj_cur, int* adj, cudaStream_t st);
-// sorted point strengths g = scale sum_v (phi_v w) q_v
+// quadrature weights qw into point order, qw[s] <- qw[perm[s]] (tmp: nq v4 T)
 template <typename T>
-cudaError_t qp_strengths(int nq, const int* perm, const int4* qv, const v4_t<T>* qw,
-                         const double* q, double scale, v4_t<T>* g, cudaStream_t st);
+cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, cudaStream_t st);
+// sorted point strengths g = scale sum_v (phi_v w) q_v from the sorted vertex
+// indices and weights: into g (v4), or into the planes soa[0, ld, 2 ld] if soa
+template <typename T>
+cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
+                         double scale, v4_t<T>* g, T* soa, size_t ld, cudaStream_t st);
 // polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double)
 template <typename T>
 cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x, const int* tri,
@@ -388,7 +395,7 @@ cudaError_t cheb_tc_prepare(int Ny, const float* M, void* prep, cudaStream_t st)
 template <typename T>
 cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
                      const double* minv, const double* coef, const double* thom,
-                     const double* isq, void* scratch, int out_sel, T* ocoef, cudaStream_t st);
+                     const double* isq, int out_sel, T* ocoef, cudaStream_t st);
 
 // mode 0: velocity, out = local + interp - self_coef * wself * qself
 // mode 1: stress (6), out = local + interp

@@ -24,14 +24,21 @@
 // between its wall values, D p = -f_y with zero mean over y.
 // The Nyquist mode in z is zero.
 //
-// GPU mapping: four threads per mode -- real / imaginary part x even / odd
-// coefficient index.  The operator is real, so real and imaginary parts only
-// meet through the i k_x, i k_z factors, and the two parities only through D;
-// both exchanges go through the mode's scratch columns after __syncwarp.  A
-// warp holds 8 consecutive modes, so every scratch access is a coalesced run
-// of 8 doubles.  The Thomas factors (Y_n, 1/d_n, Q_n) depend on k^2 only; they
-// are computed once per mode and shared by the pressure and velocity solves,
-// and the mode-independent recurrence coefficients come from a table.
+// GPU mapping: one warp per mode, lane = (real / imaginary part r, parity p,
+// chunk j).  The operator is real, so the parts only meet through the i k_x,
+// i k_z factors, and the parities only through D; the Ny/2 coefficients of one
+// parity are split into 8 contiguous chunks.  Each sequential recurrence of
+// the solve (the downward and upward Thomas sweeps, the derivative's suffix
+// sum) is a chunk-local sweep, a three-step shuffle scan of the chunks'
+// affine maps over the 8 lanes of the (part, parity), and a second local
+// sweep from the exact chunk input.  The rows of one mode live in the warp's
+// shared memory (11 KB for Ny = 129 in FP32), so a block of 4 modes needs no
+// global scratch and several blocks share an SM.  The Thomas factors
+// (Y_n, 1/d_n, B_n, Q_n) depend on k^2 only; they come from a plan-time
+// table, and the products of each chunk's factors that the scans use are
+// formed once per mode and serve all four solves.
+#include <type_traits>
+
 #include "ggem_internal.cuh"
 
 namespace ggem {
@@ -197,76 +204,74 @@ template <typename T> struct KSArgs {
     const double* coef;    // [3][Ny]
     const double* thom;    // [4][Ny][nmodes] Y, id, B, Q
     const double* isq;     // [2][nmodes]
-    T* SA;                 // aux scratch [5][2][Ny][nmodes] (T)
-    double* SX;            // recurrence scratch [3][2][Ny][nmodes] (FP64)
     int out_sel;           // bit0: u, v, w; bit1: stress
     T* o;                  // [Ny][nout][nmodes] complex T
 };
 
 enum { AU = 0, AV = 1, AW = 2, AP = 3, AT = 4 };
+constexpr int KS_WARPS = 4;     // modes (warps) per block
 
-// Thread (mode, part r, parity p).  FP64 is used where App. C's boundary-value
-// solve needs it -- the tau recurrences and the influence matrix; right-hand
-// sides, derivatives and combinations run in T.
-// SMEM: the mode scratch (SA, SX) lives in the block's shared memory, one warp
-// per block and its 8 modes fastest ([row][8]), so the sequential recurrences
-// wait on shared-memory latency instead of L2; otherwise it is the global
-// scratch ([row][nmodes]).
+// Shared memory: the coefficient table [3][Ny] (as T) per block, then per
+// warp the series rows SA [5 series][2 parts][ks_row(Ny)] (T) and the
+// recurrence rows SX [3 series][2 parts][Ny] (FP64).  The SA row length is
+// padded to 16 mod 32 elements so that the two parts fall in different banks.
+__host__ __device__ constexpr int ks_row(int Ny) { return Ny + ((16 - Ny % 32) + 32) % 32; }
 template <typename T>
-__host__ __device__ constexpr size_t ks_coef_doubles(int Ny) {
-    return ((size_t)3 * Ny * sizeof(T) + 7) / 8;
+__host__ __device__ constexpr size_t ks_coef_bytes(int Ny) {
+    return ((size_t)3 * Ny * sizeof(T) + 15) & ~(size_t)15;
+}
+template <typename T>
+__host__ __device__ constexpr size_t ks_warp_bytes(int Ny) {
+    return ((((size_t)10 * ks_row(Ny) * sizeof(T)) + 15) & ~(size_t)15) + (size_t)6 * Ny * 8;
 }
 template <typename T>
 __host__ __device__ constexpr size_t ks_smem_bytes(int Ny) {
-    return (ks_coef_doubles<T>(Ny) + (((size_t)5 * 2 * Ny * 8 * sizeof(T) + 7) / 8) +
-            (size_t)3 * 2 * Ny * 8) * sizeof(double);
+    return ks_coef_bytes<T>(Ny) + KS_WARPS * ks_warp_bytes<T>(Ny);
 }
 
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
+// Warp (mode m); lane (part r, parity p, chunk j).  FP64 is used where
+// App. C's boundary-value solve needs it -- the tau recurrences and the
+// influence matrix; right-hand sides, derivatives and combinations run in T.
+// Every __syncwarp and shuffle is reached by all 32 lanes: the branches on
+// the mode (Nyquist, k = 0) are warp-uniform.
+template <typename T>
+__global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
     const GridGeom& geo = a.geo;
     const int nkx = geo.nkx, nm = geo.Nz * nkx;
-    const int Ny = geo.Ny, N = Ny - 1;
-    extern __shared__ double smc[];            // coef table [3][Ny] as T (+ mode scratch)
-    T* ct = reinterpret_cast<T*>(smc);
+    const int Ny = geo.Ny, N = Ny - 1, RS = ks_row(Ny);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* ct = reinterpret_cast<T*>(smraw);
     for (int e = threadIdx.x; e < 3 * Ny; e += blockDim.x) ct[e] = (T)a.coef[e];
     __syncthreads();
     const T* f1 = ct;
     const T* f2 = ct + Ny;
     const T* f3 = ct + 2 * Ny;
 
-    const int lane = threadIdx.x & 31;
-    const int mm = lane & 7, p = (lane >> 3) & 1, r = lane >> 4;
-    const int m = (blockIdx.x * blockDim.x + threadIdx.x) / 32 * 8 + mm;
-    if (m >= nm) return;                        // warp-uniform (nm is a multiple of 8)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = lane & 7, p = (lane >> 3) & 1, r = lane >> 4;
+    const int m = blockIdx.x * KS_WARPS + warp;
+    if (m >= nm) return;                        // warp-uniform
     const size_t sm = nm;
-    T* saBase;
-    double* sxBase;
-    size_t sst;                                 // stride between scratch rows
-    if (SMEM) {
-        T* sa = reinterpret_cast<T*>(smc + ks_coef_doubles<T>(Ny));
-        double* sx = smc + ks_coef_doubles<T>(Ny) + ((size_t)5 * 2 * Ny * 8 * sizeof(T) + 7) / 8;
-        saBase = sa + mm;
-        sxBase = sx + mm;
-        sst = 8;
-    } else {
-        saBase = a.SA + m;
-        sxBase = a.SX + m;
-        sst = sm;
-    }
-    auto SA = [&](int A, int R, int n) -> T& {
-        return saBase[((size_t)(A * 2 + R) * Ny + n) * sst];
-    };
-    auto SX = [&](int A, int R, int n) -> double& {
-        return sxBase[((size_t)(A * 2 + R) * Ny + n) * sst];
-    };
+    unsigned char* wb = smraw + ks_coef_bytes<T>(Ny) + (size_t)warp * ks_warp_bytes<T>(Ny);
+    T* sa = reinterpret_cast<T*>(wb);
+    double* sx = reinterpret_cast<double*>(wb + ((((size_t)10 * RS * sizeof(T)) + 15) &
+                                                 ~(size_t)15));
+    auto SA = [&](int A, int R, int n) -> T& { return sa[(A * 2 + R) * RS + n]; };
+    auto SX = [&](int S, int R, int n) -> double& { return sx[(S * 2 + R) * Ny + n]; };
     auto TH = [&](int A, int n) -> double { return a.thom[((size_t)A * Ny + n) * sm + m]; };
+
+    // this lane's chunk of the parity-p coefficients: n = p + 2 i, lo <= i < hi
+    const int ntop = N - ((N - p) & 1);
+    const int CH = (N / 2 + 1 + 7) >> 3;        // chunk length (parity 0 is the longer)
+    const int lo = j * CH, hi = min(lo + CH, (ntop - p) / 2 + 1);
+    const int ilo = max(lo, 1);                 // the recurrences start at i = 1
+
     const int nout = ((a.out_sel & 1) ? 3 : 0) + ((a.out_sel & 2) ? 6 : 0);
     const int kzi = m / nkx, kxi = m - kzi * nkx;
-    const int ntop = N - ((N - p) & 1);
-    if (kzi == geo.Nz / 2) {                    // Nyquist mode in z (warp-uniform)
-        for (int n = p; n <= ntop; n += 2)
-            for (int c = 0; c < nout; ++c) a.o[2 * (((size_t)n * nout + c) * sm + m) + r] = (T)0;
+    if (kzi == geo.Nz / 2) {                    // Nyquist mode in z
+        for (int i = lo; i < hi; ++i)
+            for (int c = 0; c < nout; ++c)
+                a.o[2 * (((size_t)(p + 2 * i) * nout + c) * sm + m) + r] = (T)0;
         return;
     }
     const bool k0 = (m == 0);
@@ -284,118 +289,202 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
     auto wallrow = [&](T bot, T top) -> T {
         return (p == 0) ? (T)0.5 * (top + bot) : (T)0.5 * (top - bot);
     };
+    auto red8 = [](double v) {
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        return v;
+    };
+
+    // Right-hand-side-independent parts of this chunk's affine maps (the
+    // Thomas factors depend on k^2 only): the downward sweep
+    // X_n = B_n X_{n+2} + c_n maps the chunk's input X (just above it) to its
+    // lowest X by the product of B; the upward sweep P_n = Y_n P_{n-2} + X_n
+    // maps the input P (just below) to its highest P by the product of Y, and
+    // adds sum_n prod_{k <= n} Y_k times the input to the chunk's sum of P.
+    double Ab = 1.0, Hc = 1.0, SH = 0.0;
+    for (int i = ilo; i < hi; ++i) {
+        const int n = p + 2 * i;
+        Ab *= TH(2, n);
+        Hc *= TH(0, n);
+        SH += Hc;
+    }
+
     // rho_n of the tau recurrence for the series in A (own part), times rs
     auto rho = [&](int A, int n, T rs) -> T {
         T v = f1[n] * SA(A, r, n - 2) - f2[n] * SA(A, r, n);
         if (n + 2 <= N) v += f3[n] * SA(A, r, n + 2);
         return rs * v;
     };
-    // one real tau solve of the series in A in place (FP64 recurrence)
-    auto solve1 = [&](int A, int X, T rs, T sp) {
-        double Xn1 = 0.0;
-        for (int n = ntop; n >= p + 2; n -= 2) {
-            double xn = fma(TH(2, n), Xn1, (double)rho(A, n, rs) * TH(1, n));
-            SX(X, r, n) = xn;
-            Xn1 = xn;
+    // NS real tau solves (series As[s], wall rows sp[s]) in place, FP64
+    // recurrences.  Each sweep is a chunk-local pass, a three-step
+    // Kogge-Stone scan of the chunks' affine maps over the 8 lanes of the
+    // (part, parity), and a second chunk-local pass from the exact input.
+    // Entry: SA(As) complete for all lanes (after a __syncwarp).
+    auto solve = [&](auto ns_tag, const int* As, T rs, const T* sp) {
+        constexpr int NS = decltype(ns_tag)::value;
+        double xl[NS], xin[NS], bv[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) xl[s] = 0.0;
+        for (int i = hi - 1; i >= ilo; --i) {          // downward, local
+            const int n = p + 2 * i;
+            const double b = TH(2, n), id = TH(1, n);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const double c = (double)rho(As[s], n, rs) * id;
+                xl[s] = fma(b, xl[s], c);
+                SX(s, r, n) = c;
+            }
         }
-        double Pp = 0.0, sP = 0.0;
-        for (int n = p + 2; n <= ntop; n += 2) {
-            Pp = fma(TH(0, n), Pp, SX(X, r, n));
-            SX(X, r, n) = Pp;
-            sP += Pp;
+        double A = Ab;                                 // suffix scan over chunks
+#pragma unroll
+        for (int s = 0; s < NS; ++s) bv[s] = xl[s];
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const double Ao = __shfl_down_sync(0xffffffffu, A, d, 8);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const double bo = __shfl_down_sync(0xffffffffu, bv[s], d, 8);
+                if (j + d < 8) bv[s] = fma(A, bo, bv[s]);
+            }
+            if (j + d < 8) A *= Ao;
         }
-        double t = ((double)sp - sP) * isq;
-        SA(A, r, p) = (T)t;
-        for (int n = p + 2; n <= ntop; n += 2) SA(A, r, n) = (T)fma(TH(3, n), t, SX(X, r, n));
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            xin[s] = __shfl_down_sync(0xffffffffu, bv[s], 1, 8);
+            if (j == 7) xin[s] = 0.0;
+        }
+        for (int i = hi - 1; i >= ilo; --i) {          // downward, exact
+            const int n = p + 2 * i;
+            const double b = TH(2, n);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                xin[s] = fma(b, xin[s], SX(s, r, n));
+                SX(s, r, n) = xin[s];
+            }
+        }
+        double pl[NS], spl[NS], pin[NS], t[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) pl[s] = spl[s] = 0.0;
+        for (int i = ilo; i < hi; ++i) {               // upward, local
+            const int n = p + 2 * i;
+            const double y = TH(0, n);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                pl[s] = fma(y, pl[s], SX(s, r, n));
+                spl[s] += pl[s];
+            }
+        }
+        A = Hc;                                        // prefix scan over chunks
+#pragma unroll
+        for (int s = 0; s < NS; ++s) bv[s] = pl[s];
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const double Ao = __shfl_up_sync(0xffffffffu, A, d, 8);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const double bo = __shfl_up_sync(0xffffffffu, bv[s], d, 8);
+                if (j >= d) bv[s] = fma(A, bo, bv[s]);
+            }
+            if (j >= d) A *= Ao;
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            pin[s] = __shfl_up_sync(0xffffffffu, bv[s], 1, 8);
+            if (j == 0) pin[s] = 0.0;
+            const double sP = red8(fma(SH, pin[s], spl[s]));
+            t[s] = ((double)sp[s] - sP) * isq;
+        }
+        __syncwarp();                                  // every rho read of SA(As) is done
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if (j == 0) SA(As[s], r, p) = (T)t[s];
+        for (int i = ilo; i < hi; ++i) {               // upward, exact; a_n = P_n + Q_n a_p
+            const int n = p + 2 * i;
+            const double y = TH(0, n), q = TH(3, n);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                pin[s] = fma(y, pin[s], SX(s, r, n));
+                SA(As[s], r, n) = (T)fma(q, t[s], pin[s]);
+            }
+        }
     };
-    auto solve3 = [&](T rs, T sp0, T sp1, T sp2) {
-        double X0 = 0, X1 = 0, X2 = 0;
-        for (int n = ntop; n >= p + 2; n -= 2) {
-            double b = TH(2, n), id = TH(1, n);
-            X0 = fma(b, X0, (double)rho(AU, n, rs) * id);
-            X1 = fma(b, X1, (double)rho(AV, n, rs) * id);
-            X2 = fma(b, X2, (double)rho(AW, n, rs) * id);
-            SX(0, r, n) = X0;
-            SX(1, r, n) = X1;
-            SX(2, r, n) = X2;
-        }
-        double P0 = 0, P1 = 0, P2 = 0, q0 = 0, q1 = 0, q2 = 0;
-        for (int n = p + 2; n <= ntop; n += 2) {
-            double y = TH(0, n);
-            P0 = fma(y, P0, SX(0, r, n));
-            P1 = fma(y, P1, SX(1, r, n));
-            P2 = fma(y, P2, SX(2, r, n));
-            SX(0, r, n) = P0;
-            SX(1, r, n) = P1;
-            SX(2, r, n) = P2;
-            q0 += P0; q1 += P1; q2 += P2;
-        }
-        double t0 = ((double)sp0 - q0) * isq, t1 = ((double)sp1 - q1) * isq;
-        double t2 = ((double)sp2 - q2) * isq;
-        SA(AU, r, p) = (T)t0;
-        SA(AV, r, p) = (T)t1;
-        SA(AW, r, p) = (T)t2;
-        for (int n = p + 2; n <= ntop; n += 2) {
-            double q = TH(3, n);
-            SA(AU, r, n) = (T)fma(q, t0, SX(0, r, n));
-            SA(AV, r, n) = (T)fma(q, t1, SX(1, r, n));
-            SA(AW, r, n) = (T)fma(q, t2, SX(2, r, n));
-        }
-    };
-    // derivative (own part, own parity) of a series: b_n = b_{n+2} + 2(n+1) a_{n+1}
+    using one = std::integral_constant<int, 1>;
+    using two = std::integral_constant<int, 2>;
+    using three = std::integral_constant<int, 3>;
+    // derivative (own part, own parity) of a series:
+    // b_n = b_{n+2} + 2(n+1) a_{n+1}, b_N = 0; stored as dsc (n == 0 ? b/2 : b)
     auto deriv = [&](auto get, int AD) {
-        T b2 = 0;
-        int nstart = ntop;
-        if (nstart == N) {
-            SA(AD, r, N) = 0;
-            nstart -= 2;
+        T s = 0;
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
+            if (n < N) s += (T)(2 * (n + 1)) * get(n + 1);
         }
-        for (int n = nstart; n >= p; n -= 2) {
-            T bn = b2 + (T)(2 * (n + 1)) * get(n + 1);
-            b2 = bn;
-            SA(AD, r, n) = dsc * ((n == 0) ? (T)0.5 * bn : bn);
+        T inc = s;                                     // suffix sum over chunks
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const T o = __shfl_down_sync(0xffffffffu, inc, d, 8);
+            if (j + d < 8) inc += o;
+        }
+        T b = __shfl_down_sync(0xffffffffu, inc, 1, 8);
+        if (j == 7) b = 0;
+        for (int i = hi - 1; i >= lo; --i) {
+            const int n = p + 2 * i;
+            if (n < N) b += (T)(2 * (n + 1)) * get(n + 1);
+            SA(AD, r, n) = dsc * ((n == 0) ? (T)0.5 * b : b);
         }
     };
 
-    // Every __syncwarp and shuffle below is reached by all 32 lanes; the
-    // k = 0 mode (lanes of warp 0 with mm = 0) only changes per-lane work.
     // ---- stage 1: pressure (k != 0) or the whole k = 0 solve
     if (!k0) {
         deriv([&](int n) { return F(1, r, n); }, AT);
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             T v = (r == 0) ? (kx * F(0, 1, n) - SA(AT, 0, n) + kz * F(2, 1, n))
                            : -(kx * F(0, 0, n) + SA(AT, 1, n) + kz * F(2, 0, n));
             SA(AP, r, n) = v;
         }
-        solve1(AP, 0, s2, (T)0);
+        __syncwarp();
+        const int As[1] = {AP};
+        const T sp[1] = {(T)0};
+        solve(one{}, As, s2, sp);
     } else {
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             SA(AU, r, n) = F(0, r, n);
             SA(AW, r, n) = F(2, r, n);
         }
-        solve1(AU, 0, s2 / mu, wallrow(Wl(0, 0, r), Wl(1, 0, r)));
-        solve1(AW, 1, s2 / mu, wallrow(Wl(0, 2, r), Wl(1, 2, r)));
+        __syncwarp();
+        const int As[2] = {AU, AW};
+        const T sp[2] = {wallrow(Wl(0, 0, r), Wl(1, 0, r)), wallrow(Wl(0, 2, r), Wl(1, 2, r))};
+        solve(two{}, As, s2 / mu, sp);
         // v linear between its wall values
         T vbw = Wl(0, 1, r), vtw = Wl(1, 1, r);
-        for (int n = p; n <= ntop; n += 2)
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             SA(AV, r, n) = (n == 0) ? (T)0.5 * (vbw + vtw) : (n == 1) ? (T)0.5 * (vtw - vbw) : (T)0;
+        }
         // pressure: dp/dybar = G = -(W/2) f_y, zero mean over y
-        T psum = 0;
-        for (int n = (p == 0 ? 2 : 1); n <= ntop; n += 2) {
+        double psum = 0;
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
+            if (n == 0) continue;
             T c = (n == 1) ? (T)2 : (T)1;
             T gm = -(T)0.5 * W * F(1, r, n - 1);
             T gp = (n + 1 <= N) ? -(T)0.5 * W * F(1, r, n + 1) : (T)0;
             T pn = (c * gm - gp) / (T)(2 * n);
             SA(AP, r, n) = pn;
-            if (p == 0) psum += pn / (T)(1 - n * n);
+            if (p == 0) psum += (double)(pn / (T)(1 - n * n));
         }
-        if (p == 0) SA(AP, r, 0) = -psum;
+        psum = red8(psum);
+        if (p == 0 && j == 0) SA(AP, r, 0) = (T)(-psum);
     }
     __syncwarp();
     // ---- stage 2: velocity of the a-problem, f + grad p_a (k != 0)
     if (!k0) {
         deriv([&](int n) { return SA(AP, r, n); }, AT);
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             T pr = SA(AP, 1 - r, n);
             T ikp_x = (r == 0) ? -kx * pr : kx * pr;
             T ikp_z = (r == 0) ? -kz * pr : kz * pr;
@@ -403,37 +492,40 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
             SA(AV, r, n) = F(1, r, n) + SA(AT, r, n);
             SA(AW, r, n) = F(2, r, n) + ikp_z;
         }
-        solve3(s2 / mu, wallrow(Wl(0, 0, r), Wl(1, 0, r)), wallrow(Wl(0, 1, r), Wl(1, 1, r)),
-               wallrow(Wl(0, 2, r), Wl(1, 2, r)));
+        __syncwarp();
+        const int As[3] = {AU, AV, AW};
+        const T sp[3] = {wallrow(Wl(0, 0, r), Wl(1, 0, r)), wallrow(Wl(0, 1, r), Wl(1, 1, r)),
+                         wallrow(Wl(0, 2, r), Wl(1, 2, r))};
+        solve(three{}, As, s2 / mu, sp);
     }
     __syncwarp();
     // ---- stage 3: influence matrix from the divergence at both walls (FP64)
-    double ub = 0, ut = 0, wb = 0, wt = 0, vb = 0, vt = 0;
     if (!k0) {
-        for (int n = p; n <= ntop; n += 2) {
-            double n2 = (double)(n * n);
-            double u = (double)SA(AU, r, n), w = (double)SA(AW, r, n), v = (double)SA(AV, r, n);
-            ub += u; ut += u;
-            wb += w; wt += w;
-            vb += n2 * v; vt += n2 * v;
+        double su = 0, sw = 0, sv = 0;
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
+            su += (double)SA(AU, r, n);
+            sw += (double)SA(AW, r, n);
+            sv += (double)(n * n) * (double)SA(AV, r, n);
         }
-        // parity sign (-1)^n is constant per thread: apply once
-        double sg = (double)sgn;
-        ub *= sg; wb *= sg; vb *= -sg;
-    }
-    ub += __shfl_xor_sync(0xffffffffu, ub, 8);
-    ut += __shfl_xor_sync(0xffffffffu, ut, 8);
-    wb += __shfl_xor_sync(0xffffffffu, wb, 8);
-    wt += __shfl_xor_sync(0xffffffffu, wt, 8);
-    vb += __shfl_xor_sync(0xffffffffu, vb, 8);
-    vt += __shfl_xor_sync(0xffffffffu, vt, 8);
-    double ubo = __shfl_xor_sync(0xffffffffu, ub, 16);
-    double uto = __shfl_xor_sync(0xffffffffu, ut, 16);
-    double wbo = __shfl_xor_sync(0xffffffffu, wb, 16);
-    double wto = __shfl_xor_sync(0xffffffffu, wt, 16);
-    double vbo = __shfl_xor_sync(0xffffffffu, vb, 16);
-    double vto = __shfl_xor_sync(0xffffffffu, vt, 16);
-    if (!k0) {
+        su = red8(su);
+        sw = red8(sw);
+        sv = red8(sv);
+        // parity sign (-1)^n is constant per lane: apply once
+        const double sg = (double)sgn;
+        double ub = sg * su, ut = su, wb = sg * sw, wt = sw, vb = -sg * sv, vt = sv;
+        ub += __shfl_xor_sync(0xffffffffu, ub, 8);
+        ut += __shfl_xor_sync(0xffffffffu, ut, 8);
+        wb += __shfl_xor_sync(0xffffffffu, wb, 8);
+        wt += __shfl_xor_sync(0xffffffffu, wt, 8);
+        vb += __shfl_xor_sync(0xffffffffu, vb, 8);
+        vt += __shfl_xor_sync(0xffffffffu, vt, 8);
+        double ubo = __shfl_xor_sync(0xffffffffu, ub, 16);
+        double uto = __shfl_xor_sync(0xffffffffu, ut, 16);
+        double wbo = __shfl_xor_sync(0xffffffffu, wb, 16);
+        double wto = __shfl_xor_sync(0xffffffffu, wt, 16);
+        double vbo = __shfl_xor_sync(0xffffffffu, vb, 16);
+        double vto = __shfl_xor_sync(0xffffffffu, vt, 16);
         dc Ub = r == 0 ? mkc(ub, ubo) : mkc(ubo, ub);
         dc Ut = r == 0 ? mkc(ut, uto) : mkc(uto, ut);
         dc Wb = r == 0 ? mkc(wb, wbo) : mkc(wbo, wb);
@@ -447,7 +539,6 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
         const double* mi = a.minv + m;
         dc p1 = -1.0 * (mi[0] * Cb + mi[sm] * Ct);
         dc p2 = -1.0 * (mi[2 * sm] * Cb + mi[3 * sm] * Ct);
-        double sg = (double)sgn;
         dc pp = p1 + sg * p2, pm = p1 - sg * p2;
         const double* pbv = a.ksb + m;
         const double* phv = a.ksb + (size_t)Ny * sm + m;
@@ -455,7 +546,8 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
         T ppr = (T)(r == 0 ? pp.x : pp.y), pmr = (T)(r == 0 ? pm.x : pm.y);
         T ppo = (T)(r == 0 ? pp.y : pp.x);       // other part of pp
         T ikf = r == 0 ? (T)-1 : (T)1;           // (i z)_r = ikf * z_other
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             size_t o = (size_t)n * sm;
             T ph = (T)phv[o];
             SA(AU, r, n) += ikf * kx * ph * ppo;
@@ -469,7 +561,8 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
     T* op = a.o;
     int c0 = 0;
     if (a.out_sel & 1) {
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             size_t b = ((size_t)n * nout) * sm + m;
             op[2 * b + r] = SA(AU, r, n);
             op[2 * (b + sm) + r] = SA(AV, r, n);
@@ -480,10 +573,10 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
     if (a.out_sel & 2) {
         // d/dy of u, v, w, one at a time, into the aux row AT
         deriv([&](int n) { return SA(AU, r, n); }, AT);
-        __syncwarp();
         T ikf = r == 0 ? (T)-1 : (T)1;
         // first pass: components that use du/dy
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             T P = SA(AP, r, n);
             T Uo = SA(AU, 1 - r, n), Vo = SA(AV, 1 - r, n), Wo = SA(AW, 1 - r, n);
             size_t b = ((size_t)n * nout + c0) * sm + m;
@@ -492,15 +585,15 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
             op[2 * (b + 2 * sm) + r] = mu * (ikf * kz * Uo + ikf * kx * Wo);        // xz
             op[2 * (b + 5 * sm) + r] = -P + (T)2 * mu * ikf * kz * Wo;              // zz
         }
-        __syncwarp();
         deriv([&](int n) { return SA(AV, r, n); }, AT);
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             size_t b = ((size_t)n * nout + c0) * sm + m;
             op[2 * (b + 3 * sm) + r] = -SA(AP, r, n) + (T)2 * mu * SA(AT, r, n);   // yy
         }
-        __syncwarp();
         deriv([&](int n) { return SA(AW, r, n); }, AT);
-        for (int n = p; n <= ntop; n += 2) {
+        for (int i = lo; i < hi; ++i) {
+            const int n = p + 2 * i;
             T Vo = SA(AV, 1 - r, n);
             size_t b = ((size_t)n * nout + c0) * sm + m;
             op[2 * (b + 4 * sm) + r] = mu * (ikf * kz * Vo + SA(AT, r, n));         // yz
@@ -511,37 +604,23 @@ __global__ void __launch_bounds__(SMEM ? 32 : 128) k_ks(KSArgs<T> a) {
 template <typename T>
 cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
                      const double* minv, const double* coef, const double* thom,
-                     const double* isq, void* scratch, int out_sel, T* ocoef, cudaStream_t st) {
-    int nm = geo.Nz * geo.nkx;
-    size_t naux = (size_t)5 * 2 * geo.Ny * nm;
-    T* SA = (T*)scratch;
-    double* SX = (double*)((char*)scratch + ((naux * sizeof(T) + 255) & ~(size_t)255));
-    KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, SA, SX, out_sel, ocoef};
-    long warps = (long)(nm + 7) / 8;
-    // mode scratch in shared memory when a warp's share fits the opt-in limit
-    // (the kernel has no static shared memory)
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
-            cudaSuccess ||
-        grant_max_smem((const void*)k_ks<T, true>) != cudaSuccess)
-        optin = 0;
-    const size_t bytes = ks_smem_bytes<T>(geo.Ny);
-    if (bytes <= (size_t)optin) {
-        k_ks<T, true><<<(unsigned)warps, 32, bytes, st>>>(a);
-        return cudaGetLastError();
-    }
-    size_t smem = (size_t)3 * geo.Ny * sizeof(double);
-    k_ks<T, false><<<(unsigned)((warps * 32 + 127) / 128), 128, smem, st>>>(a);
+                     const double* isq, int out_sel, T* ocoef, cudaStream_t st) {
+    const int nm = geo.Nz * geo.nkx;
+    KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, out_sel, ocoef};
+    // at most 3 x 257 T + 4 x (10 x 272 T + 6 x 257 FP64) = 137 KB (FP64, Ny = 257)
+    cudaError_t e = grant_max_smem((const void*)k_ks<T>);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((nm + KS_WARPS - 1) / KS_WARPS);
+    k_ks<T><<<blocks, KS_WARPS * 32, ks_smem_bytes<T>(geo.Ny), st>>>(a);
     return cudaGetLastError();
 }
 
 template cudaError_t ks_modes<float>(const GridGeom&, const float*, const float*, const double*,
                                      const double*, const double*, const double*,
-                                     const double*, void*, int, float*, cudaStream_t);
+                                     const double*, int, float*, cudaStream_t);
 template cudaError_t ks_modes<double>(const GridGeom&, const double*, const double*,
                                       const double*, const double*, const double*,
-                                      const double*, const double*, void*, int, double*,
+                                      const double*, const double*, int, double*,
                                       cudaStream_t);
 
 }  // namespace ggem

@@ -432,6 +432,56 @@ __device__ __forceinline__ int cull_cells(const LocalArgs<T>& a, int lane, T ox,
     return nc;
 }
 
+// The same culling in batches: rounds of 32 neighbour offsets from *round
+// on, stopping before a round could overflow `cap` entries; *round is left at
+// the first round not culled (nb rounds = done).
+template <typename T, int R>
+__device__ __forceinline__ int cull_cells_batch(const LocalArgs<T>& a, int lane, T ox, T oy,
+                                                T oz, int cx, int cy, int cz, int* s_cst,
+                                                int* s_cnt, unsigned short* s_off, int& round,
+                                                int cap) {
+    const CellGrid& cg = a.cg;
+    const unsigned lt = (1u << lane) - 1u;
+    const T reach2 = a.k.rc2 * (T)1.0001;
+    constexpr int side = 2 * R + 1, nb = side * side * side, nr = (nb + 31) / 32;
+    int nc = 0;
+    for (; round < nr && nc + 32 <= cap; ++round) {
+        const int oi = round * 32 + lane;
+        bool keep = false;
+        int st = 0, cnt = 0;
+        if (oi < nb) {
+            const int ix = oi % side - R, iy = (oi / side) % side - R, iz = oi / (side * side) - R;
+            const int cyy = cy + iy;
+            if (cyy >= 0 && cyy < cg.ncy) {
+                const T gx = ix > 0 ? (T)ix * a.k.hx - ox : (ix < 0 ? ox - (T)(ix + 1) * a.k.hx : (T)0);
+                const T gy = iy > 0 ? (T)iy * a.k.hy - oy : (iy < 0 ? oy - (T)(iy + 1) * a.k.hy : (T)0);
+                const T gz = iz > 0 ? (T)iz * a.k.hz - oz : (iz < 0 ? oz - (T)(iz + 1) * a.k.hz : (T)0);
+                if (gx * gx + gy * gy + gz * gz <= reach2) {
+                    int cxx = cx + ix, czz = cz + iz;
+                    cxx += (cxx < 0) ? cg.ncx : 0;
+                    cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
+                    czz += (czz < 0) ? cg.ncz : 0;
+                    czz -= (czz >= cg.ncz) ? cg.ncz : 0;
+                    const int c = (czz * cg.ncy + cyy) * cg.ncx + cxx;
+                    st = a.src.cell_start[c];
+                    cnt = a.src.cell_start[c + 1] - st;
+                    keep = cnt > 0;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int slot = nc + __popc(m & lt);
+            s_cst[slot] = st;
+            s_cnt[slot] = cnt;
+            s_off[slot] = (unsigned short)oi;
+        }
+        nc += __popc(m);
+    }
+    __syncwarp();
+    return nc;
+}
+
 // u_i = sum G^l_ij g_j ; sigma_ik = sum T^l_ijk g_j ; v_i = n_k sigma_ik
 // (unscaled in the loop; the caller-facing factors are applied at the end).
 //
@@ -565,8 +615,8 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 }
 
 // ------------------------------------------------- FP32 element rule
-// The element-rule local sum in FP32 reads ~1,500 quadrature points per cell
-// and evaluates about 70 % of them, so no hit queue: every lane takes two
+// The element-rule local sum in FP32 reads ~700 quadrature points per cell
+// and evaluates about 80 % of them, so no hit queue: every lane takes two
 // adjacent candidates of each 64-point step through a cell and evaluates both
 // with paired FP32 arithmetic; a miss contributes nothing (its strength is
 // zero, and every term carries a factor g).  The points are read from
@@ -574,17 +624,18 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 // one 8-byte load brings a coordinate of both candidates already paired.
 // Steps start at even sorted indices (8-byte alignment); slots outside the cell
 // are masked like misses (the planes are padded by one step, zero-filled).
-constexpr int LWE = 8;        // warps (targets) per block
+constexpr int LWE = 8;        // warps (targets) per block; 5 blocks per SM (48 registers)
+constexpr int kCap = 128;     // culled cells per batch (a target may need several batches)
 constexpr int kChunk = 64;    // candidates per warp step
 
 template <int MODE, int REACH>
-__global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
+__global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a,
                                                           const float* __restrict__ ps,
                                                           const float* __restrict__ gs,
                                                           size_t ld) {
-    __shared__ int s_cst[LWE][kNb];
-    __shared__ int s_cnt[LWE][kNb];
-    __shared__ unsigned short s_off[LWE][kNb];
+    __shared__ int s_cst[LWE][kCap];
+    __shared__ int s_cnt[LWE][kCap];
+    __shared__ unsigned short s_off[LWE][kCap];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * LWE + wid;
     if (t >= a.n_tgt) return;                     // warp-uniform
@@ -592,8 +643,6 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
     float ox, oy, oz;
     load_target<float, TK_POINTS>(a, t, ox, oy, oz, cx, cy, cz, oidx);
     constexpr int R = REACH, side = 2 * R + 1;
-    const int nc = cull_cells<float, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid],
-                                        s_cnt[wid], s_off[wid]);
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (MODE & OUT_DBL) {
         nx = (float)a.nrm[3 * oidx]; ny = (float)a.nrm[3 * oidx + 1]; nz = (float)a.nrm[3 * oidx + 2];
@@ -607,6 +656,9 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
     const float2* gy = (const float2*)(gs + ld);
     const float2* gz = (const float2*)(gs + 2 * ld);
     PairAcc2 acc;
+    for (int round = 0; round < (side * side * side + 31) / 32;) {
+    const int nc = cull_cells_batch<float, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid],
+                                              s_cnt[wid], s_off[wid], round, kCap);
     for (int ci = 0; ci < nc; ++ci) {
         const int st = s_cst[wid][ci], end = st + s_cnt[wid][ci], oi = s_off[wid][ci];
         // target position in the frame of this source cell's corner
@@ -641,6 +693,8 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
                               f2_make(h0 ? wz.x : 0.f, h1 ? wz.y : 0.f), nx2, ny2, nz2, acc);
         }
     }
+    __syncwarp();
+    }
     float ux = f2_sum(acc.ux), uy = f2_sum(acc.uy), uz = f2_sum(acc.uz);
     if (MODE & OUT_DBL) {
         const float sn = f2_sum(acc.sn);
@@ -659,6 +713,46 @@ __global__ void __launch_bounds__(LWE * 32) k_local_elem32(LocalArgs<float> a,
         o[0] = a.k.fU * ux;
         o[1] = a.k.fU * uy;
         o[2] = a.k.fU * uz;
+    }
+}
+
+// Order of the sorted points within each cell: 4 x 4 x 4 sub-cells in Morton
+// order, so that consecutive points (the 64-point steps of the FP32 element
+// rule) lie close together.  One block per cell; a counting sort by the 6-bit
+// key into pos_out / perm_out.
+__device__ __forceinline__ int subcell_key(float4 p, float ihx, float ihy, float ihz) {
+    const int ix = min(3, max(0, (int)(p.x * ihx))), iy = min(3, max(0, (int)(p.y * ihy))),
+              iz = min(3, max(0, (int)(p.z * ihz)));
+    return (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2) | ((ix & 2) << 2) | ((iy & 2) << 3) |
+           ((iz & 2) << 4);
+}
+
+__global__ void k_cell_subsort(const int* __restrict__ start, const float4* __restrict__ pos,
+                               const int* __restrict__ perm, float ihx, float ihy, float ihz,
+                               float4* __restrict__ pos_out, int* __restrict__ perm_out) {
+    __shared__ int cnt[64];
+    const int c = blockIdx.x;
+    const int st = start[c], n = start[c + 1] - st;
+    if (n == 0) return;                          // block-uniform
+    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        atomicAdd(&cnt[subcell_key(pos[st + i], ihx, ihy, ihz)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < 64; ++k) {
+            const int v = cnt[k];
+            cnt[k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 p = pos[st + i];
+        const int slot = st + atomicAdd(&cnt[subcell_key(p, ihx, ihy, ihz)], 1);
+        pos_out[slot] = p;
+        perm_out[slot] = perm[st + i];
     }
 }
 
@@ -891,6 +985,18 @@ static void launch_kind(const LocalArgs<T>& a, int mode, cudaStream_t st) {
     else launch_kind<T, KIND, 2>(a, mode, st);
 }
 
+// Within-cell sub-sort of sorted points (pos, perm); tmp_* of n entries as scratch.
+cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start, float4* pos,
+                         int* perm, float4* tmp_pos, int* tmp_perm, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_cell_subsort<<<ncell, 256, 0, st>>>(start, pos, perm, (float)(4.0 / cg.hx),
+                                          (float)(4.0 / cg.hy), (float)(4.0 / cg.hz), tmp_pos,
+                                          tmp_perm);
+    cudaMemcpyAsync(pos, tmp_pos, (size_t)n * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(perm, tmp_perm, (size_t)n * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
 cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st) {
     if (n > 0) k_to_soa<<<(n + 255) / 256, 256, 0, st>>>(n, (const float4*)in, out, ld);
     return cudaGetLastError();
@@ -918,6 +1024,15 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
         const float* ps = (const float*)aux_pos;
         const float* gs = (const float*)aux_g;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
+        // ~11 KB of shared memory per block, 5 blocks per SM: ask for a small
+        // shared-memory carveout so that the rest of the SM's 256 KB serves as L1
+        // for the candidates the warps of a block re-read (a preference; cheap
+        // per launch)
+        const void* kf = layer == 0 ? (cg.reach == 3 ? (const void*)k_local_elem32<OUT_U, 3>
+                                                     : (const void*)k_local_elem32<OUT_U, 2>)
+                                    : (cg.reach == 3 ? (const void*)k_local_elem32<OUT_DBL, 3>
+                                                     : (const void*)k_local_elem32<OUT_DBL, 2>);
+        cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
         if (cg.reach == 3) {
             if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
             else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);

@@ -174,7 +174,7 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
     });
     stage(P, ST_KS, 1, [&] {
         GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom, P->d_isq,
-                            P->d_ksw, out_sel, A, st));
+                            out_sel, A, st));
     });
     int nout = nout_of(out_sel);
     if (P->offgrid == GGEM_OFFGRID_SPECTRAL) {
@@ -315,10 +315,10 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         GG_CUDA(gather_strengths<T>(n, P->d_mesh_perm, q, P->d_area, 8.0 * kPi * geo.mu,
                                     (v4_t<T>*)P->d_sg, st));
         if (elem)
-            GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qp_perm, P->d_qv, (const v4_t<T>*)P->d_qw, q,
-                                    8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg, st));
+            GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, q,
+                                    8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
+                                    P->fp64 ? nullptr : (T*)P->d_qg_soa, P->soa_ld, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
-        if (elem && !P->fp64) GG_CUDA(to_soa(P->n_qp, P->d_qg, P->d_qg_soa, P->soa_ld, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
     src.n = n;
@@ -609,11 +609,6 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     GG_CUDA(cudaMalloc(&P->d_gridB, P->grid_elems * esz));
     GG_CUDA(cudaMalloc(&P->d_wall, (size_t)6 * prm.Nz * prm.Nx * esz));
     {
-        size_t naux = (size_t)5 * 2 * Ny * nm * esz;
-        size_t nbytes = ((naux + 255) & ~(size_t)255) + (size_t)3 * 2 * Ny * nm * sizeof(double);
-        GG_CUDA(cudaMalloc(&P->d_ksw, nbytes));
-    }
-    {
         std::vector<double> tab(3 * Ny);
         ks_coef_table(Ny, tab.data());
         dalloc(P, &P->d_kscoef, tab.size());
@@ -729,7 +724,7 @@ void plan_free(ggem_plan_t* P) {
     void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
                     P->d_minv, P->d_ydiff, P->d_sdi, P->d_sdf, P->d_mesh_sdi, P->d_mesh_sdf,
                     P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall,
-                    P->d_ksw, P->d_cell_count, P->d_cell_start, P->d_cursor, P->d_src_cell,
+                    P->d_cell_count, P->d_cell_start, P->d_cursor, P->d_src_cell,
                     P->d_perm, P->d_spos, P->d_sg, P->d_src_x, P->d_local, P->d_in0, P->d_in1,
                     P->d_in2, P->d_out0, P->d_out1, P->d_tgt_cell, P->d_tgt_pos,
                     P->d_wall_cell, P->d_wall_pos, P->d_x, P->d_tri, P->d_area, P->d_nrm,
@@ -911,9 +906,20 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 GG_CUDA(build_cells<float>(P->geo, P->cg, nq, P->d_qx, P->d_cell_count,
                                            P->d_qp_start, P->d_cursor, P->d_qp_cell,
                                            P->d_qp_perm, (float4*)P->d_qp_pos, st));
+                // within-cell order (scratch: the strength buffer and the cursors,
+                // both free until the first evaluation)
+                GG_CUDA(cell_subsort(P->cg, nq, P->ncell, P->d_qp_start, (float4*)P->d_qp_pos,
+                                     P->d_qp_perm, (float4*)P->d_qg, P->d_cursor, st));
                 GG_CUDA(to_soa(nq, P->d_qp_pos, P->d_qp_soa, P->soa_ld, st));
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
+            // weights into point order too (scratch: the strength buffer)
+            if (P->fp64)
+                GG_CUDA(qp_sort_weights<double>(nq, P->d_qp_perm, (double4_32a*)P->d_qw,
+                                                (double4_32a*)P->d_qg, st));
+            else
+                GG_CUDA(qp_sort_weights<float>(nq, P->d_qp_perm, (float4*)P->d_qw,
+                                               (float4*)P->d_qg, st));
             P->n_qp = nq;
         }
         P->n_nodes = n_nodes;

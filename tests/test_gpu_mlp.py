@@ -135,8 +135,14 @@ def test_tensor_core_forward_rows_and_guess(ggem, susp):
     f, sc = P.mlp_features(_dev(kappa), _dev(r))
     y = P.mlp_forward(f)
     g = P.mlp_guess(_dev(kappa), _dev(r)).cpu().numpy()
-    expect = r + sc * s_y * y
-    assert np.abs(g - expect).max() < 1e-6 * np.abs(expect).max()
+    # mlp_guess evaluates the features again: the double layer's spreading adds
+    # in L2 reductions of arbitrary order, so its features differ from f by FP32
+    # rounding, which now and then moves a BF16 rounding of the network's input;
+    # compare the correction row by row as the forward check above does
+    corr = sc * s_y * y
+    cerr = np.abs((g - r) - corr).max(1) / np.abs(corr).max()
+    assert cerr.max() < 1e-2
+    assert (cerr < 1e-5).mean() > 0.95, float((cerr < 1e-5).mean())
     P.check()
 
 
