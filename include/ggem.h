@@ -556,6 +556,16 @@ ggem_status ggem_trace_read(const ggem_plan_t *plan, int stage, double *total_ms
  * frees its buffer. */
 ggem_status ggem_probe_l2_reduction(long nvec, int iters, void *stream, double *ms,
                                     double *vec_per_s);
+/* Measurement probe (no counterpart in the paper): the throughput of FP32
+ * atomic adds into shared memory -- what a spreading staged in shared memory
+ * (sources accumulated into a tile of the grid, one write per node) would be
+ * bound by: 4 blocks of 256 threads per SM, each holding 4096 nodes x 3
+ * components (48 KB); every warp adds into 32 consecutive nodes of each
+ * component at a pseudo-random place of its block's tile, `iters` times
+ * (1 <= iters <= 2^20); one untimed launch, then one timed by CUDA events on
+ * `stream`.  *ms: the timed launch; *adds_per_s: scalar adds per second.
+ * Allocates and frees a 48 KB result buffer. */
+ggem_status ggem_probe_smem_reduction(int iters, void *stream, double *ms, double *adds_per_s);
 
 /* Number of library kernels launched by this plan since creation or the
  * last ggem_trace_enable. */

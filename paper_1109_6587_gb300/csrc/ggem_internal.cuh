@@ -101,7 +101,7 @@ struct ggem_plan {
     void* d_cheb_inv = nullptr;        // [Ny][Ny] T
     void* d_tw_x = nullptr;            // complex T: [Nx/4] FFT-length-Nx/2 twiddles + [Nx/2] post twiddles
     void* d_tw_z = nullptr;            // complex T: [Nz/2]
-    double* d_ksb = nullptr;           // [3][Ny][nmodes] p_b, phi_b, v_b coefficients
+    void* d_ksb = nullptr;             // [3][Ny][nmodes] T: p_b, phi_b, v_b coefficients
     double* d_minv = nullptr;          // [4][nmodes] inverse influence matrix
     double* d_kscoef = nullptr;        // [3][Ny] recurrence coefficients
     void* d_ydiff = nullptr;           // [Ny][Ny] T, y_j - y_k
@@ -111,6 +111,7 @@ struct ggem_plan {
     void* d_gridB = nullptr;
     void* d_wall = nullptr;            // [2][3][Nz][Nx] T
     double* d_thom = nullptr;          // [4][Ny][nmodes] Thomas factors
+    double* d_kschunk = nullptr;       // [nmodes][3][2][8] chunk products of the factors
     double* d_isq = nullptr;           // [2][nmodes]
     size_t grid_elems = 0;
 
@@ -393,9 +394,10 @@ cudaError_t cheb_tc_prepare(int Ny, const float* M, void* prep, cudaStream_t st)
 // thom = per-mode Thomas factors [4][Ny][nmodes], isq = [2][nmodes];
 // scratch = [5][2][Ny][nmodes] T, then (256-byte aligned) [3][2][Ny][nmodes] double
 template <typename T>
-cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
+cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const T* ksb,
                      const double* minv, const double* coef, const double* thom,
-                     const double* isq, int out_sel, T* ocoef, cudaStream_t st);
+                     const double* chunk, const double* isq, int out_sel, T* ocoef,
+                     cudaStream_t st);
 
 // mode 0: velocity, out = local + interp - self_coef * wself * qself
 // mode 1: stress (6), out = local + interp

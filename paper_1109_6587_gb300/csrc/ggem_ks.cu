@@ -35,8 +35,8 @@
 // shared memory (11 KB for Ny = 129 in FP32), so a block of 4 modes needs no
 // global scratch and several blocks share an SM.  The Thomas factors
 // (Y_n, 1/d_n, B_n, Q_n) depend on k^2 only; they come from a plan-time
-// table, and the products of each chunk's factors that the scans use are
-// formed once per mode and serve all four solves.
+// table, and so do the products of each chunk's factors that the scans use
+// (ks_chunk_mode).
 #include <type_traits>
 
 #include "ggem_internal.cuh"
@@ -194,15 +194,56 @@ void ks_thomas_mode(int Ny, double lam, double* tab, double* isq) {
     }
 }
 
+// The recurrence indices of chunk j of parity p: coefficients n = p + 2 i,
+// ilo <= i < hi; the Ny/2 coefficients of a parity are split into 8 chunks of
+// equal length (parity 0, the longer, sets it) and i = 0 (the wall row's
+// coefficient a_p) takes no part in the sweeps.
+__host__ __device__ inline void ks_chunk_range(int N, int p, int j, int& lo, int& ilo, int& hi) {
+    const int ntop = N - ((N - p) & 1);
+    const int ch = (N / 2 + 1 + 7) >> 3;
+    lo = j * ch;
+    hi = (lo + ch < (ntop - p) / 2 + 1) ? lo + ch : (ntop - p) / 2 + 1;
+    ilo = lo > 1 ? lo : 1;
+}
+
+// Right-hand-side-independent parts of the chunks' affine maps, per parity p
+// and chunk j, from the Thomas factors tab [4][Ny] (Y, id, B, Q): the downward
+// sweep X_n = B_n X_{n+2} + c_n maps the chunk's input X (just above it) to
+// its lowest X by prod B; the upward sweep P_n = Y_n P_{n-2} + X_n maps the
+// input P (just below) to its highest P by prod Y and adds
+// sum_n prod_{k <= n} Y_k times the input to the chunk's sum of P.
+// out[k * 16 + p * 8 + j], k = 0: prod B, 1: prod Y, 2: the sum.
+void ks_chunk_mode(int Ny, const double* tab, double* out) {
+    const int N = Ny - 1;
+    const double* Y = tab;
+    const double* B = tab + 2 * Ny;
+    for (int p = 0; p < 2; ++p)
+        for (int j = 0; j < 8; ++j) {
+            int lo, ilo, hi;
+            ks_chunk_range(N, p, j, lo, ilo, hi);
+            double ab = 1.0, hc = 1.0, sh = 0.0;
+            for (int i = ilo; i < hi; ++i) {
+                const int n = p + 2 * i;
+                ab *= B[n];
+                hc *= Y[n];
+                sh += hc;
+            }
+            out[0 * 16 + p * 8 + j] = ab;
+            out[1 * 16 + p * 8 + j] = hc;
+            out[2 * 16 + p * 8 + j] = sh;
+        }
+}
+
 // -------------------------------------------------------------- device side
 template <typename T> struct KSArgs {
     GridGeom geo;
     const T* f;            // [Ny][3][nmodes] complex T (re, im interleaved)
     const T* wall;         // [2][3][nmodes] complex T
-    const double* ksb;     // [3][Ny][nmodes]
+    const T* ksb;          // [3][Ny][nmodes]
     const double* minv;    // [4][nmodes]
     const double* coef;    // [3][Ny]
     const double* thom;    // [4][Ny][nmodes] Y, id, B, Q
+    const double* chunk;   // [nmodes][3][2][8] (ks_chunk_mode)
     const double* isq;     // [2][nmodes]
     int out_sel;           // bit0: u, v, w; bit1: stress
     T* o;                  // [Ny][nout][nmodes] complex T
@@ -261,10 +302,8 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
     auto TH = [&](int A, int n) -> double { return a.thom[((size_t)A * Ny + n) * sm + m]; };
 
     // this lane's chunk of the parity-p coefficients: n = p + 2 i, lo <= i < hi
-    const int ntop = N - ((N - p) & 1);
-    const int CH = (N / 2 + 1 + 7) >> 3;        // chunk length (parity 0 is the longer)
-    const int lo = j * CH, hi = min(lo + CH, (ntop - p) / 2 + 1);
-    const int ilo = max(lo, 1);                 // the recurrences start at i = 1
+    int lo, ilo, hi;
+    ks_chunk_range(N, p, j, lo, ilo, hi);
 
     const int nout = ((a.out_sel & 1) ? 3 : 0) + ((a.out_sel & 2) ? 6 : 0);
     const int kzi = m / nkx, kxi = m - kzi * nkx;
@@ -296,19 +335,9 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
         return v;
     };
 
-    // Right-hand-side-independent parts of this chunk's affine maps (the
-    // Thomas factors depend on k^2 only): the downward sweep
-    // X_n = B_n X_{n+2} + c_n maps the chunk's input X (just above it) to its
-    // lowest X by the product of B; the upward sweep P_n = Y_n P_{n-2} + X_n
-    // maps the input P (just below) to its highest P by the product of Y, and
-    // adds sum_n prod_{k <= n} Y_k times the input to the chunk's sum of P.
-    double Ab = 1.0, Hc = 1.0, SH = 0.0;
-    for (int i = ilo; i < hi; ++i) {
-        const int n = p + 2 * i;
-        Ab *= TH(2, n);
-        Hc *= TH(0, n);
-        SH += Hc;
-    }
+    // this chunk's right-hand-side-independent map parts (ks_chunk_mode)
+    const double* chk = a.chunk + (size_t)48 * m + p * 8 + j;
+    const double Ab = chk[0], Hc = chk[16], SH = chk[32];
 
     // rho_n of the tau recurrence for the series in A (own part), times rs
     auto rho = [&](int A, int n, T rs) -> T {
@@ -501,12 +530,35 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
     __syncwarp();
     // ---- stage 3: influence matrix from the divergence at both walls (FP64)
     if (!k0) {
-        double su = 0, sw = 0, sv = 0;
-        for (int i = lo; i < hi; ++i) {
-            const int n = p + 2 * i;
-            su += (double)SA(AU, r, n);
-            sw += (double)SA(AW, r, n);
-            sv += (double)(n * n) * (double)SA(AV, r, n);
+        // sums over the chunk: in FP64 plans in FP64; in FP32 plans the terms
+        // are FP32 values, summed with compensation (Kahan) in FP32, as
+        // accurate as an FP64 sum of the same terms and off the FP64 pipe
+        double su, sw, sv;
+        if constexpr (sizeof(T) == 8) {
+            su = sw = sv = 0;
+            for (int i = lo; i < hi; ++i) {
+                const int n = p + 2 * i;
+                su += SA(AU, r, n);
+                sw += SA(AW, r, n);
+                sv += (double)(n * n) * SA(AV, r, n);
+            }
+        } else {
+            float s3[3] = {0.f, 0.f, 0.f}, e3[3] = {0.f, 0.f, 0.f};
+            auto kadd = [&](int q, float v) {
+                const float y = v - e3[q];
+                const float t = s3[q] + y;
+                e3[q] = (t - s3[q]) - y;
+                s3[q] = t;
+            };
+            for (int i = lo; i < hi; ++i) {
+                const int n = p + 2 * i;
+                kadd(0, SA(AU, r, n));
+                kadd(1, SA(AW, r, n));
+                kadd(2, (float)(n * n) * SA(AV, r, n));
+            }
+            su = (double)s3[0] - (double)e3[0];
+            sw = (double)s3[1] - (double)e3[1];
+            sv = (double)s3[2] - (double)e3[2];
         }
         su = red8(su);
         sw = red8(sw);
@@ -540,20 +592,20 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
         dc p1 = -1.0 * (mi[0] * Cb + mi[sm] * Ct);
         dc p2 = -1.0 * (mi[2 * sm] * Cb + mi[3 * sm] * Ct);
         dc pp = p1 + sg * p2, pm = p1 - sg * p2;
-        const double* pbv = a.ksb + m;
-        const double* phv = a.ksb + (size_t)Ny * sm + m;
-        const double* vbv = a.ksb + (size_t)2 * Ny * sm + m;
+        const T* pbv = a.ksb + m;
+        const T* phv = a.ksb + (size_t)Ny * sm + m;
+        const T* vbv = a.ksb + (size_t)2 * Ny * sm + m;
         T ppr = (T)(r == 0 ? pp.x : pp.y), pmr = (T)(r == 0 ? pm.x : pm.y);
         T ppo = (T)(r == 0 ? pp.y : pp.x);       // other part of pp
         T ikf = r == 0 ? (T)-1 : (T)1;           // (i z)_r = ikf * z_other
         for (int i = lo; i < hi; ++i) {
             const int n = p + 2 * i;
             size_t o = (size_t)n * sm;
-            T ph = (T)phv[o];
+            const T ph = phv[o];
             SA(AU, r, n) += ikf * kx * ph * ppo;
             SA(AW, r, n) += ikf * kz * ph * ppo;
-            SA(AV, r, n) += (T)vbv[o] * pmr;
-            SA(AP, r, n) += (T)pbv[o] * ppr;
+            SA(AV, r, n) += vbv[o] * pmr;
+            SA(AP, r, n) += pbv[o] * ppr;
         }
     }
     __syncwarp();
@@ -602,11 +654,12 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_ks(KSArgs<T> a) {
 }
 
 template <typename T>
-cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const double* ksb,
+cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const T* ksb,
                      const double* minv, const double* coef, const double* thom,
-                     const double* isq, int out_sel, T* ocoef, cudaStream_t st) {
+                     const double* chunk, const double* isq, int out_sel, T* ocoef,
+                     cudaStream_t st) {
     const int nm = geo.Nz * geo.nkx;
-    KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, isq, out_sel, ocoef};
+    KSArgs<T> a{geo, fcoef, wall, ksb, minv, coef, thom, chunk, isq, out_sel, ocoef};
     // at most 3 x 257 T + 4 x (10 x 272 T + 6 x 257 FP64) = 137 KB (FP64, Ny = 257)
     cudaError_t e = grant_max_smem((const void*)k_ks<T>);
     if (e != cudaSuccess) return e;
@@ -615,12 +668,12 @@ cudaError_t ks_modes(const GridGeom& geo, const T* fcoef, const T* wall, const d
     return cudaGetLastError();
 }
 
-template cudaError_t ks_modes<float>(const GridGeom&, const float*, const float*, const double*,
+template cudaError_t ks_modes<float>(const GridGeom&, const float*, const float*, const float*,
                                      const double*, const double*, const double*,
-                                     const double*, int, float*, cudaStream_t);
+                                     const double*, const double*, int, float*, cudaStream_t);
 template cudaError_t ks_modes<double>(const GridGeom&, const double*, const double*,
                                       const double*, const double*, const double*,
-                                      const double*, const double*, int, double*,
-                                      cudaStream_t);
+                                      const double*, const double*, const double*, int,
+                                      double*, cudaStream_t);
 
 }  // namespace ggem

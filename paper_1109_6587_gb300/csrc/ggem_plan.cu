@@ -19,6 +19,7 @@ void ks_precompute_mode(int Ny, double W, double mu, double k2, double* pb, doub
                         double* vb, double* minv);
 void ks_coef_table(int Ny, double* tab);
 void ks_thomas_mode(int Ny, double lam, double* tab, double* isq);
+void ks_chunk_mode(int Ny, const double* tab, double* out);
 }
 
 namespace {
@@ -173,8 +174,8 @@ void run_global(ggem_plan_t* P, const SortedSources<T>& src, bool mesh, int out_
                               st, P->d_tc_err, P->nsm, P->d_tc_fwd));
     });
     stage(P, ST_KS, 1, [&] {
-        GG_CUDA(ks_modes<T>(geo, B, Wl, P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom, P->d_isq,
-                            out_sel, A, st));
+        GG_CUDA(ks_modes<T>(geo, B, Wl, (const T*)P->d_ksb, P->d_minv, P->d_kscoef, P->d_thom,
+                            P->d_kschunk, P->d_isq, out_sel, A, st));
     });
     int nout = nout_of(out_sel);
     if (P->offgrid == GGEM_OFFGRID_SPECTRAL) {
@@ -564,6 +565,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
     const int nm = P->nmodes;
     std::vector<double> ksb((size_t)3 * Ny * nm, 0.0), minv((size_t)4 * nm, 0.0);
     std::vector<double> thom((size_t)4 * Ny * nm, 0.0), isq((size_t)2 * nm, 0.0);
+    std::vector<double> kschunk((size_t)48 * nm, 0.0);
 #pragma omp parallel
     {
         std::vector<double> pb(Ny), ph(Ny), vb(Ny), th(4 * Ny);
@@ -578,6 +580,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             ks_thomas_mode(Ny, k2 * 0.25 * prm.W * prm.W, th.data(), iq);
             for (int c = 0; c < 4; ++c)
                 for (int n = 0; n < Ny; ++n) thom[((size_t)c * Ny + n) * nm + m] = th[c * Ny + n];
+            ks_chunk_mode(Ny, th.data(), kschunk.data() + (size_t)48 * m);
             isq[m] = iq[0];
             isq[nm + m] = iq[1];
             if (m == 0) continue;
@@ -596,9 +599,22 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
                        cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_isq, isq.data(), isq.size() * sizeof(double),
                        cudaMemcpyHostToDevice));
-    dalloc(P, &P->d_ksb, ksb.size());
+    dalloc(P, &P->d_kschunk, kschunk.size());
+    GG_CUDA(cudaMemcpy(P->d_kschunk, kschunk.data(), kschunk.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    // the homogeneous solutions in the plan's precision: the tau kernel adds
+    // them in T
+    if (P->fp64) {
+        dalloc(P, (double**)&P->d_ksb, ksb.size());
+        GG_CUDA(cudaMemcpy(P->d_ksb, ksb.data(), ksb.size() * sizeof(double),
+                           cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> kf(ksb.begin(), ksb.end());
+        dalloc(P, (float**)&P->d_ksb, kf.size());
+        GG_CUDA(cudaMemcpy(P->d_ksb, kf.data(), kf.size() * sizeof(float),
+                           cudaMemcpyHostToDevice));
+    }
     dalloc(P, &P->d_minv, minv.size());
-    GG_CUDA(cudaMemcpy(P->d_ksb, ksb.data(), ksb.size() * sizeof(double), cudaMemcpyHostToDevice));
     GG_CUDA(cudaMemcpy(P->d_minv, minv.data(), minv.size() * sizeof(double),
                        cudaMemcpyHostToDevice));
 
@@ -723,7 +739,7 @@ void plan_free(ggem_plan_t* P) {
     }
     void* ptrs[] = {P->d_yj, P->d_cheb_fwd, P->d_cheb_inv, P->d_tw_x, P->d_tw_z, P->d_ksb,
                     P->d_minv, P->d_ydiff, P->d_sdi, P->d_sdf, P->d_mesh_sdi, P->d_mesh_sdf,
-                    P->d_kscoef, P->d_thom, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall,
+                    P->d_kscoef, P->d_thom, P->d_kschunk, P->d_isq, P->d_gridA, P->d_gridB, P->d_wall,
                     P->d_cell_count, P->d_cell_start, P->d_cursor, P->d_src_cell,
                     P->d_perm, P->d_spos, P->d_sg, P->d_src_x, P->d_local, P->d_in0, P->d_in1,
                     P->d_in2, P->d_out0, P->d_out1, P->d_tgt_cell, P->d_tgt_pos,

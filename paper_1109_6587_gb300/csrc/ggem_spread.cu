@@ -352,9 +352,71 @@ __global__ void k_red_probe(float4* __restrict__ buf, unsigned nvec, int iters, 
         atomicAdd(buf + base + lane, make_float4(1.f, 1.f, 1.f, 0.f));
     }
 }
+
+// Throughput of FP32 atomic adds into shared memory, the operation a spreading
+// staged in shared memory would be bound by: a block holds a tile of 4096
+// nodes x 3 components (48 KB, as a 16 x 16 x 16 tile of the grid), and every
+// warp adds into 32 consecutive nodes (one per lane: no bank conflict within
+// the warp) of each component at a pseudo-random place of the tile, `iters`
+// times; the warps of a block collide as the sources of a tile would.  The
+// tile is added into `out` at the end so that the adds are kept.
+constexpr int kProbeNodes = 4096;
+__global__ void k_smem_probe(float* __restrict__ out, int iters, unsigned seed) {
+    __shared__ float acc[3 * kProbeNodes];
+    for (int e = threadIdx.x; e < 3 * kProbeNodes; e += blockDim.x) acc[e] = 0.f;
+    __syncthreads();
+    const unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    unsigned h = (w + 1u) * 2654435761u ^ seed;
+    for (int it = 0; it < iters; ++it) {
+        h = h * 1664525u + 1013904223u;
+        const unsigned base = ((h >> 8) % (kProbeNodes >> 5)) << 5;
+        atomicAdd(&acc[base + lane], 1.f);
+        atomicAdd(&acc[kProbeNodes + base + lane], 1.f);
+        atomicAdd(&acc[2 * kProbeNodes + base + lane], 1.f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * kProbeNodes; e += blockDim.x) atomicAdd(out + e, acc[e]);
+}
 }  // namespace
 
 }  // namespace ggem
+
+extern "C" ggem_status ggem_probe_smem_reduction(int iters, void* stream, double* ms,
+                                                 double* adds_per_s) {
+    if (iters < 1 || iters > (1 << 20) || !ms || !adds_per_s) return GGEM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GGEM_ERR_CUDA;
+    const size_t nout = (size_t)3 * ggem::kProbeNodes;
+    float* out = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ggem_status s = GGEM_OK;
+    if (cudaMalloc((void**)&out, nout * sizeof(float)) != cudaSuccess) return GGEM_ERR_CUDA;
+    const int blocks = 4 * nsm, threads = 256;     // 48 KB per block: 4 blocks per SM
+    if (cudaMemsetAsync(out, 0, nout * sizeof(float), st) != cudaSuccess ||
+        cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        s = GGEM_ERR_CUDA;
+    } else {
+        ggem::k_smem_probe<<<blocks, threads, 0, st>>>(out, iters, 7u);  // warm
+        cudaEventRecord(a, st);
+        ggem::k_smem_probe<<<blocks, threads, 0, st>>>(out, iters, 11u);
+        cudaEventRecord(b, st);
+        float t = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess) {
+            s = GGEM_ERR_CUDA;
+        } else {
+            *ms = t;
+            *adds_per_s = 3.0 * blocks * threads * iters / (t * 1e-3);
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(out);
+    return s;
+}
 
 extern "C" ggem_status ggem_probe_l2_reduction(long nvec, int iters, void* stream, double* ms,
                                                double* vec_per_s) {

@@ -54,7 +54,8 @@ EXPORTS = ["ggem_plan", "ggem_plan_destroy", "ggem_last_error", "ggem_plan_info"
            "ggem_particle_volumes", "ggem_volume_correct", "ggem_overlap_correct",
            "ggem_set_offgrid", "ggem_mlp_precision", "ggem_precond_set",
            "ggem_precond_enable", "ggem_precond_block", "ggem_inject_tc_wait_expiry",
-           "ggem_mlp_adam_state", "ggem_probe_l2_reduction"]
+           "ggem_mlp_adam_state", "ggem_probe_l2_reduction",
+           "ggem_probe_smem_reduction"]
 
 GGEM_OFFGRID = {"lagrange": 0, "spectral": 1}
 
@@ -122,6 +123,7 @@ def lib():
         L.ggem_inject_tc_wait_expiry.argtypes = [ctypes.c_long]
         L.ggem_probe_l2_reduction.argtypes = [ctypes.c_long, I, P, ctypes.POINTER(D),
                                               ctypes.POINTER(D)]
+        L.ggem_probe_smem_reduction.argtypes = [I, P, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.ggem_mlp_adam_state.argtypes = [P, I, P, P, ctypes.POINTER(ctypes.c_longlong)]
         L.ggem_mlp_save.argtypes = [P, P, ctypes.c_size_t]
         L.ggem_mlp_forward.argtypes = [P, I, P, P]
@@ -646,4 +648,15 @@ def probe_l2_reduction(nvec=1 << 21, iters=256, stream=None):
                                        ctypes.byref(ms), ctypes.byref(rate))
     if st != 0:
         raise GGEMError(st, "L2 reduction probe failed")
+    return ms.value, rate.value
+
+
+def probe_smem_reduction(iters=4096, stream=None):
+    """Throughput of FP32 atomic adds into shared memory
+    (ggem_probe_smem_reduction): (milliseconds, scalar adds per second)."""
+    ms, rate = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().ggem_probe_smem_reduction(int(iters), ctypes.c_void_p(stream or 0),
+                                         ctypes.byref(ms), ctypes.byref(rate))
+    if st != 0:
+        raise GGEMError(st, "shared-memory reduction probe failed")
     return ms.value, rate.value
