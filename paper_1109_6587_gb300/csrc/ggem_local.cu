@@ -222,18 +222,24 @@ cudaError_t locate_targets(const GridGeom& geo, const CellGrid& cg, int n, int k
 
 // Pair arithmetic of Eq. (local), shared by the local-sum kernels.
 // exp(-alpha^2 r^2) and erfc(alpha r) = exp(-x^2) erfcx(x) with the
-// polynomials of ggem_erfcx.cuh (FP32: degree 14; FP64: 8 pieces of degree 12,
-// coefficients in shared memory), so the pair needs one exponential and no
-// erfc call; the FP32 exponential is 2^(ke r^2).
+// approximations of ggem_erfcx.cuh (FP32: t Q(t), t = 1/(1 + P x), Q of degree
+// 7; FP64: 8 polynomial pieces of degree 12, coefficients in shared memory),
+// so the pair needs one exponential and no erfc call; the FP32 exponential is
+// 2^(ke r^2), the FP32 reciprocal the hardware's.
 template <typename T> struct PairAcc {
     T ux = 0, uy = 0, uz = 0;
     T sxx = 0, sxy = 0, sxz = 0, syy = 0, syz = 0, szz = 0;
 };
 
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ void exp_erfc(const LocalConst<float>& k, float r2, float x, float& ex,
                                          float& ec, const double*) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(k.ke * r2));
-    ec = ex * erfcx_poly(x);
+    ec = ex * erfcx_t(rcp_ftz(fmaf(x, GGEM_ERFCX_P, 1.0f)));
 }
 __device__ __forceinline__ void exp_erfc(const LocalConst<double>& k, double r2, double x,
                                          double& ex, double& ec, const double* tab) {
@@ -312,8 +318,9 @@ __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f
     const f2 r = r2 * ir;
     f2_split(f2_splat(k.ke) * r2, lo, hi);
     const f2 ex = f2_make(ex2_ftz(lo), ex2_ftz(hi));                 // exp(-alpha^2 r^2)
-    const f2 u = fma2(r, f2_splat(0.5f * k.al), f2_splat(-1.0f));  // alpha r / 2 - 1
-    const f2 ec = ex * erfcx_poly2(u);                               // erfc(alpha r)
+    f2_split(fma2(r, f2_splat(GGEM_ERFCX_P * k.al), f2_splat(1.0f)), lo, hi);
+    const f2 t = f2_make(rcp_ftz(lo), rcp_ftz(hi));                 // 1/(1 + P alpha r)
+    const f2 ec = ex * erfcx_t2(t);                                  // erfc(alpha r)
     const f2 xg = fma2(dz, gz, fma2(dy, gy, dx * gx));
     if (MODE & OUT_U) {
         // A = ec/r - c1 ex,  B = (ec/r^3 + c1 ex/r^2) xg

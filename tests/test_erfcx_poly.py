@@ -1,11 +1,10 @@
-"""The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the polynomials of
-ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff): degree 14 (FP32),
-8 pieces of degree 12 (FP64).  FP32:
-Its coefficients, read from the generated header, must approximate scipy's
-erfcx to 2e-7 relative in FP64 (the approximation error is kept near the
-rounding error of the polynomial's own FP32 evaluation, ~2e-7, so neither
-dominates) and to 4e-7 (a few FP32 ulps, like CUDA's erfcf) when evaluated in
-FP32 by the same Horner scheme."""
+"""The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the approximations
+of ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff).  FP32:
+erfcx(x) ~ t Q(t), t = 1/(1 + P x), Q of degree 7 in t.  Its coefficients, read
+from the generated header, must approximate scipy's erfcx to 2e-8 relative in
+FP64 and to 5e-7 (a few FP32 ulps, like CUDA's erfcf) when t and the Horner
+scheme are evaluated in FP32 (the rounding of t dominates).  FP64: 8 pieces of
+degree 12."""
 import pathlib
 import re
 
@@ -19,9 +18,13 @@ HDR = pathlib.Path(__file__).resolve().parents[1] / "paper_1109_6587_gb300" / "c
 
 def _coefficients():
     txt = HDR.read_text()
-    first = re.search(r"float p = ([-+0-9.eE]+)f;", txt).group(1)
-    rest = re.findall(r"p = fmaf\(p, u, ([-+0-9.eE]+)f\);", txt)
+    first = re.search(r"float q = ([-+0-9.eE]+)f;", txt).group(1)
+    rest = re.findall(r"q = fmaf\(q, t, ([-+0-9.eE]+)f\);", txt)
     return [float(first)] + [float(v) for v in rest]    # highest degree first
+
+
+def _p():
+    return float(re.search(r"#define GGEM_ERFCX_P ([0-9.]+)f", HDR.read_text()).group(1))
 
 
 def _table64():
@@ -32,20 +35,22 @@ def _table64():
 
 def test_polynomial_error():
     c = _coefficients()
-    assert len(c) == 15
+    assert len(c) == 8
+    p = _p()
     x = np.linspace(0.0, 4.0, 100001)
     ref = special.erfcx(x)
-    u = x / 2 - 1
-    p = np.full_like(u, c[0])
+    t = 1.0 / (1.0 + p * x)
+    q = np.full_like(t, c[0])
     for a in c[1:]:
-        p = p * u + a
-    assert np.abs(p / ref - 1).max() < 2e-7
+        q = q * t + a
+    assert np.abs(q * t / ref - 1).max() < 2e-8
     x32 = x.astype(np.float32)
-    u32 = (x32 * np.float32(0.5) - np.float32(1)).astype(np.float32)
-    p32 = np.full_like(u32, np.float32(c[0]))
+    t32 = (np.float32(1) / (np.float32(p) * x32 + np.float32(1))).astype(np.float32)
+    q32 = np.full_like(t32, np.float32(c[0]))
     for a in c[1:]:
-        p32 = (p32 * u32 + np.float32(a)).astype(np.float32)
-    assert np.abs(p32.astype(np.float64) / ref - 1).max() < 4e-7
+        q32 = (q32 * t32 + np.float32(a)).astype(np.float32)
+    q32 = (q32 * t32).astype(np.float32)
+    assert np.abs(q32.astype(np.float64) / ref - 1).max() < 5e-7
 
 
 def test_polynomial_error_fp64():
@@ -68,6 +73,6 @@ def test_polynomial_error_fp64():
 def test_paired_polynomial_has_the_same_coefficients():
     # the paired-lane copy used by the FP32 element-rule kernel
     txt = HDR.read_text()
-    first = re.search(r"f2 p = f2_splat\(([-+0-9.eE]+)f\);", txt).group(1)
-    rest = re.findall(r"p = fma2\(p, u, f2_splat\(([-+0-9.eE]+)f\)\);", txt)
+    first = re.search(r"f2 q = f2_splat\(([-+0-9.eE]+)f\);", txt).group(1)
+    rest = re.findall(r"q = fma2\(q, t, f2_splat\(([-+0-9.eE]+)f\)\);", txt)
     assert [float(first)] + [float(v) for v in rest] == _coefficients()
