@@ -179,9 +179,7 @@ FLOPS_PAIR_DOUBLE = 75
 # kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum; the
 # summaries are kept with the profiles), per (workload, precision, quadrature);
 # none for other configurations
-LOCAL_TRAFFIC = {
-    ("rbc4000", "mixed", "element"): (3816876032 + 41026560 + 4464229888 + 95442944) / 2,
-}
+LOCAL_TRAFFIC = {}
 
 SAMPLE_ABOVE = 100_000      # larger workloads count pairs on a sample of targets
 SAMPLE_TARGETS = 20_000

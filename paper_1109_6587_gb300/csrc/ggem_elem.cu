@@ -51,11 +51,12 @@ __global__ void k_qp_gen(int m, const double* __restrict__ x, const int* __restr
 // strengths of the sorted quadrature points: g = scale * sum_v (phi_v w) q_v,
 // from the vertex indices and weights already in point order (qv, qw); into
 // interleaved v4 (g) or, for the FP32 element rule, straight into the
-// structure-of-arrays planes x, y, z of stride ld (soa)
+// structure-of-arrays planes x, y, z of stride ld (soa) at the padded slot
+// pidx[s] of each point
 template <typename T>
 __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>* __restrict__ qw,
                               const double* __restrict__ q, double scale, v4_t<T>* __restrict__ g,
-                              T* __restrict__ soa, size_t ld) {
+                              T* __restrict__ soa, size_t ld, const int* __restrict__ pidx) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int4 v = qv[s];
@@ -65,9 +66,10 @@ __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>*
     T ry = (T)(a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1]);
     T rz = (T)(a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2]);
     if (soa) {
-        soa[s] = rx;
-        soa[ld + s] = ry;
-        soa[2 * ld + s] = rz;
+        const int p = pidx[s];
+        soa[p] = rx;
+        soa[ld + p] = ry;
+        soa[2 * ld + p] = rz;
     } else {
         v4_t<T> r;
         r.x = rx; r.y = ry; r.z = rz; r.w = (T)0;
@@ -255,9 +257,12 @@ cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, 
 
 template <typename T>
 cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
-                         double scale, v4_t<T>* g, T* soa, size_t ld, cudaStream_t st) {
+                         double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
+                         cudaStream_t st) {
+    if (soa && !pidx) return cudaErrorInvalidValue;
     if (nq > 0)
-        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, q, scale, g, soa, ld);
+        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, q, scale, g, soa, ld,
+                                                          pidx);
     return cudaGetLastError();
 }
 
@@ -279,7 +284,8 @@ cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x,
                                        int*, int*, int*, cudaStream_t);                         \
     template cudaError_t qp_sort_weights<T>(int, const int*, v4_t<T>*, v4_t<T>*, cudaStream_t); \
     template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, const double*,      \
-                                         double, v4_t<T>*, T*, size_t, cudaStream_t);          \
+                                         double, v4_t<T>*, T*, size_t, const int*,             \
+                                         cudaStream_t);                                        \
     template cudaError_t elem_correct<T>(int, int, const GridGeom&, const double*, const int*, \
                                          const double*, const double*, const int*, const int*,  \
                                          const double*, const QuadRule&, T*, int, cudaStream_t);

@@ -233,9 +233,12 @@ struct ggem_plan {
     bool ff = false;                   // element-rule local sum in double-float arithmetic
     void* d_qp_ff = nullptr;           // [cap_qp][2] float4: sorted point offsets, hi / lo
     void* d_qg_ff = nullptr;           // [cap_qp][2] float4: sorted point strengths, hi / lo
-    float* d_qp_soa = nullptr;         // [3][soa_ld] FP32 plans: sorted point offsets x, y, z
-    float* d_qg_soa = nullptr;         // [3][soa_ld] FP32 plans: sorted point strengths
-    size_t soa_ld = 0;                 // plane stride: cap_qp + one padded step, even
+    float* d_qp_soa = nullptr;         // [3][soa_ld] FP32 plans: point offsets x, y, z (padded layout)
+    float* d_qg_soa = nullptr;         // [3][soa_ld] FP32 plans: point strengths (padded layout)
+    size_t soa_ld = 0;                 // plane stride: at least the padded size, a multiple of 64
+    int* d_qp_pstart = nullptr;        // [ncell + 1] FP32 plans: padded cell starts
+    int* d_qp_pidx = nullptr;          // [cap_qp] sorted point -> padded slot
+    int* d_qp_inv = nullptr;           // [soa_ld] padded slot -> sorted point, -1 for dummies
     int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
     double* d_orecd = nullptr;         // [4 cap] overlap records: node gap
     int* d_ocount = nullptr;           // record count
@@ -325,13 +328,22 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
                            cudaStream_t st, const void* aux_pos = nullptr,
-                           const void* aux_g = nullptr, size_t aux_ld = 0);
+                           const void* aux_g = nullptr, size_t aux_ld = 0,
+                           const int* aux_inv = nullptr);
+// FP32 element rule, padded layout of the sorted points (each cell from a
+// multiple of 64, whole 64-point steps, dummies of zero strength far away):
+// padded counts and starts (pcnt: ncell scratch, pstart: ncell + 1), then the
+// position planes (dummies at 1e4), zeroed strength planes, and the maps
+// sorted point -> padded slot (pidx) and slot -> point (inv, -1 for dummies)
+cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstart,
+                              cudaStream_t st);
+cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
+                            const int* pstart, const float4* pos, float* pos_soa, float* g_soa,
+                            size_t ld, int* pidx, int* inv, cudaStream_t st);
 // FP32 element rule: sub-sort the sorted points within each cell (4 x 4 x 4
 // sub-cells in Morton order; tmp_* of n entries as scratch)
 cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start, float4* pos,
                          int* perm, float4* tmp_pos, int* tmp_perm, cudaStream_t st);
-// structure-of-arrays planes (x, y, z; stride ld) of n float4 values
-cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st);
 // float-pair copy of n double4 (x, y, z, w) values: out[2 i] = hi, out[2 i + 1] = lo
 cudaError_t to_float_pairs(int n, const void* in, void* out, cudaStream_t st);
 cudaError_t gather_int4(int n, const int* perm, const int4* in, int4* out, cudaStream_t st);
@@ -349,10 +361,12 @@ cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri
 template <typename T>
 cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, cudaStream_t st);
 // sorted point strengths g = scale sum_v (phi_v w) q_v from the sorted vertex
-// indices and weights: into g (v4), or into the planes soa[0, ld, 2 ld] if soa
+// indices and weights: into g (v4), or into the planes soa[0, ld, 2 ld] at the
+// padded slots pidx[s] if soa
 template <typename T>
 cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
-                         double scale, v4_t<T>* g, T* soa, size_t ld, cudaStream_t st);
+                         double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
+                         cudaStream_t st);
 // polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double)
 template <typename T>
 cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x, const int* tri,

@@ -8,6 +8,8 @@
 // +-R cells carries the image; as r_cut < L/2 (Sec. 3.2.2, alpha L > 8), at
 // most one image of a source lies within r_cut even where a small grid
 // visits a cell twice.
+#include <type_traits>
+
 #include "ggem_internal.cuh"
 #include "ggem_erfcx.cuh"
 #include "ggem_ff.cuh"
@@ -185,6 +187,7 @@ template <typename T> struct LocalArgs {
     const double* nrm;       // OUT_DBL: [n][3] target normals (caller order)
     T* out;
     int out_stride;
+    const int* qinv = nullptr;   // FP32 element rule: padded slot -> sorted point (-1: dummy)
 };
 
 // Locate targets once (one thread each, FP64): cell index and offsets from
@@ -441,7 +444,9 @@ __device__ __forceinline__ int cull_cells(const LocalArgs<T>& a, int lane, T ox,
 
 // The same culling in batches: rounds of 32 neighbour offsets from *round
 // on, stopping before a round could overflow `cap` entries; *round is left at
-// the first round not culled (nb rounds = done).
+// the first round not culled (nb rounds = done).  Bit 15 of s_off marks the
+// cells within near2 of the target (the only ones that can hold points of
+// the triangles around it).
 template <typename T, int R>
 __device__ __forceinline__ int cull_cells_batch(const LocalArgs<T>& a, int lane, T ox, T oy,
                                                 T oz, int cx, int cy, int cz, int* s_cst,
@@ -454,7 +459,7 @@ __device__ __forceinline__ int cull_cells_batch(const LocalArgs<T>& a, int lane,
     int nc = 0;
     for (; round < nr && nc + 32 <= cap; ++round) {
         const int oi = round * 32 + lane;
-        bool keep = false;
+        bool keep = false, nearc = false;
         int st = 0, cnt = 0;
         if (oi < nb) {
             const int ix = oi % side - R, iy = (oi / side) % side - R, iz = oi / (side * side) - R;
@@ -463,7 +468,9 @@ __device__ __forceinline__ int cull_cells_batch(const LocalArgs<T>& a, int lane,
                 const T gx = ix > 0 ? (T)ix * a.k.hx - ox : (ix < 0 ? ox - (T)(ix + 1) * a.k.hx : (T)0);
                 const T gy = iy > 0 ? (T)iy * a.k.hy - oy : (iy < 0 ? oy - (T)(iy + 1) * a.k.hy : (T)0);
                 const T gz = iz > 0 ? (T)iz * a.k.hz - oz : (iz < 0 ? oz - (T)(iz + 1) * a.k.hz : (T)0);
-                if (gx * gx + gy * gy + gz * gz <= reach2) {
+                const T d2 = gx * gx + gy * gy + gz * gz;
+                nearc = d2 <= a.near2 * (T)1.0001;
+                if (d2 <= reach2) {
                     int cxx = cx + ix, czz = cz + iz;
                     cxx += (cxx < 0) ? cg.ncx : 0;
                     cxx -= (cxx >= cg.ncx) ? cg.ncx : 0;
@@ -481,7 +488,7 @@ __device__ __forceinline__ int cull_cells_batch(const LocalArgs<T>& a, int lane,
             const int slot = nc + __popc(m & lt);
             s_cst[slot] = st;
             s_cnt[slot] = cnt;
-            s_off[slot] = (unsigned short)oi;
+            s_off[slot] = (unsigned short)(oi | (nearc ? 0x8000 : 0));
         }
         nc += __popc(m);
     }
@@ -623,14 +630,19 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 
 // ------------------------------------------------- FP32 element rule
 // The element-rule local sum in FP32 reads ~700 quadrature points per cell
-// and evaluates about 80 % of them, so no hit queue: every lane takes two
-// adjacent candidates of each 64-point step through a cell and evaluates both
-// with paired FP32 arithmetic; a miss contributes nothing (its strength is
-// zero, and every term carries a factor g).  The points are read from
-// structure-of-arrays copies (x, y, z and gx, gy, gz planes of stride ld), so
+// and finds about 80 % of them within r_cut, so no hit queue: every lane
+// takes two adjacent candidates of each 64-point step through a cell and
+// evaluates both with paired FP32 arithmetic.  The points are read from
+// structure-of-arrays copies (x, y, z and gx, gy, gz planes of stride ld) in
+// a padded layout: each cell starts on a multiple of 64 and fills whole steps
+// with dummies of zero strength far away, so a step needs no bounds test and
 // one 8-byte load brings a coordinate of both candidates already paired.
-// Steps start at even sorted indices (8-byte alignment); slots outside the cell
-// are masked like misses (the planes are padded by one step, zero-filled).
+// Candidates beyond r_cut are evaluated unmasked: their terms carry
+// exp(-alpha^2 r^2) <= e^-16 (and erfc(alpha r) <= 1.6e-8), below the FP32
+// rounding of the sum, and a step with no candidate within r_cut is skipped.
+// Points of the triangles around the target (left to the singular
+// correction) can only lie in the cells the culling marks near; only there
+// is each candidate within near2 checked and, if excluded, given zero strength.
 constexpr int LWE = 8;        // warps (targets) per block; 5 blocks per SM (48 registers)
 constexpr int kCap = 128;     // culled cells per batch (a target may need several batches)
 constexpr int kChunk = 64;    // candidates per warp step
@@ -667,37 +679,49 @@ __global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a
     const int nc = cull_cells_batch<float, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid],
                                               s_cnt[wid], s_off[wid], round, kCap);
     for (int ci = 0; ci < nc; ++ci) {
-        const int st = s_cst[wid][ci], end = st + s_cnt[wid][ci], oi = s_off[wid][ci];
+        const int st = s_cst[wid][ci], end = st + s_cnt[wid][ci];
+        const int oi = s_off[wid][ci] & 0x7fff;
+        const bool nearc = s_off[wid][ci] >> 15;
         // target position in the frame of this source cell's corner
         const f2 tx = f2_splat(ox - (float)(oi % side - R) * a.k.hx);
         const f2 ty = f2_splat(oy - (float)((oi / side) % side - R) * a.k.hy);
         const f2 tz = f2_splat(oz - (float)(oi / (side * side) - R) * a.k.hz);
-        for (int i0 = st & ~1; i0 < end; i0 += kChunk) {
+        // one 64-point step; NEAR: check for points of the target's own triangles
+        auto step = [&](int i0, auto near_tag) {
+            constexpr bool NEAR = decltype(near_tag)::value;
             const int i = i0 + 2 * lane;          // even: candidates i and i + 1
             const int h = i >> 1;
             const float2 qx = px[h], qy = py[h], qz = pz[h];
             const f2 dx = tx - f2_make(qx.x, qx.y), dy = ty - f2_make(qy.x, qy.y),
                      dz = tz - f2_make(qz.x, qz.y);
-            f2 r2 = fma2(dz, dz, fma2(dy, dy, dx * dx));
+            const f2 r2 = fma2(dz, dz, fma2(dy, dy, dx * dx));
             float r0, r1;
             f2_split(r2, r0, r1);
-            bool h0 = i >= st && i < end && r0 < rc2;
-            bool h1 = i + 1 >= st && i + 1 < end && r1 < rc2;
-            if (h0 && r0 < a.near2) {
-                const int4 v = a.qvs[i];
-                h0 = !(v.x == oidx || v.y == oidx || v.z == oidx);
+            if (!__any_sync(0xffffffffu, r0 < rc2 || r1 < rc2)) return;
+            float2 wx = gx[h], wy = gy[h], wz = gz[h];
+            if (NEAR) {
+                if (r0 < a.near2) {
+                    const int s = a.qinv[i];
+                    if (s >= 0) {
+                        const int4 v = a.qvs[s];
+                        if (v.x == oidx || v.y == oidx || v.z == oidx) wx.x = wy.x = wz.x = 0.f;
+                    }
+                }
+                if (r1 < a.near2) {
+                    const int s = a.qinv[i + 1];
+                    if (s >= 0) {
+                        const int4 v = a.qvs[s];
+                        if (v.x == oidx || v.y == oidx || v.z == oidx) wx.y = wy.y = wz.y = 0.f;
+                    }
+                }
             }
-            if (h1 && r1 < a.near2) {
-                const int4 v = a.qvs[i + 1];
-                h1 = !(v.x == oidx || v.y == oidx || v.z == oidx);
-            }
-            if (!__any_sync(0xffffffffu, h0 || h1)) continue;
-            // misses: zero strength and an in-range r^2 (selects, off the FMA pipe)
-            r2 = f2_make(h0 ? r0 : rc2, h1 ? r1 : rc2);
-            const float2 wx = gx[h], wy = gy[h], wz = gz[h];
-            pair_terms2<MODE>(a.k, dx, dy, dz, r2, f2_make(h0 ? wx.x : 0.f, h1 ? wx.y : 0.f),
-                              f2_make(h0 ? wy.x : 0.f, h1 ? wy.y : 0.f),
-                              f2_make(h0 ? wz.x : 0.f, h1 ? wz.y : 0.f), nx2, ny2, nz2, acc);
+            pair_terms2<MODE>(a.k, dx, dy, dz, r2, f2_make(wx.x, wx.y), f2_make(wy.x, wy.y),
+                              f2_make(wz.x, wz.y), nx2, ny2, nz2, acc);
+        };
+        if (nearc) {
+            for (int i0 = st; i0 < end; i0 += kChunk) step(i0, std::true_type{});
+        } else {
+            for (int i0 = st; i0 < end; i0 += kChunk) step(i0, std::false_type{});
         }
     }
     __syncwarp();
@@ -761,16 +785,6 @@ __global__ void k_cell_subsort(const int* __restrict__ start, const float4* __re
         pos_out[slot] = p;
         perm_out[slot] = perm[st + i];
     }
-}
-
-// structure-of-arrays copy of n float4 (x, y, z, w): planes x, y, z of stride ld
-__global__ void k_to_soa(int n, const float4* __restrict__ in, float* __restrict__ out, size_t ld) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float4 v = in[i];
-    out[i] = v.x;
-    out[ld + i] = v.y;
-    out[2 * ld + i] = v.z;
 }
 
 // ----------------------------------- element rule, FP64-accurate in float pairs
@@ -1004,8 +1018,57 @@ cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start,
     return cudaGetLastError();
 }
 
-cudaError_t to_soa(int n, const void* in, float* out, size_t ld, cudaStream_t st) {
-    if (n > 0) k_to_soa<<<(n + 255) / 256, 256, 0, st>>>(n, (const float4*)in, out, ld);
+// Padded structure-of-arrays layout of the sorted points for the FP32 element
+// rule: each cell's points start on a multiple of 64 and fill whole 64-point
+// steps; the slots after a cell's last point hold dummies (offset 1e4 from the
+// cell corner, strength zero), whose terms are exactly zero.
+__global__ void k_pad_counts(int ncell, const int* __restrict__ start, int* __restrict__ pcnt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) pcnt[c] = (start[c + 1] - start[c] + 63) & ~63;
+}
+
+__global__ void k_pad_fill(size_t np, float v, float* __restrict__ out, size_t ld) {
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    out[p] = v;
+    out[ld + p] = v;
+    out[2 * ld + p] = v;
+}
+
+__global__ void k_pad_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
+                              const int* __restrict__ pstart, const float4* __restrict__ pos,
+                              float* __restrict__ out, size_t ld, int* __restrict__ pidx,
+                              int* __restrict__ inv) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int c = cell[s];
+    const int p = pstart[c] + (s - start[c]);
+    const float4 v = pos[s];
+    out[p] = v.x;
+    out[ld + p] = v.y;
+    out[2 * ld + p] = v.z;
+    pidx[s] = p;
+    inv[p] = s;
+}
+
+cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstart,
+                              cudaStream_t st) {
+    if (ncell <= 0) return cudaSuccess;
+    k_pad_counts<<<(ncell + 255) / 256, 256, 0, st>>>(ncell, start, pcnt);
+    return scan_counts(ncell, pcnt, pstart, st);
+}
+
+cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
+                            const int* pstart, const float4* pos, float* pos_soa, float* g_soa,
+                            size_t ld, int* pidx, int* inv, cudaStream_t st) {
+    if (np > 0) {
+        k_pad_fill<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(np, 1e4f, pos_soa, ld);
+        cudaMemsetAsync(g_soa, 0, 3 * ld * sizeof(float), st);
+        cudaMemsetAsync(inv, 0xff, np * sizeof(int), st);
+    }
+    if (n > 0)
+        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pos_soa, ld,
+                                                      pidx, inv);
     return cudaGetLastError();
 }
 
@@ -1020,14 +1083,15 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
                            const int4* qvs, double near, const SortedSources<T>& tgt,
                            const double* nrm_tgt, int layer, T* out, int out_stride,
                            cudaStream_t st, const void* aux_pos, const void* aux_g,
-                           size_t aux_ld) {
+                           size_t aux_ld, const int* aux_inv) {
     if (tgt.n <= 0) return cudaSuccess;
     // targets: the mesh nodes in cell order, so the warps of a block mostly
     // scan the same candidate cells (L1 reuse); output in caller order
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
                    tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
     if constexpr (sizeof(T) == 4) {
-        if (!aux_pos || !aux_g || aux_ld == 0) return cudaErrorInvalidValue;
+        if (!aux_pos || !aux_g || aux_ld == 0 || !aux_inv) return cudaErrorInvalidValue;
+        a.qinv = aux_inv;
         const float* ps = (const float*)aux_pos;
         const float* gs = (const float*)aux_g;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
@@ -1102,7 +1166,8 @@ cudaError_t local_sum(const GridGeom& geo, const CellGrid& cg, const SortedSourc
     template cudaError_t local_sum_elem<T>(const GridGeom&, const CellGrid&,                  \
                                            const SortedSources<T>&, const int4*, double,        \
                                            const SortedSources<T>&, const double*, int, T*, int, \
-                                           cudaStream_t, const void*, const void*, size_t);
+                                           cudaStream_t, const void*, const void*, size_t, \
+                                           const int*);
 GGEM_INST_LOCAL(float)
 GGEM_INST_LOCAL(double)
 

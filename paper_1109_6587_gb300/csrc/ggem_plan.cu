@@ -318,7 +318,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         if (elem)
             GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, q,
                                     8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
-                                    P->fp64 ? nullptr : (T*)P->d_qg_soa, P->soa_ld, st));
+                                    P->fp64 ? nullptr : (T*)P->d_qg_soa, P->soa_ld,
+                                    P->d_qp_pidx, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
@@ -356,13 +357,14 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         qs.g = (v4_t<T>*)P->d_qg;
         qs.cell = P->d_qp_cell;
         qs.perm = P->d_qp_perm;
-        qs.cell_start = P->d_qp_start;
+        qs.cell_start = P->fp64 ? P->d_qp_start : P->d_qp_pstart;   // FP32: padded layout
         qs.n = P->n_qp;
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
                                       P->d_nrm, layer, loc, 3, ls,
                                       P->fp64 ? P->d_qp_ff : (void*)P->d_qp_soa,
-                                      P->fp64 ? P->d_qg_ff : (void*)P->d_qg_soa, P->soa_ld));
+                                      P->fp64 ? P->d_qg_ff : (void*)P->d_qg_soa, P->soa_ld,
+                                      P->d_qp_inv));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
@@ -708,12 +710,13 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             GG_CUDA(cudaMalloc(&P->d_qp_ff, cq * 2 * sizeof(float4) + 32));
             GG_CUDA(cudaMalloc(&P->d_qg_ff, cq * 2 * sizeof(float4) + 32));
         }
-        if (!P->fp64) {                    // planes padded by one 64-point step, zeroed
-            P->soa_ld = (cq + 64 + 63) / 64 * 64;
+        if (!P->fp64) {                    // padded planes; grown at mesh_set if needed
+            P->soa_ld = (cq + cq / 8 + 64 + 63) / 64 * 64;
             dalloc(P, &P->d_qp_soa, 3 * P->soa_ld);
             dalloc(P, &P->d_qg_soa, 3 * P->soa_ld);
-            GG_CUDA(cudaMemset(P->d_qp_soa, 0, 3 * P->soa_ld * sizeof(float)));
-            GG_CUDA(cudaMemset(P->d_qg_soa, 0, 3 * P->soa_ld * sizeof(float)));
+            dalloc(P, &P->d_qp_inv, P->soa_ld);
+            dalloc(P, &P->d_qp_pidx, cq);
+            dalloc(P, &P->d_qp_pstart, (size_t)P->ncell + 1);
         }
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
@@ -760,7 +763,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
                     P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
                     P->d_spec_dz, P->d_spec_mid, P->d_spec_ct, P->d_mlp_tc,
-                    P->d_mlp_tcs};
+                    P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_pidx, P->d_qp_inv};
     for (void* p : ptrs) dfree(p);
     precond_free(P);
     dfree(P->d_pc_Zb);
@@ -926,7 +929,28 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 // both free until the first evaluation)
                 GG_CUDA(cell_subsort(P->cg, nq, P->ncell, P->d_qp_start, (float4*)P->d_qp_pos,
                                      P->d_qp_perm, (float4*)P->d_qg, P->d_cursor, st));
-                GG_CUDA(to_soa(nq, P->d_qp_pos, P->d_qp_soa, P->soa_ld, st));
+                // padded layout: whole 64-point steps per cell (the cursors as
+                // scratch for the padded counts); the planes grow if it needs more
+                GG_CUDA(pad_layout_counts(P->ncell, P->d_qp_start, P->d_cursor, P->d_qp_pstart,
+                                          st));
+                int np = 0;
+                GG_CUDA(cudaMemcpyAsync(&np, P->d_qp_pstart + P->ncell, sizeof(int),
+                                        cudaMemcpyDeviceToHost, st));
+                GG_CUDA(cudaStreamSynchronize(st));
+                if ((size_t)np + 64 > P->soa_ld) {
+                    dfree(P->d_qp_soa);
+                    dfree(P->d_qg_soa);
+                    dfree(P->d_qp_inv);
+                    P->d_qp_soa = P->d_qg_soa = nullptr;
+                    P->d_qp_inv = nullptr;
+                    P->soa_ld = ((size_t)np + (size_t)np / 8 + 64 + 63) / 64 * 64;
+                    dalloc(P, &P->d_qp_soa, 3 * P->soa_ld);
+                    dalloc(P, &P->d_qg_soa, 3 * P->soa_ld);
+                    dalloc(P, &P->d_qp_inv, P->soa_ld);
+                }
+                GG_CUDA(pad_layout_fill(nq, P->soa_ld, P->d_qp_cell, P->d_qp_start,
+                                        P->d_qp_pstart, (const float4*)P->d_qp_pos, P->d_qp_soa,
+                                        P->d_qg_soa, P->soa_ld, P->d_qp_pidx, P->d_qp_inv, st));
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
             // weights into point order too (scratch: the strength buffer)
