@@ -696,9 +696,11 @@ __global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a
                      dz = tz - f2_make(qz.x, qz.y);
             const f2 r2 = fma2(dz, dz, fma2(dy, dy, dx * dx));
             float r0, r1;
+            // the strengths are loaded with the positions, before the test,
+            // so their latency overlaps the distance arithmetic
+            float2 wx = gx[h], wy = gy[h], wz = gz[h];
             f2_split(r2, r0, r1);
             if (!__any_sync(0xffffffffu, r0 < rc2 || r1 < rc2)) return;
-            float2 wx = gx[h], wy = gy[h], wz = gz[h];
             if (NEAR) {
                 if (r0 < a.near2) {
                     const int s = a.qinv[i];
@@ -1096,14 +1098,15 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
         const float* gs = (const float*)aux_g;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
         // ~11 KB of shared memory per block, 5 blocks per SM: ask for a small
-        // shared-memory carveout so that the rest of the SM's 256 KB serves as L1
+        // shared-memory carveout (25 %: the 64 KB configuration) so that the
+        // rest of the SM's 256 KB serves as L1
         // for the candidates the warps of a block re-read (a preference; cheap
         // per launch)
         const void* kf = layer == 0 ? (cg.reach == 3 ? (const void*)k_local_elem32<OUT_U, 3>
                                                      : (const void*)k_local_elem32<OUT_U, 2>)
                                     : (cg.reach == 3 ? (const void*)k_local_elem32<OUT_DBL, 3>
                                                      : (const void*)k_local_elem32<OUT_DBL, 2>);
-        cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
+        cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
         if (cg.reach == 3) {
             if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
             else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
