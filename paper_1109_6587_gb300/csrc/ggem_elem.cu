@@ -53,18 +53,20 @@ __global__ void k_qp_gen(int m, const double* __restrict__ x, const int* __restr
 // interleaved v4 (g) or, for the FP32 element rule, straight into the
 // structure-of-arrays planes x, y, z of stride ld (soa) at the padded slot
 // pidx[s] of each point
+// (in T throughout: q is the nodal density in T, so FP32 plans spend no FP64
+// instruction here -- GB300 runs FP64 at 1/64 of the FP32 rate)
 template <typename T>
 __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>* __restrict__ qw,
-                              const double* __restrict__ q, double scale, v4_t<T>* __restrict__ g,
+                              const T* __restrict__ q, T scale, v4_t<T>* __restrict__ g,
                               T* __restrict__ soa, size_t ld, const int* __restrict__ pidx) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int4 v = qv[s];
     v4_t<T> w = qw[s];
-    double a = scale * (double)w.x, b = scale * (double)w.y, c = scale * (double)w.z;
-    T rx = (T)(a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z]);
-    T ry = (T)(a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1]);
-    T rz = (T)(a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2]);
+    T a = scale * w.x, b = scale * w.y, c = scale * w.z;
+    T rx = a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z];
+    T ry = a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1];
+    T rz = a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2];
     if (soa) {
         const int p = pidx[s];
         soa[p] = rx;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(128) k_elem_correct(
     int n, int layer, T alpha, T rc2, const double* __restrict__ x, const int* __restrict__ tri,
     const double* __restrict__ tri_nrm, const double* __restrict__ nrm,
     const int* __restrict__ adj_start, const int* __restrict__ adj,
-    const double* __restrict__ q, QuadRule rule, T* __restrict__ out, int out_stride) {
+    const T* __restrict__ q, QuadRule rule, T* __restrict__ out, int out_stride) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const T al = alpha, al2 = alpha * alpha;
@@ -138,9 +140,9 @@ __global__ void __launch_bounds__(128) k_elem_correct(
         for (int d = 0; d < 3; ++d) {
             e2[d] = (T)(x[3 * i2 + d] - x[3 * b + d]);
             e3[d] = (T)(x[3 * i3 + d] - x[3 * b + d]);
-            q1[d] = (T)q[3 * b + d];
-            q2[d] = (T)q[3 * i2 + d];
-            q3[d] = (T)q[3 * i3 + d];
+            q1[d] = q[3 * b + d];
+            q2[d] = q[3 * i2 + d];
+            q3[d] = q[3 * i3 + d];
             nt[d] = (T)tri_nrm[3 * k + d];
         }
         T cx = e2[1] * e3[2] - e2[2] * e3[1], cy = e2[2] * e3[0] - e2[0] * e3[2],
@@ -255,13 +257,28 @@ cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, 
     return cudaMemcpyAsync(qw, tmp, (size_t)nq * sizeof(v4_t<T>), cudaMemcpyDeviceToDevice, st);
 }
 
+__global__ void k_density_f32(long n, const double* __restrict__ q, float* __restrict__ out) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (float)q[e];
+}
+
 template <typename T>
-cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
-                         double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
+cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, const double* q,
+                         T* qT, double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
                          cudaStream_t st) {
     if (soa && !pidx) return cudaErrorInvalidValue;
+    const T* qs;
+    if constexpr (sizeof(T) == 8) {
+        (void)qT;
+        qs = q;
+    } else {
+        if (!qT) return cudaErrorInvalidValue;
+        const long ne = 3L * nnodes;
+        if (ne > 0) k_density_f32<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, q, qT);
+        qs = qT;
+    }
     if (nq > 0)
-        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, q, scale, g, soa, ld,
+        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, qs, (T)scale, g, soa, ld,
                                                           pidx);
     return cudaGetLastError();
 }
@@ -269,7 +286,7 @@ cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double
 template <typename T>
 cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x, const int* tri,
                          const double* tri_nrm, const double* nrm, const int* adj_start,
-                         const int* adj, const double* q, const QuadRule& rule, T* out,
+                         const int* adj, const T* q, const QuadRule& rule, T* out,
                          int out_stride, cudaStream_t st) {
     if (n > 0)
         k_elem_correct<T><<<(n + 127) / 128, 128, 0, st>>>(
@@ -283,12 +300,12 @@ cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x,
                                        const QuadRule&, double*, int4*, v4_t<T>*, int, int*,    \
                                        int*, int*, int*, cudaStream_t);                         \
     template cudaError_t qp_sort_weights<T>(int, const int*, v4_t<T>*, v4_t<T>*, cudaStream_t); \
-    template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, const double*,      \
-                                         double, v4_t<T>*, T*, size_t, const int*,             \
+    template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, int, const double*, \
+                                         T*, double, v4_t<T>*, T*, size_t, const int*,         \
                                          cudaStream_t);                                        \
     template cudaError_t elem_correct<T>(int, int, const GridGeom&, const double*, const int*, \
                                          const double*, const double*, const int*, const int*,  \
-                                         const double*, const QuadRule&, T*, int, cudaStream_t);
+                                         const T*, const QuadRule&, T*, int, cudaStream_t);
 GGEM_INST_ELEM(float)
 GGEM_INST_ELEM(double)
 

@@ -239,6 +239,7 @@ struct ggem_plan {
     int* d_qp_pstart = nullptr;        // [ncell + 1] FP32 plans: padded cell starts
     int* d_qp_pidx = nullptr;          // [cap_qp] sorted point -> padded slot
     int* d_qp_inv = nullptr;           // [soa_ld] padded slot -> sorted point, -1 for dummies
+    float* d_q32 = nullptr;            // [cap][3] FP32 plans: the density in FP32
     int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
     double* d_orecd = nullptr;         // [4 cap] overlap records: node gap
     int* d_ocount = nullptr;           // record count
@@ -361,17 +362,19 @@ cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri
 template <typename T>
 cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, cudaStream_t st);
 // sorted point strengths g = scale sum_v (phi_v w) q_v from the sorted vertex
-// indices and weights: into g (v4), or into the planes soa[0, ld, 2 ld] at the
-// padded slots pidx[s] if soa
+// indices and weights, in T (FP32 plans first copy the nnodes x 3 density q
+// into qT): into g (v4), or into the planes soa[0, ld, 2 ld] at the padded
+// slots pidx[s] if soa
 template <typename T>
-cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, const double* q,
-                         double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
+cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, const double* q,
+                         T* qT, double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
                          cudaStream_t st);
-// polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double)
+// polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double);
+// q: the nodal density in T
 template <typename T>
 cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x, const int* tri,
                          const double* tri_nrm, const double* nrm, const int* adj_start,
-                         const int* adj, const double* q, const QuadRule& rule, T* out,
+                         const int* adj, const T* q, const QuadRule& rule, T* out,
                          int out_stride, cudaStream_t st);
 
 // locate targets: kind TK_POINTS (x[n][3]) or TK_WALL (the 2 Nz Nx wall nodes)

@@ -316,8 +316,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         GG_CUDA(gather_strengths<T>(n, P->d_mesh_perm, q, P->d_area, 8.0 * kPi * geo.mu,
                                     (v4_t<T>*)P->d_sg, st));
         if (elem)
-            GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, q,
-                                    8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
+            GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, n, q,
+                                    (T*)P->d_q32, 8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
                                     P->fp64 ? nullptr : (T*)P->d_qg_soa, P->soa_ld,
                                     P->d_qp_pidx, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
@@ -368,7 +368,9 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
-                                    P->d_adj_start, P->d_adj, q, P->rule, loc, 3, ls));
+                                    P->d_adj_start, P->d_adj,
+                                    P->fp64 ? (const T*)q : (const T*)P->d_q32, P->rule, loc, 3,
+                                    ls));
         });
     }
     run_global<T>(P, src, true, layer == 0 ? 1 : 2, gs);
@@ -717,6 +719,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             dalloc(P, &P->d_qp_inv, P->soa_ld);
             dalloc(P, &P->d_qp_pidx, cq);
             dalloc(P, &P->d_qp_pstart, (size_t)P->ncell + 1);
+            dalloc(P, &P->d_q32, (size_t)3 * cap);
         }
     }
     GG_CUDA(cudaEventCreate(&P->ev0));
@@ -763,7 +766,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
                     P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
                     P->d_spec_dz, P->d_spec_mid, P->d_spec_ct, P->d_mlp_tc,
-                    P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_pidx, P->d_qp_inv};
+                    P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_pidx, P->d_qp_inv, P->d_q32};
     for (void* p : ptrs) dfree(p);
     precond_free(P);
     dfree(P->d_pc_Zb);
