@@ -50,15 +50,15 @@ __global__ void k_qp_gen(int m, const double* __restrict__ x, const int* __restr
 
 // strengths of the sorted quadrature points: g = scale * sum_v (phi_v w) q_v,
 // from the vertex indices and weights already in point order (qv, qw); into
-// interleaved v4 (g) or, for the FP32 element rule, straight into the
-// structure-of-arrays planes x, y, z of stride ld (soa) at the padded slot
-// pidx[s] of each point
+// interleaved v4 (g) or, for the FP32 element rule, straight into the packed
+// point layout (pack: 12 floats per slot pair, gx gy gz at 6, 8, 10) at the
+// padded slot pidx[s] of each point
 // (in T throughout: q is the nodal density in T, so FP32 plans spend no FP64
 // instruction here -- GB300 runs FP64 at 1/64 of the FP32 rate)
 template <typename T>
 __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>* __restrict__ qw,
                               const T* __restrict__ q, T scale, v4_t<T>* __restrict__ g,
-                              T* __restrict__ soa, size_t ld, const int* __restrict__ pidx) {
+                              T* __restrict__ pack, const int* __restrict__ pidx) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int4 v = qv[s];
@@ -67,11 +67,12 @@ __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>*
     T rx = a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z];
     T ry = a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1];
     T rz = a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2];
-    if (soa) {
+    if (pack) {
         const int p = pidx[s];
-        soa[p] = rx;
-        soa[ld + p] = ry;
-        soa[2 * ld + p] = rz;
+        T* o = pack + 12 * (size_t)(p >> 1) + 6 + (p & 1);
+        o[0] = rx;
+        o[2] = ry;
+        o[4] = rz;
     } else {
         v4_t<T> r;
         r.x = rx; r.y = ry; r.z = rz; r.w = (T)0;
@@ -264,9 +265,9 @@ __global__ void k_density_f32(long n, const double* __restrict__ q, float* __res
 
 template <typename T>
 cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, const double* q,
-                         T* qT, double scale, v4_t<T>* g, T* soa, size_t ld, const int* pidx,
+                         T* qT, double scale, v4_t<T>* g, T* pack, const int* pidx,
                          cudaStream_t st) {
-    if (soa && !pidx) return cudaErrorInvalidValue;
+    if (pack && !pidx) return cudaErrorInvalidValue;
     const T* qs;
     if constexpr (sizeof(T) == 8) {
         (void)qT;
@@ -278,7 +279,7 @@ cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, 
         qs = qT;
     }
     if (nq > 0)
-        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, qs, (T)scale, g, soa, ld,
+        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, qs, (T)scale, g, pack,
                                                           pidx);
     return cudaGetLastError();
 }
@@ -301,7 +302,7 @@ cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x,
                                        int*, int*, int*, cudaStream_t);                         \
     template cudaError_t qp_sort_weights<T>(int, const int*, v4_t<T>*, v4_t<T>*, cudaStream_t); \
     template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, int, const double*, \
-                                         T*, double, v4_t<T>*, T*, size_t, const int*,         \
+                                         T*, double, v4_t<T>*, T*, const int*,                 \
                                          cudaStream_t);                                        \
     template cudaError_t elem_correct<T>(int, int, const GridGeom&, const double*, const int*, \
                                          const double*, const double*, const int*, const int*,  \

@@ -632,11 +632,12 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 // The element-rule local sum in FP32 reads ~700 quadrature points per cell
 // and finds about 80 % of them within r_cut, so no hit queue: every lane
 // takes two adjacent candidates of each 64-point step through a cell and
-// evaluates both with paired FP32 arithmetic.  The points are read from
-// structure-of-arrays copies (x, y, z and gx, gy, gz planes of stride ld) in
-// a padded layout: each cell starts on a multiple of 64 and fills whole steps
-// with dummies of zero strength far away, so a step needs no bounds test and
-// one 8-byte load brings a coordinate of both candidates already paired.
+// evaluates both with paired FP32 arithmetic.  The points are read from a
+// packed copy, 48 bytes per pair of adjacent points (x0 x1 y0 y1 | z0 z1 gx0
+// gx1 | gy0 gy1 gz0 gz1), so a lane's two candidates arrive with three 16-byte
+// loads, every coordinate already paired; the layout is padded: each cell
+// starts on a multiple of 64 points and fills whole steps with dummies of zero
+// strength far away, so a step needs no bounds test.
 // Candidates beyond r_cut are evaluated unmasked: their terms carry
 // exp(-alpha^2 r^2) <= e^-16 (and erfc(alpha r) <= 1.6e-8), below the FP32
 // rounding of the sum, and a step with no candidate within r_cut is skipped.
@@ -649,9 +650,7 @@ constexpr int kChunk = 64;    // candidates per warp step
 
 template <int MODE, int REACH>
 __global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a,
-                                                          const float* __restrict__ ps,
-                                                          const float* __restrict__ gs,
-                                                          size_t ld) {
+                                                          const float4* __restrict__ pk) {
     __shared__ int s_cst[LWE][kCap];
     __shared__ int s_cnt[LWE][kCap];
     __shared__ unsigned short s_off[LWE][kCap];
@@ -668,12 +667,6 @@ __global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a
     }
     const f2 nx2 = f2_splat(nx), ny2 = f2_splat(ny), nz2 = f2_splat(nz);
     const float rc2 = a.k.rc2;
-    const float2* px = (const float2*)ps;
-    const float2* py = (const float2*)(ps + ld);
-    const float2* pz = (const float2*)(ps + 2 * ld);
-    const float2* gx = (const float2*)gs;
-    const float2* gy = (const float2*)(gs + ld);
-    const float2* gz = (const float2*)(gs + 2 * ld);
     PairAcc2 acc;
     for (int round = 0; round < (side * side * side + 31) / 32;) {
     const int nc = cull_cells_batch<float, R>(a, lane, ox, oy, oz, cx, cy, cz, s_cst[wid],
@@ -691,14 +684,15 @@ __global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a
             constexpr bool NEAR = decltype(near_tag)::value;
             const int i = i0 + 2 * lane;          // even: candidates i and i + 1
             const int h = i >> 1;
-            const float2 qx = px[h], qy = py[h], qz = pz[h];
-            const f2 dx = tx - f2_make(qx.x, qx.y), dy = ty - f2_make(qy.x, qy.y),
-                     dz = tz - f2_make(qz.x, qz.y);
+            // positions and strengths in one go (the strengths before the test,
+            // so their latency overlaps the distance arithmetic)
+            const float4 pa = pk[3 * h], pb = pk[3 * h + 1], pc = pk[3 * h + 2];
+            const f2 dx = tx - f2_make(pa.x, pa.y), dy = ty - f2_make(pa.z, pa.w),
+                     dz = tz - f2_make(pb.x, pb.y);
             const f2 r2 = fma2(dz, dz, fma2(dy, dy, dx * dx));
             float r0, r1;
-            // the strengths are loaded with the positions, before the test,
-            // so their latency overlaps the distance arithmetic
-            float2 wx = gx[h], wy = gy[h], wz = gz[h];
+            float2 wx = make_float2(pb.z, pb.w), wy = make_float2(pc.x, pc.y),
+                   wz = make_float2(pc.z, pc.w);
             f2_split(r2, r0, r1);
             if (!__any_sync(0xffffffffu, r0 < rc2 || r1 < rc2)) return;
             if (NEAR) {
@@ -1020,35 +1014,37 @@ cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start,
     return cudaGetLastError();
 }
 
-// Padded structure-of-arrays layout of the sorted points for the FP32 element
-// rule: each cell's points start on a multiple of 64 and fill whole 64-point
-// steps; the slots after a cell's last point hold dummies (offset 1e4 from the
-// cell corner, strength zero), whose terms are exactly zero.
+// Padded, packed layout of the sorted points for the FP32 element rule: each
+// cell's points start on a multiple of 64 and fill whole 64-point steps; slot
+// pair h holds 12 floats x0 x1 y0 y1 z0 z1 gx0 gx1 gy0 gy1 gz0 gz1 (slots 2h,
+// 2h + 1); the slots after a cell's last point hold dummies (offset 1e4 from
+// the cell corner, strength zero), whose terms are exactly zero.
 __global__ void k_pad_counts(int ncell, const int* __restrict__ start, int* __restrict__ pcnt) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < ncell) pcnt[c] = (start[c + 1] - start[c] + 63) & ~63;
 }
 
-__global__ void k_pad_fill(size_t np, float v, float* __restrict__ out, size_t ld) {
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    out[p] = v;
-    out[ld + p] = v;
-    out[2 * ld + p] = v;
+__global__ void k_pad_fill(size_t npairs, float4* __restrict__ pack) {
+    const size_t h = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= npairs) return;
+    pack[3 * h] = make_float4(1e4f, 1e4f, 1e4f, 1e4f);
+    pack[3 * h + 1] = make_float4(1e4f, 1e4f, 0.f, 0.f);
+    pack[3 * h + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void k_pad_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
                               const int* __restrict__ pstart, const float4* __restrict__ pos,
-                              float* __restrict__ out, size_t ld, int* __restrict__ pidx,
+                              float* __restrict__ pack, int* __restrict__ pidx,
                               int* __restrict__ inv) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int c = cell[s];
     const int p = pstart[c] + (s - start[c]);
     const float4 v = pos[s];
-    out[p] = v.x;
-    out[ld + p] = v.y;
-    out[2 * ld + p] = v.z;
+    float* o = pack + 12 * (size_t)(p >> 1) + (p & 1);
+    o[0] = v.x;
+    o[2] = v.y;
+    o[4] = v.z;
     pidx[s] = p;
     inv[p] = s;
 }
@@ -1061,16 +1057,16 @@ cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstar
 }
 
 cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
-                            const int* pstart, const float4* pos, float* pos_soa, float* g_soa,
-                            size_t ld, int* pidx, int* inv, cudaStream_t st) {
+                            const int* pstart, const float4* pos, float* pack, int* pidx,
+                            int* inv, cudaStream_t st) {
     if (np > 0) {
-        k_pad_fill<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(np, 1e4f, pos_soa, ld);
-        cudaMemsetAsync(g_soa, 0, 3 * ld * sizeof(float), st);
+        const size_t npairs = np / 2;
+        k_pad_fill<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(npairs, (float4*)pack);
         cudaMemsetAsync(inv, 0xff, np * sizeof(int), st);
     }
     if (n > 0)
-        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pos_soa, ld,
-                                                      pidx, inv);
+        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pack, pidx,
+                                                      inv);
     return cudaGetLastError();
 }
 
@@ -1092,10 +1088,11 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
     LocalArgs<T> a{geo, cg, local_const<T>(geo, cg), src, qvs, (T)(near * near), tgt.n,
                    tgt.cell, tgt.pos, tgt.perm, nrm_tgt, out, out_stride};
     if constexpr (sizeof(T) == 4) {
-        if (!aux_pos || !aux_g || aux_ld == 0 || !aux_inv) return cudaErrorInvalidValue;
+        (void)aux_g;
+        (void)aux_ld;
+        if (!aux_pos || !aux_inv) return cudaErrorInvalidValue;
         a.qinv = aux_inv;
-        const float* ps = (const float*)aux_pos;
-        const float* gs = (const float*)aux_g;
+        const float4* pk = (const float4*)aux_pos;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
         // ~11 KB of shared memory per block, 5 blocks per SM: ask for a small
         // shared-memory carveout (25 %: the 64 KB configuration) so that the
@@ -1108,11 +1105,11 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
                                                      : (const void*)k_local_elem32<OUT_DBL, 2>);
         cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
         if (cg.reach == 3) {
-            if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
-            else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
+            if (layer == 0) k_local_elem32<OUT_U, 3><<<g, b, 0, st>>>(a, pk);
+            else k_local_elem32<OUT_DBL, 3><<<g, b, 0, st>>>(a, pk);
         } else {
-            if (layer == 0) k_local_elem32<OUT_U, 2><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
-            else k_local_elem32<OUT_DBL, 2><<<g, b, 0, st>>>(a, ps, gs, aux_ld);
+            if (layer == 0) k_local_elem32<OUT_U, 2><<<g, b, 0, st>>>(a, pk);
+            else k_local_elem32<OUT_DBL, 2><<<g, b, 0, st>>>(a, pk);
         }
         return cudaGetLastError();
     }

@@ -318,8 +318,7 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         if (elem)
             GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, n, q,
                                     (T*)P->d_q32, 8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
-                                    P->fp64 ? nullptr : (T*)P->d_qg_soa, P->soa_ld,
-                                    P->d_qp_pidx, st));
+                                    P->fp64 ? nullptr : (T*)P->d_qp_pack, P->d_qp_pidx, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
@@ -362,9 +361,8 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         stage(P, ST_LOCAL, 1, [&] {
             GG_CUDA(local_sum_elem<T>(geo, P->cg, qs, P->d_qv_sorted, 1.01 * P->near_edge, src,
                                       P->d_nrm, layer, loc, 3, ls,
-                                      P->fp64 ? P->d_qp_ff : (void*)P->d_qp_soa,
-                                      P->fp64 ? P->d_qg_ff : (void*)P->d_qg_soa, P->soa_ld,
-                                      P->d_qp_inv));
+                                      P->fp64 ? P->d_qp_ff : (void*)P->d_qp_pack,
+                                      P->fp64 ? P->d_qg_ff : nullptr, P->soa_ld, P->d_qp_inv));
         });
         stage(P, ST_ELEM, 1, [&] {
             GG_CUDA(elem_correct<T>(n, layer, geo, P->d_x, P->d_tri, P->d_tri_nrm, P->d_nrm,
@@ -714,8 +712,7 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
         }
         if (!P->fp64) {                    // padded planes; grown at mesh_set if needed
             P->soa_ld = (cq + cq / 8 + 64 + 63) / 64 * 64;
-            dalloc(P, &P->d_qp_soa, 3 * P->soa_ld);
-            dalloc(P, &P->d_qg_soa, 3 * P->soa_ld);
+            dalloc(P, &P->d_qp_pack, 6 * P->soa_ld);
             dalloc(P, &P->d_qp_inv, P->soa_ld);
             dalloc(P, &P->d_qp_pidx, cq);
             dalloc(P, &P->d_qp_pstart, (size_t)P->ncell + 1);
@@ -763,8 +760,8 @@ void plan_free(ggem_plan_t* P) {
                     P->d_pnodes, P->d_rc, P->d_rscale, P->d_mref, P->d_cx0, P->d_cdf,
                     P->d_cuinf, P->d_cfinf, P->d_cb, P->d_ckap, P->d_clam, P->d_cw, P->d_cq,
                     P->d_cmin, P->d_tstart, P->d_tlist, P->d_cvol, P->d_orec, P->d_orecd,
-                    P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_soa,
-                    P->d_qg_soa, P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
+                    P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_pack,
+                    P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
                     P->d_spec_dz, P->d_spec_mid, P->d_spec_ct, P->d_mlp_tc,
                     P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_pidx, P->d_qp_inv, P->d_q32};
     for (void* p : ptrs) dfree(p);
@@ -941,19 +938,17 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                                         cudaMemcpyDeviceToHost, st));
                 GG_CUDA(cudaStreamSynchronize(st));
                 if ((size_t)np + 64 > P->soa_ld) {
-                    dfree(P->d_qp_soa);
-                    dfree(P->d_qg_soa);
+                    dfree(P->d_qp_pack);
                     dfree(P->d_qp_inv);
-                    P->d_qp_soa = P->d_qg_soa = nullptr;
+                    P->d_qp_pack = nullptr;
                     P->d_qp_inv = nullptr;
                     P->soa_ld = ((size_t)np + (size_t)np / 8 + 64 + 63) / 64 * 64;
-                    dalloc(P, &P->d_qp_soa, 3 * P->soa_ld);
-                    dalloc(P, &P->d_qg_soa, 3 * P->soa_ld);
+                    dalloc(P, &P->d_qp_pack, 6 * P->soa_ld);
                     dalloc(P, &P->d_qp_inv, P->soa_ld);
                 }
                 GG_CUDA(pad_layout_fill(nq, P->soa_ld, P->d_qp_cell, P->d_qp_start,
-                                        P->d_qp_pstart, (const float4*)P->d_qp_pos, P->d_qp_soa,
-                                        P->d_qg_soa, P->soa_ld, P->d_qp_pidx, P->d_qp_inv, st));
+                                        P->d_qp_pstart, (const float4*)P->d_qp_pos, P->d_qp_pack,
+                                        P->d_qp_pidx, P->d_qp_inv, st));
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
             // weights into point order too (scratch: the strength buffer)
