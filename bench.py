@@ -179,7 +179,9 @@ FLOPS_PAIR_DOUBLE = 75
 # kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum; the
 # summaries are kept with the profiles), per (workload, precision, quadrature);
 # none for other configurations
-LOCAL_TRAFFIC = {}
+LOCAL_TRAFFIC = {
+    ("rbc4000", "mixed", "element"): (4687680000 + 41640448 + 5192181248 + 67060480) / 2,
+}
 
 SAMPLE_ABOVE = 100_000      # larger workloads count pairs on a sample of targets
 SAMPLE_TARGETS = 20_000
