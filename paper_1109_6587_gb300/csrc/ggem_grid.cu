@@ -25,30 +25,52 @@ template <typename T> struct Cx {
     static __device__ __forceinline__ C conj(C a) { return mk(a.x, -a.y); }
 };
 
-// In-place radix-2 DIT butterflies on R transforms of length M stored
-// contiguously in shared memory, input already in bit-reversed order.
+// In-place DIT butterflies on R transforms of length M stored contiguously
+// in shared memory, input already in bit-reversed order.
 // tw[k] = exp(-2 pi i k / M), k < M/2; inv selects the conjugate twiddles.
+// Two radix-2 stages (spans h and 2h) are fused into one radix-4 pass over
+// the quadruples i0, i0 + h, i0 + 2h, i0 + 3h: the first stage pairs them with
+// the twiddle W_2h^pos, the second with W_4h^pos and W_4h^(pos+h) =
+// W_4h^pos * (-i) (+i inverse); an odd number of stages starts with one
+// radix-2 pass.  Half the passes over shared memory and half the barriers of
+// the radix-2 form, same operations per element.
 template <typename T>
 __device__ void smem_fft(c2_t<T>* s, int R, int M, int logM, const c2_t<T>* __restrict__ tw,
                          bool inv) {
     using X = Cx<T>;
-    int half = M >> 1;
-    for (int lh = 0; lh < logM; ++lh) {
-        int h = 1 << lh;
+    int lh = 0;
+    if (logM & 1) {                         // one radix-2 pass (h = 1, twiddle 1)
         __syncthreads();
-        for (int b = threadIdx.x; b < R * half; b += blockDim.x) {
-            int r = b >> (logM - 1);
-            int jj = b & (half - 1);
-            int pos = jj & (h - 1);
-            int grp = jj >> lh;
-            int i0 = r * M + (grp << (lh + 1)) + pos;
-            int i1 = i0 + h;
-            c2_t<T> w = tw[pos << (logM - 1 - lh)];
-            if (inv) w.y = -w.y;
-            c2_t<T> a = s[i0];
-            c2_t<T> bb = X::mul(s[i1], w);
+        for (int b = threadIdx.x; b < R * (M >> 1); b += blockDim.x) {
+            const int i0 = 2 * b;
+            const c2_t<T> a = s[i0], bb = s[i0 + 1];
             s[i0] = X::add(a, bb);
-            s[i1] = X::sub(a, bb);
+            s[i0 + 1] = X::sub(a, bb);
+        }
+        lh = 1;
+    }
+    for (; lh < logM; lh += 2) {
+        const int h = 1 << lh;
+        const int q = M >> 2;               // quadruples per transform
+        __syncthreads();
+        for (int b = threadIdx.x; b < R * q; b += blockDim.x) {
+            const int r = b / q, jj = b - r * q;
+            const int pos = jj & (h - 1), grp = jj >> lh;
+            const int i0 = r * M + (grp << (lh + 2)) + pos;
+            c2_t<T> w1 = tw[pos << (logM - 1 - lh)];      // W_2h^pos
+            c2_t<T> w2 = tw[pos << (logM - 2 - lh)];      // W_4h^pos
+            if (inv) { w1.y = -w1.y; w2.y = -w2.y; }
+            // W_4h^(pos+h) = W_4h^pos * (-i) forward, * (+i) inverse
+            const c2_t<T> w3 = inv ? X::mk(-w2.y, w2.x) : X::mk(w2.y, -w2.x);
+            const c2_t<T> a = s[i0], bb = X::mul(s[i0 + h], w1);
+            const c2_t<T> c = s[i0 + 2 * h], d = X::mul(s[i0 + 3 * h], w1);
+            const c2_t<T> t0 = X::add(a, bb), t1 = X::sub(a, bb);
+            const c2_t<T> t2 = X::add(c, d), t3 = X::sub(c, d);
+            const c2_t<T> u2 = X::mul(t2, w2), u3 = X::mul(t3, w3);
+            s[i0] = X::add(t0, u2);
+            s[i0 + 2 * h] = X::sub(t0, u2);
+            s[i0 + h] = X::add(t1, u3);
+            s[i0 + 3 * h] = X::sub(t1, u3);
         }
     }
     __syncthreads();
