@@ -49,35 +49,52 @@ __global__ void k_qp_gen(int m, const double* __restrict__ x, const int* __restr
 }
 
 // strengths of the sorted quadrature points: g = scale * sum_v (phi_v w) q_v,
-// from the vertex indices and weights already in point order (qv, qw); into
-// interleaved v4 (g) or, for the FP32 element rule, straight into the packed
-// point layout (pack: 12 floats per slot pair, gx gy gz at 6, 8, 10) at the
-// padded slot pidx[s] of each point
-// (in T throughout: q is the nodal density in T, so FP32 plans spend no FP64
-// instruction here -- GB300 runs FP64 at 1/64 of the FP32 rate)
+// from the vertex indices and weights already in point order (qv, qw), into
+// interleaved v4 (g); in T throughout (q is the nodal density in T, so FP32
+// plans spend no FP64 instruction here -- GB300 runs FP64 at 1/64 of the FP32
+// rate)
+template <typename T>
+__device__ __forceinline__ void qp_strength_of(int s, const int4* __restrict__ qv,
+                                               const v4_t<T>* __restrict__ qw,
+                                               const T* __restrict__ q, T scale, T& rx, T& ry,
+                                               T& rz) {
+    const int4 v = qv[s];
+    const v4_t<T> w = qw[s];
+    const T a = scale * w.x, b = scale * w.y, c = scale * w.z;
+    rx = a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z];
+    ry = a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1];
+    rz = a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2];
+}
+
 template <typename T>
 __global__ void k_qp_strength(int n, const int4* __restrict__ qv, const v4_t<T>* __restrict__ qw,
-                              const T* __restrict__ q, T scale, v4_t<T>* __restrict__ g,
-                              T* __restrict__ pack, const int* __restrict__ pidx) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+                              const T* __restrict__ q, T scale, v4_t<T>* __restrict__ g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int4 v = qv[s];
-    v4_t<T> w = qw[s];
-    T a = scale * w.x, b = scale * w.y, c = scale * w.z;
-    T rx = a * q[3 * v.x] + b * q[3 * v.y] + c * q[3 * v.z];
-    T ry = a * q[3 * v.x + 1] + b * q[3 * v.y + 1] + c * q[3 * v.z + 1];
-    T rz = a * q[3 * v.x + 2] + b * q[3 * v.y + 2] + c * q[3 * v.z + 2];
-    if (pack) {
-        const int p = pidx[s];
-        T* o = pack + 12 * (size_t)(p >> 1) + 6 + (p & 1);
-        o[0] = rx;
-        o[2] = ry;
-        o[4] = rz;
-    } else {
-        v4_t<T> r;
-        r.x = rx; r.y = ry; r.z = rz; r.w = (T)0;
-        g[s] = r;
-    }
+    v4_t<T> r;
+    qp_strength_of<T>(s, qv, qw, q, scale, r.x, r.y, r.z);
+    r.w = (T)0;
+    g[s] = r;
+}
+
+// The same for the FP32 element rule, straight into the packed point layout:
+// one thread per pair of slots h (slots 2h, 2h + 1; inv maps a slot to its
+// sorted point, -1 for a dummy, whose strength stays zero), writing gx, gy, gz
+// of both as three 8-byte pairs at floats 6, 8, 10 of the pair's 12
+__global__ void k_qp_strength_pack(long npairs, const int* __restrict__ inv,
+                                   const int4* __restrict__ qv, const float4* __restrict__ qw,
+                                   const float* __restrict__ q, float scale,
+                                   float* __restrict__ pack) {
+    const long h = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= npairs) return;
+    const int s0 = inv[2 * h], s1 = inv[2 * h + 1];
+    float x0 = 0.f, y0 = 0.f, z0 = 0.f, x1 = 0.f, y1 = 0.f, z1 = 0.f;
+    if (s0 >= 0) qp_strength_of<float>(s0, qv, qw, q, scale, x0, y0, z0);
+    if (s1 >= 0) qp_strength_of<float>(s1, qv, qw, q, scale, x1, y1, z1);
+    float2* o = reinterpret_cast<float2*>(pack + 12 * h + 6);
+    o[0] = make_float2(x0, x1);
+    o[1] = make_float2(y0, y1);
+    o[2] = make_float2(z0, z1);
 }
 
 // out[s] = in[perm[s]] (the quadrature weights into point order)
@@ -265,22 +282,23 @@ __global__ void k_density_f32(long n, const double* __restrict__ q, float* __res
 
 template <typename T>
 cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, const double* q,
-                         T* qT, double scale, v4_t<T>* g, T* pack, const int* pidx,
+                         T* qT, double scale, v4_t<T>* g, T* pack, const int* inv, long nslots,
                          cudaStream_t st) {
-    if (pack && !pidx) return cudaErrorInvalidValue;
-    const T* qs;
     if constexpr (sizeof(T) == 8) {
         (void)qT;
-        qs = q;
+        (void)pack;
+        (void)inv;
+        (void)nslots;
+        if (nq > 0) k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, q, scale, g);
     } else {
-        if (!qT) return cudaErrorInvalidValue;
+        if (!qT || !pack || !inv) return cudaErrorInvalidValue;
         const long ne = 3L * nnodes;
         if (ne > 0) k_density_f32<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(ne, q, qT);
-        qs = qT;
+        const long npairs = nslots / 2;
+        if (npairs > 0)
+            k_qp_strength_pack<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(
+                npairs, inv, qv, qw, qT, (float)scale, pack);
     }
-    if (nq > 0)
-        k_qp_strength<T><<<(nq + 255) / 256, 256, 0, st>>>(nq, qv, qw, qs, (T)scale, g, pack,
-                                                          pidx);
     return cudaGetLastError();
 }
 
@@ -302,7 +320,7 @@ cudaError_t elem_correct(int n, int layer, const GridGeom& geo, const double* x,
                                        int*, int*, int*, cudaStream_t);                         \
     template cudaError_t qp_sort_weights<T>(int, const int*, v4_t<T>*, v4_t<T>*, cudaStream_t); \
     template cudaError_t qp_strengths<T>(int, const int4*, const v4_t<T>*, int, const double*, \
-                                         T*, double, v4_t<T>*, T*, const int*,                 \
+                                         T*, double, v4_t<T>*, T*, const int*, long,           \
                                          cudaStream_t);                                        \
     template cudaError_t elem_correct<T>(int, int, const GridGeom&, const double*, const int*, \
                                          const double*, const double*, const int*, const int*,  \

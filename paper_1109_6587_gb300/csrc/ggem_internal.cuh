@@ -235,8 +235,8 @@ struct ggem_plan {
     void* d_qg_ff = nullptr;           // [cap_qp][2] float4: sorted point strengths, hi / lo
     float* d_qp_pack = nullptr;        // [6 soa_ld] FP32 plans: packed point offsets and strengths
     size_t soa_ld = 0;                 // slots of the packed layout: padded size + 64, a multiple of 64
+    long qp_np = 0;                    // slots in use (the padded size, even)
     int* d_qp_pstart = nullptr;        // [ncell + 1] FP32 plans: padded cell starts
-    int* d_qp_pidx = nullptr;          // [cap_qp] sorted point -> padded slot
     int* d_qp_inv = nullptr;           // [soa_ld] padded slot -> sorted point, -1 for dummies
     float* d_q32 = nullptr;            // [cap][3] FP32 plans: the density in FP32
     int* d_orec = nullptr;             // [4 cap][2] overlap records: particle pair
@@ -335,13 +335,12 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
 // away; 12 floats per slot pair: x0 x1 y0 y1 z0 z1 gx0 gx1 gy0 gy1 gz0 gz1):
 // padded counts and starts (pcnt: ncell scratch, pstart: ncell + 1), then the
 // np slots of pack (np even; dummies at 1e4, strengths zero), the positions,
-// and the maps sorted point -> slot (pidx) and slot -> point (inv, -1 for
-// dummies)
+// and the map slot -> sorted point (inv, -1 for dummies)
 cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstart,
                               cudaStream_t st);
 cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
-                            const int* pstart, const float4* pos, float* pack, int* pidx,
-                            int* inv, cudaStream_t st);
+                            const int* pstart, const float4* pos, float* pack, int* inv,
+                            cudaStream_t st);
 // FP32 element rule: sub-sort the sorted points within each cell (4 x 4 x 4
 // sub-cells in Morton order; tmp_* of n entries as scratch)
 cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start, float4* pos,
@@ -363,12 +362,12 @@ cudaError_t elem_setup(int m, const double* x, const int* tri, const double* tri
 template <typename T>
 cudaError_t qp_sort_weights(int nq, const int* perm, v4_t<T>* qw, v4_t<T>* tmp, cudaStream_t st);
 // sorted point strengths g = scale sum_v (phi_v w) q_v from the sorted vertex
-// indices and weights, in T (FP32 plans first copy the nnodes x 3 density q
-// into qT): into g (v4), or into the packed layout (pad_layout_fill) at the
-// padded slots pidx[s] if pack
+// indices and weights, in T: FP64 plans into g (v4); FP32 plans copy the
+// nnodes x 3 density q into qT, then fill the strengths of the nslots slots of
+// the packed layout (pad_layout_fill; inv: slot -> sorted point)
 template <typename T>
 cudaError_t qp_strengths(int nq, const int4* qv, const v4_t<T>* qw, int nnodes, const double* q,
-                         T* qT, double scale, v4_t<T>* g, T* pack, const int* pidx,
+                         T* qT, double scale, v4_t<T>* g, T* pack, const int* inv, long nslots,
                          cudaStream_t st);
 // polar-rule correction of the local part at the mesh nodes (layer 0 single, 1 double);
 // q: the nodal density in T

@@ -1034,8 +1034,7 @@ __global__ void k_pad_fill(size_t npairs, float4* __restrict__ pack) {
 
 __global__ void k_pad_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
                               const int* __restrict__ pstart, const float4* __restrict__ pos,
-                              float* __restrict__ pack, int* __restrict__ pidx,
-                              int* __restrict__ inv) {
+                              float* __restrict__ pack, int* __restrict__ inv) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int c = cell[s];
@@ -1045,7 +1044,6 @@ __global__ void k_pad_scatter(int n, const int* __restrict__ cell, const int* __
     o[0] = v.x;
     o[2] = v.y;
     o[4] = v.z;
-    pidx[s] = p;
     inv[p] = s;
 }
 
@@ -1057,16 +1055,15 @@ cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstar
 }
 
 cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
-                            const int* pstart, const float4* pos, float* pack, int* pidx,
-                            int* inv, cudaStream_t st) {
+                            const int* pstart, const float4* pos, float* pack, int* inv,
+                            cudaStream_t st) {
     if (np > 0) {
         const size_t npairs = np / 2;
         k_pad_fill<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(npairs, (float4*)pack);
         cudaMemsetAsync(inv, 0xff, np * sizeof(int), st);
     }
     if (n > 0)
-        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pack, pidx,
-                                                      inv);
+        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pack, inv);
     return cudaGetLastError();
 }
 

@@ -318,7 +318,7 @@ void layer_impl(ggem_plan_t* P, int layer, const double* q, double* out) {
         if (elem)
             GG_CUDA(qp_strengths<T>(P->n_qp, P->d_qv_sorted, (const v4_t<T>*)P->d_qw, n, q,
                                     (T*)P->d_q32, 8.0 * kPi * geo.mu, (v4_t<T>*)P->d_qg,
-                                    P->fp64 ? nullptr : (T*)P->d_qp_pack, P->d_qp_pidx, st));
+                                    (T*)P->d_qp_pack, P->d_qp_inv, P->qp_np, st));
         if (elem && P->ff) GG_CUDA(to_float_pairs(P->n_qp, P->d_qg, P->d_qg_ff, st));
     });
     SortedSources<T> src = sources_of<T>(P, true);
@@ -714,7 +714,6 @@ void plan_build(ggem_plan_t* P, const ggem_params& prm) {
             P->soa_ld = (cq + cq / 8 + 64 + 63) / 64 * 64;
             dalloc(P, &P->d_qp_pack, 6 * P->soa_ld);
             dalloc(P, &P->d_qp_inv, P->soa_ld);
-            dalloc(P, &P->d_qp_pidx, cq);
             dalloc(P, &P->d_qp_pstart, (size_t)P->ncell + 1);
             dalloc(P, &P->d_q32, (size_t)3 * cap);
         }
@@ -763,7 +762,7 @@ void plan_free(ggem_plan_t* P) {
                     P->d_ocount, P->d_odisp, P->d_qp_ff, P->d_qg_ff, P->d_qp_pack,
                     P->d_spec, P->d_spec_twx, P->d_spec_twz, P->d_spec_dx,
                     P->d_spec_dz, P->d_spec_mid, P->d_spec_ct, P->d_mlp_tc,
-                    P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_pidx, P->d_qp_inv, P->d_q32};
+                    P->d_mlp_tcs, P->d_qp_pstart, P->d_qp_inv, P->d_q32};
     for (void* p : ptrs) dfree(p);
     precond_free(P);
     dfree(P->d_pc_Zb);
@@ -948,7 +947,8 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                 }
                 GG_CUDA(pad_layout_fill(nq, P->soa_ld, P->d_qp_cell, P->d_qp_start,
                                         P->d_qp_pstart, (const float4*)P->d_qp_pos, P->d_qp_pack,
-                                        P->d_qp_pidx, P->d_qp_inv, st));
+                                        P->d_qp_inv, st));
+                P->qp_np = np;
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
             // weights into point order too (scratch: the strength buffer)

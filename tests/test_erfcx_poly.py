@@ -1,10 +1,10 @@
 """The pair kernels form erfc(x) = exp(-x^2) erfcx(x) with the approximations
 of ggem_erfcx.cuh on 0 <= x <= 4 (alpha r inside the cutoff).  FP32:
-erfcx(x) ~ t Q(t), t = 1/(1 + P x), Q of degree 7 in t.  Its coefficients, read
-from the generated header, must approximate scipy's erfcx to 2e-8 relative in
-FP64 and to 5e-7 (a few FP32 ulps, like CUDA's erfcf) when t and the Horner
-scheme are evaluated in FP32 (the rounding of t dominates).  FP64: 8 pieces of
-degree 12."""
+erfcx(x) ~ t Q(t), t = 1/(1 + P x), Q of degree 6 in t.  Its coefficients, read
+from the generated header, must approximate scipy's erfcx to 2e-7 relative in
+FP64 (about the rounding of its own FP32 evaluation) and to 5e-7 (a few FP32
+ulps, like CUDA's erfcf) when t and the Horner scheme are evaluated in FP32.
+FP64: 8 pieces of degree 12."""
 import pathlib
 import re
 
@@ -35,7 +35,7 @@ def _table64():
 
 def test_polynomial_error():
     c = _coefficients()
-    assert len(c) == 8
+    assert len(c) == 7
     p = _p()
     x = np.linspace(0.0, 4.0, 100001)
     ref = special.erfcx(x)
@@ -43,7 +43,7 @@ def test_polynomial_error():
     q = np.full_like(t, c[0])
     for a in c[1:]:
         q = q * t + a
-    assert np.abs(q * t / ref - 1).max() < 2e-8
+    assert np.abs(q * t / ref - 1).max() < 2e-7
     x32 = x.astype(np.float32)
     t32 = (np.float32(1) / (np.float32(p) * x32 + np.float32(1))).astype(np.float32)
     q32 = np.full_like(t32, np.float32(c[0]))
