@@ -644,12 +644,12 @@ __global__ void __launch_bounds__(LW * 32) k_local(LocalArgs<T> a) {
 // Points of the triangles around the target (left to the singular
 // correction) can only lie in the cells the culling marks near; only there
 // is each candidate within near2 checked and, if excluded, given zero strength.
-constexpr int LWE = 8;        // warps (targets) per block; 5 blocks per SM (48 registers)
+constexpr int LWE = 4;        // warps (targets) per block; 10 blocks per SM (48 registers)
 constexpr int kCap = 128;     // culled cells per batch (a target may need several batches)
 constexpr int kChunk = 64;    // candidates per warp step
 
 template <int MODE, int REACH>
-__global__ void __launch_bounds__(LWE * 32, 5) k_local_elem32(LocalArgs<float> a,
+__global__ void __launch_bounds__(LWE * 32, 10) k_local_elem32(LocalArgs<float> a,
                                                           const float4* __restrict__ pk) {
     __shared__ int s_cst[LWE][kCap];
     __shared__ int s_cnt[LWE][kCap];
@@ -1091,7 +1091,7 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
         a.qinv = aux_inv;
         const float4* pk = (const float4*)aux_pos;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
-        // ~11 KB of shared memory per block, 5 blocks per SM: ask for a small
+        // ~6 KB of shared memory per block, 10 blocks per SM: ask for a small
         // shared-memory carveout (25 %: the 64 KB configuration) so that the
         // rest of the SM's 256 KB serves as L1
         // for the candidates the warps of a block re-read (a preference; cheap
