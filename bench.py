@@ -172,8 +172,8 @@ def _peaks():
 
 
 # Algorithmic flops of one (target, source) pair of the local sum (see roofline)
-FLOPS_PAIR_SINGLE = 53
-FLOPS_PAIR_DOUBLE = 73
+FLOPS_PAIR_SINGLE = 52
+FLOPS_PAIR_DOUBLE = 72
 # DRAM bytes (read + write) of one local-sum launch, the single- and the
 # double-layer launch averaged as the stage is, from ncu captures of the
 # kernels as they stand (dram__bytes_read.sum + dram__bytes_write.sum; the
@@ -349,13 +349,14 @@ def roofline(res, args):
         # algorithmic flops per (target, source) pair within r_cut, counting
         # add, sub, mul and rsqrt / exp2 as 1 and a fused multiply-add as 2
         # (the peak below counts an FMA as 2): displacement, r^2, 1/r, r,
-        # exp(-alpha^2 r^2), erfc(alpha r) = exp(-alpha^2 r^2) erfcx(alpha r)
-        # with erfcx = t Q(t), t = 1/(1 + P alpha r), Q of degree 6 (17),
-        # x.g -- 34 -- then the single layer's A = erfc/r - c1 e,
-        # B = (erfc/r^3 + c1 e/r^2) x.g and u += A g + B x (19: 53 in all) or
-        # the double layer's D, E, x.n, g.n and v += x (D x.g x.n + E g.n) +
-        # g E x.n + n E x.g with the last term summed as a scalar (39: 73 in
-        # all); the stage averages one launch of each
+        # exp(-alpha^2 r^2) as one exp2 of the scaled r^2, erfc(alpha r) =
+        # exp(-alpha^2 r^2) erfcx(alpha r) with erfcx = t Q(t),
+        # t = 1/(1 + P alpha r), Q of degree 6 (17), x.g -- 33 -- then the
+        # single layer's A = erfc/r - c1 e, B = (erfc/r^3 + c1 e/r^2) x.g and
+        # u += A g + B x (19: 52 in all) or the double layer's D, E, x.n, g.n
+        # and v += x (D x.g x.n + E g.n) + g E x.n + n E x.g with the last
+        # term summed as a scalar (39: 72 in all); the stage averages one
+        # launch of each
         flops = pairs * (FLOPS_PAIR_SINGLE + FLOPS_PAIR_DOUBLE) / 2.0
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = flops / avg_s / 1e12

@@ -334,13 +334,14 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
 // from a multiple of 64, whole 64-point steps, dummies of zero strength far
 // away; 12 floats per slot pair: x0 x1 y0 y1 z0 z1 gx0 gx1 gy0 gy1 gz0 gz1):
 // padded counts and starts (pcnt: ncell scratch, pstart: ncell + 1), then the
-// np slots of pack (np even; dummies at 1e4, strengths zero), the positions,
-// and the map slot -> sorted point (inv, -1 for dummies)
+// np slots of pack (np even; dummies at 1e4, strengths zero), the positions
+// (scaled by alpha sqrt(log2 e), the local-sum kernel's units), and the map
+// slot -> sorted point (inv, -1 for dummies)
 cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstart,
                               cudaStream_t st);
 cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
-                            const int* pstart, const float4* pos, float* pack, int* inv,
-                            cudaStream_t st);
+                            const int* pstart, const float4* pos, double alpha, float* pack,
+                            int* inv, cudaStream_t st);
 // FP32 element rule: sub-sort the sorted points within each cell (4 x 4 x 4
 // sub-cells in Morton order; tmp_* of n entries as scratch)
 cudaError_t cell_subsort(const CellGrid& cg, int n, int ncell, const int* start, float4* pos,

@@ -158,6 +158,9 @@ cudaError_t gather_strengths(int n, const int* perm, const double* q, const doub
 template <typename T> struct LocalConst {
     T al, al2, rc2, c1, c2, c3, c4, fU, fS, hx, hy, hz;
     T ke;   // -alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(ke r^2)
+    // FP32 element rule (scaled coordinates, see elem32_const): the
+    // coordinate scale s, the reciprocal's slope P alpha / s, and -6 s^3
+    T sc = (T)1, pt = (T)0, c6 = (T)-6;
 };
 
 template <typename T> LocalConst<T> local_const(const GridGeom& geo, const CellGrid& cg) {
@@ -311,6 +314,11 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return r;
 }
 
+// In the FP32 element rule the coordinates are scaled by s = alpha sqrt(log2 e)
+// (elem32_const), so exp(-alpha^2 r^2) = 2^(-r_s^2) takes no multiply; the
+// displacements, r and 1/r below are in scaled units, and the constants
+// (c1 / s, c2 s^2, -6 s^3, the output factor s or 1 / s) make every term the
+// unscaled one.
 template <int MODE>
 __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f2 dy, f2 dz,
                                             f2 r2, f2 gx, f2 gy, f2 gz, f2 nx, f2 ny, f2 nz,
@@ -318,10 +326,9 @@ __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f
     float lo, hi;
     f2_split(r2, lo, hi);
     const f2 ir = f2_make(rsqrt_ftz(lo), rsqrt_ftz(hi));
+    const f2 ex = f2_make(ex2_ftz(-lo), ex2_ftz(-hi));               // exp(-alpha^2 r^2)
     const f2 r = r2 * ir;
-    f2_split(f2_splat(k.ke) * r2, lo, hi);
-    const f2 ex = f2_make(ex2_ftz(lo), ex2_ftz(hi));                 // exp(-alpha^2 r^2)
-    f2_split(fma2(r, f2_splat(GGEM_ERFCX_P * k.al), f2_splat(1.0f)), lo, hi);
+    f2_split(fma2(r, f2_splat(k.pt), f2_splat(1.0f)), lo, hi);
     const f2 t = f2_make(rcp_ftz(lo), rcp_ftz(hi));                 // 1/(1 + P alpha r)
     const f2 ec = ex * erfcx_t2(t);                                  // erfc(alpha r)
     const f2 xg = fma2(dz, gz, fma2(dy, gy, dx * gx));
@@ -340,7 +347,7 @@ __device__ __forceinline__ void pair_terms2(const LocalConst<float>& k, f2 dx, f
         // d (D xg xn + E gn) + g (E xn) + n (E xg), the last term's scalar E xg
         // summed over the pairs and multiplied by the (fixed) target normal once
         const f2 ir2 = ir * ir;
-        const f2 t = fma2(f2_splat(-6.0f), ec * ir, f2_splat(-k.c2) * ex);
+        const f2 t = fma2(f2_splat(k.c6), ec * ir, f2_splat(-k.c2) * ex);
         const f2 D = ir2 * fma2(ir2, t, f2_splat(-k.c3) * ex);
         const f2 E = f2_splat(k.c4) * ex;
         const f2 xn = fma2(dz, nz, fma2(dy, ny, dx * nx));
@@ -660,6 +667,9 @@ __global__ void __launch_bounds__(LWE * 32, 10) k_local_elem32(LocalArgs<float> 
     int cx, cy, cz, oidx;
     float ox, oy, oz;
     load_target<float, TK_POINTS>(a, t, ox, oy, oz, cx, cy, cz, oidx);
+    ox *= a.k.sc;                                 // scaled coordinates (elem32_const)
+    oy *= a.k.sc;
+    oz *= a.k.sc;
     constexpr int R = REACH, side = 2 * R + 1;
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (MODE & OUT_DBL) {
@@ -1034,16 +1044,16 @@ __global__ void k_pad_fill(size_t npairs, float4* __restrict__ pack) {
 
 __global__ void k_pad_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
                               const int* __restrict__ pstart, const float4* __restrict__ pos,
-                              float* __restrict__ pack, int* __restrict__ inv) {
+                              float sc, float* __restrict__ pack, int* __restrict__ inv) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int c = cell[s];
     const int p = pstart[c] + (s - start[c]);
     const float4 v = pos[s];
     float* o = pack + 12 * (size_t)(p >> 1) + (p & 1);
-    o[0] = v.x;
-    o[2] = v.y;
-    o[4] = v.z;
+    o[0] = v.x * sc;
+    o[2] = v.y * sc;
+    o[4] = v.z * sc;
     inv[p] = s;
 }
 
@@ -1054,16 +1064,19 @@ cudaError_t pad_layout_counts(int ncell, const int* start, int* pcnt, int* pstar
     return scan_counts(ncell, pcnt, pstart, st);
 }
 
+float elem32_scale(double alpha) { return (float)(alpha * 1.2011224087864498); }
+
 cudaError_t pad_layout_fill(int n, size_t np, const int* cell, const int* start,
-                            const int* pstart, const float4* pos, float* pack, int* inv,
-                            cudaStream_t st) {
+                            const int* pstart, const float4* pos, double alpha, float* pack,
+                            int* inv, cudaStream_t st) {
     if (np > 0) {
         const size_t npairs = np / 2;
         k_pad_fill<<<(unsigned)((npairs + 255) / 256), 256, 0, st>>>(npairs, (float4*)pack);
         cudaMemsetAsync(inv, 0xff, np * sizeof(int), st);
     }
     if (n > 0)
-        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos, pack, inv);
+        k_pad_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell, start, pstart, pos,
+                                                      elem32_scale(alpha), pack, inv);
     return cudaGetLastError();
 }
 
@@ -1089,6 +1102,23 @@ cudaError_t local_sum_elem(const GridGeom& geo, const CellGrid& cg, const Sorted
         (void)aux_ld;
         if (!aux_pos || !aux_inv) return cudaErrorInvalidValue;
         a.qinv = aux_inv;
+        // scaled coordinates: lengths times s = alpha sqrt(log2 e), the
+        // packed points scaled likewise at mesh_set (pad_layout_fill)
+        {
+            const double sc = (double)elem32_scale(geo.alpha);
+            LocalConst<float>& k = a.k;
+            k.sc = (float)sc;
+            k.hx = (float)(cg.hx * sc);
+            k.hy = (float)(cg.hy * sc);
+            k.hz = (float)(cg.hz * sc);
+            k.rc2 = (float)(geo.rcut * geo.rcut * sc * sc);
+            a.near2 = (float)(near * near * sc * sc);
+            k.pt = (float)(GGEM_ERFCX_P * geo.alpha / sc);
+            k.c1 = (float)(2.0 * geo.alpha / 1.7724538509055160273 / sc);
+            k.c2 = (float)(12.0 * geo.alpha / 1.7724538509055160273 * sc * sc);
+            k.c6 = (float)(-6.0 * sc * sc * sc);
+            k.fU = (float)(layer == 0 ? sc : 1.0 / sc) * k.fU;
+        }
         const float4* pk = (const float4*)aux_pos;
         dim3 b(LWE * 32), g((tgt.n + LWE - 1) / LWE);
         // ~6 KB of shared memory per block, 10 blocks per SM: ask for a small

@@ -946,8 +946,8 @@ ggem_status ggem_mesh_set(ggem_plan_t* P, int n_nodes, const double* x, int n_tr
                     dalloc(P, &P->d_qp_inv, P->soa_ld);
                 }
                 GG_CUDA(pad_layout_fill(nq, P->soa_ld, P->d_qp_cell, P->d_qp_start,
-                                        P->d_qp_pstart, (const float4*)P->d_qp_pos, P->d_qp_pack,
-                                        P->d_qp_inv, st));
+                                        P->d_qp_pstart, (const float4*)P->d_qp_pos,
+                                        P->geo.alpha, P->d_qp_pack, P->d_qp_inv, st));
                 P->qp_np = np;
             }
             GG_CUDA(gather_int4(nq, P->d_qp_perm, P->d_qv, P->d_qv_sorted, st));
