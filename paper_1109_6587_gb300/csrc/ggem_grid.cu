@@ -320,15 +320,18 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
     if (t >= a.n) return;
     const GridGeom& geo = a.geo;
     double xt = a.x[3 * t], yt = a.x[3 * t + 1], zt = a.x[3 * t + 2];
-    double ux = xt / geo.dx, uz = zt / geo.dz;
+    // grid coordinates in FP64 (positions up to the box size), by multiplies:
+    // GB300 runs FP64 at 1/64 of FP32 and an FP64 divide is a long sequence
+    double ux = xt * (1.0 / geo.dx), uz = zt * (1.0 / geo.dz);
     double i0 = rint(ux), k0 = rint(uz);
     T wx[5], wz[5], wy[5];
     lag5_uniform<T>((T)(ux - i0), wx);
     lag5_uniform<T>((T)(uz - k0), wz);
     int N = geo.Ny - 1;
-    double yb = fmin(1.0, fmax(-1.0, 2.0 * (yt - geo.y0) / geo.W - 1.0));
-    const double pi = 3.14159265358979323846;
-    int jc = (int)rint(acos(yb) * N / pi);
+    double yb = fmin(1.0, fmax(-1.0, (yt - geo.y0) * (2.0 / geo.W) - 1.0));
+    // first guess of the nearest Chebyshev node from theta = acos(yb) in FP32
+    // (the search below compares the FP64 distances to its neighbours)
+    int jc = (int)rintf(acosf((float)yb) * ((float)N * 0.318309886f));
     jc = min(max(jc, 0), N);
     int jbest = jc;
     double dbest = fabs(yt - a.yj[jc]);
@@ -344,12 +347,24 @@ __global__ void __launch_bounds__(128) k_interp(InterpArgs<T> a) {
     double yn[5];
 #pragma unroll
     for (int p = 0; p < 5; ++p) yn[p] = a.yj[js + p];
+    // Lagrange weights in y: the five FP64 differences to the target and the
+    // ten between the nodes, each rounded once to T
+    T dt[5], dn[5][5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dt[q] = (T)(yt - yn[q]);
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+#pragma unroll
+        for (int q = p + 1; q < 5; ++q) {
+            dn[p][q] = (T)(yn[p] - yn[q]);
+            dn[q][p] = -dn[p][q];
+        }
 #pragma unroll
     for (int p = 0; p < 5; ++p) {
         T v = 1;
 #pragma unroll
         for (int q = 0; q < 5; ++q)
-            if (q != p) v *= (T)(yt - yn[q]) / (T)(yn[p] - yn[q]);
+            if (q != p) v *= dt[q] / dn[p][q];
         wy[p] = v;
     }
     int ib = (int)(((long)i0 - 2) % geo.Nx); ib += (ib < 0) ? geo.Nx : 0;
