@@ -307,20 +307,23 @@ cudaError_t spread(const GridGeom& geo, const CellGrid& cg, const double* yj, co
     size_t nodes = (size_t)geo.Ny * geo.Nz * geo.Nx;
     cudaMemsetAsync(work, 0, nodes * 4 * sizeof(T), st);
     if (src.n > 0) {
-        if (sizeof(T) == 4 && list && geo.Ny <= PMAXJ) {
-            // pairs of sources; the pairs that do not fit go back to the single path
-            int* nleft = list + src.n;
-            cudaMemsetAsync(nleft, 0, sizeof(int), st);
-            const int npairs = (src.n + 1) / 2;
-            k_spread_pair<<<(npairs + SW - 1) / SW, SW * 32, 0, st>>>(
-                geo, *reinterpret_cast<const SpreadConst<float>*>(&kc), (const float*)ydiff,
-                src.n, R, di, (const float4*)df, (const float4*)src.g, (float*)work, list, nleft);
-            k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(
-                geo, kc, ydiff, src.n, R, di, df, src.g, work, list, nleft);
-        } else {
+        bool paired = false;
+        if constexpr (sizeof(T) == 4) {
+            if (list && geo.Ny <= PMAXJ) {
+                // pairs of sources; the pairs that do not fit go back to the single path
+                int* nleft = list + src.n;
+                cudaMemsetAsync(nleft, 0, sizeof(int), st);
+                const int npairs = (src.n + 1) / 2;
+                k_spread_pair<<<(npairs + SW - 1) / SW, SW * 32, 0, st>>>(
+                    geo, kc, ydiff, src.n, R, di, df, src.g, work, list, nleft);
+                k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(
+                    geo, kc, ydiff, src.n, R, di, df, src.g, work, list, nleft);
+                paired = true;
+            }
+        }
+        if (!paired)
             k_spread_scatter<T><<<(src.n + SW - 1) / SW, SW * 32, 0, st>>>(
                 geo, kc, ydiff, src.n, R, di, df, src.g, work, nullptr, nullptr);
-        }
     }
     k_deinterleave<T><<<(unsigned)((nodes + 255) / 256), 256, 0, st>>>(geo.Ny, geo.Nz, geo.Nx,
                                                                        work, grid);
