@@ -158,7 +158,7 @@ cudaError_t gather_strengths(int n, const int* perm, const double* q, const doub
 template <typename T> struct LocalConst {
     T al, al2, rc2, c1, c2, c3, c4, fU, fS, hx, hy, hz;
     T ke;   // -alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(ke r^2)
-    // FP32 element rule (scaled coordinates, see elem32_const): the
+    // FP32 element rule (scaled coordinates, set by local_sum_elem): the
     // coordinate scale s, the reciprocal's slope P alpha / s, and -6 s^3
     T sc = (T)1, pt = (T)0, c6 = (T)-6;
 };
@@ -315,7 +315,7 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 }
 
 // In the FP32 element rule the coordinates are scaled by s = alpha sqrt(log2 e)
-// (elem32_const), so exp(-alpha^2 r^2) = 2^(-r_s^2) takes no multiply; the
+// (local_sum_elem), so exp(-alpha^2 r^2) = 2^(-r_s^2) takes no multiply; the
 // displacements, r and 1/r below are in scaled units, and the constants
 // (c1 / s, c2 s^2, -6 s^3, the output factor s or 1 / s) make every term the
 // unscaled one.
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(LWE * 32, 10) k_local_elem32(LocalArgs<float> 
     int cx, cy, cz, oidx;
     float ox, oy, oz;
     load_target<float, TK_POINTS>(a, t, ox, oy, oz, cx, cy, cz, oidx);
-    ox *= a.k.sc;                                 // scaled coordinates (elem32_const)
+    ox *= a.k.sc;                                 // scaled coordinates (set by local_sum_elem)
     oy *= a.k.sc;
     oz *= a.k.sc;
     constexpr int R = REACH, side = 2 * R + 1;
