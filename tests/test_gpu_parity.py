@@ -224,6 +224,31 @@ def test_element_single_and_double_layer(ggem, prec):
     assert_close(v, v_ref, TOL[prec])
 
 
+def test_element_padded_layout_grows(ggem):
+    """Mixed plan sized exactly for the mesh: padding every cell's quadrature
+    points to whole 64-point steps needs more slots than the plan set aside,
+    so mesh_set grows the packed layout; the element rule still matches the
+    oracle, again after a second mesh_set of a moved mesh."""
+    s = W.single_sphere(radius=R_STRICT)
+    q = W.normal_forces(s.x.shape[0], seed=17)
+    P = ggem.Plan.for_box(s.box, precision="mixed", quadrature="element",
+                          max_points=s.x.shape[0], max_tris=s.tri.shape[0])
+    for shift in (0.0, 0.37):
+        x = s.x + np.array([shift, 0.0, 0.5 * shift])
+        moved = W.Suspension(box=s.box, x=x, tri=s.tri, particle=s.particle,
+                             centres=s.centres + np.array([shift, 0.0, 0.5 * shift]),
+                             radius=s.radius)
+        w_ref = O.single_layer(moved, q, quadrature="element")
+        v_ref = O.double_layer(moved, q, quadrature="element")
+        P.mesh_set(_dev(x), torch.as_tensor(s.tri, device="cuda"))
+        w = P.single_layer(_dev(q))
+        v = P.double_layer(_dev(q))
+        torch.cuda.synchronize()
+        assert_close(w, w_ref, TOL["mixed"])
+        assert_close(v, v_ref, TOL["mixed"])
+    P.check()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_emulated"])
 def test_element_100_capsules_sampled(ggem, prec):
     s = W.capsules_100()
