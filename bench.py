@@ -424,8 +424,12 @@ def oracle_sample_step(susp, args, seed, aux):
 
     pick = lambda total, k: np.sort(rng.choice(total, min(k, total), replace=False))
     tri_s = pick(m, S["triangles"])
-    # geometry: once per layer evaluation
-    run("geometry", m / len(tri_s), lambda: O.geometry(susp.x, susp.tri[tri_s]), reps=2)
+    # geometry: once per layer evaluation (the nodes no sampled triangle touches
+    # get 0/0 normals in the sample, which are not used)
+    def geometry_sample():
+        with np.errstate(invalid="ignore"):
+            return O.geometry(susp.x, susp.tri[tri_s])
+    run("geometry", m / len(tri_s), geometry_sample, reps=2)
     tg = pick(n, S["targets"]).astype(np.int32)
     run("local_single", n / len(tg),
         lambda: O.local_elem(box, a, rc, 0, susp.x, susp.tri, q, targets=tg))
